@@ -1,0 +1,172 @@
+/*
+ * gbnfft.h - C ABI of a nonequispaced fast Fourier transform (NFFT) for one NVIDIA GB300 GPU.
+ *
+ * The library computes, for d = 1, 2 or 3, the NFFT of Schmischke, "NFFT Interface for Julia"
+ * (arXiv 1810.09891), Section 2:
+ *
+ *   forward (Algorithm "NFFT"):          f_j   ~ sum_{k in I_N} fhat_k e^{-2 pi i k.x_j},
+ *                                        computed as f = B F D fhat,
+ *   adjoint (Algorithm "adjoint NFFT"):  hhat_k ~ sum_j f_j e^{+2 pi i k.x_j},
+ *                                        computed as hhat = D^H F^H B^H f,
+ *
+ * with nodes x_j on the torus T^d = [-1/2, 1/2)^d, the index set
+ * I_N = { k : -N_t/2 <= k_t <= N_t/2 - 1 } (Section 2, eq. index_set), an oversampled FFT grid
+ * of size n = sigma N and a Kaiser-Bessel window truncated to |n_t x_t - l_t| <= m
+ * (Section 2, eq. window_cutoff and eq. Inm). D divides by the window's Fourier coefficients and
+ * zero-pads, F is the d-variate FFT of size n, B interpolates the grid at the nodes with the
+ * window, and B^H spreads node values onto the grid (the transposed index set of Section 2).
+ *
+ * Every call that computes runs hand-written CUDA kernels (sm_103a) on the plan's stream and
+ * returns without waiting for them. There is no CPU fallback: a call either enqueues GPU work
+ * or returns an error code.
+ *
+ * Memory and layout (all device pointers unless the function name ends in _host):
+ *   - Complex values are interleaved (re, im): float2 for NFFT_FP32, double2 for NFFT_FP64.
+ *   - fhat / hhat: |I_N| complex values, row-major over (k_0, ..., k_{d-1}) with axis t at
+ *     position k_t + N_t/2 (the centred order of the paper's Julia example, Section 4.2,
+ *     extended row-major to d > 1).
+ *   - x: M x d reals of the plan's precision, row-major (node j, coordinate t). Any finite real
+ *     is accepted; it is taken modulo 1 (the torus).
+ *   - f: M complex values in the caller's node order.
+ *   - Pointers must be aligned to one complex value (8 bytes FP32, 16 bytes FP64); the caller
+ *     owns all of them. No input array is modified.
+ *
+ * Errors: every function returns an nfft_status_code. Argument errors are detected on the host
+ * before anything is enqueued. Errors found on the GPU (a node that is NaN or infinite) are
+ * recorded in a device-side status word and reported by nfft_status() (which waits for the
+ * stream).
+ *
+ * Threads: a plan is not thread-safe; distinct plans may be used from distinct threads.
+ */
+#ifndef GBNFFT_H
+#define GBNFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbnfft_plan *nfft_plan;
+
+/* Precision of x, fhat, f and the internal grid. */
+enum nfft_dtype { NFFT_FP32 = 0, NFFT_FP64 = 1 };
+
+enum nfft_status_code {
+    NFFT_OK = 0,
+    NFFT_EINVAL = 1,      /* bad argument: dimension, size, null or misaligned pointer */
+    NFFT_ENOMEM = 2,      /* a device allocation failed, or the workspace given is too small */
+    NFFT_ECUDA = 3,       /* a CUDA runtime call failed */
+    NFFT_ENOTREADY = 4,   /* a transform was requested before nfft_set_nodes */
+    NFFT_EBADNODE = 5,    /* a node coordinate was NaN, infinite or too large (|n x| >= 2^52) */
+    NFFT_ETIMEOUT = 6,    /* reserved: a bounded device-side wait gave up */
+    NFFT_EUNSUPPORTED = 7 /* valid for the paper's method but not built here (see below) */
+};
+
+/* Plan creation: Section 3.1, Table tab:params (N, M, n, m) plus the precision.
+ *   d      1, 2 or 3.
+ *   N      d even bandwidths, N_t >= 2 (Section 2, eq. index_set: N in 2 N^d).
+ *   M      number of nodes, M >= 0 and M < 2^31.
+ *   n      d FFT lengths, or NULL for the paper's default n_t = 2^(ceil(log2 N_t) + 1)
+ *          (Section 2, after eq. gl). Each n_t must be even and > N_t (Section 3.1); this
+ *          library builds power-of-two n_t only (NFFT_EUNSUPPORTED otherwise), with
+ *          n_t <= 16384 (FP32) / 8192 (FP64) and |I_n| < 2^31.
+ *   m      window cutoff, 1 <= m <= 8, with 2m + 2 <= n_t; m <= 0 selects the paper's default 8
+ *          (Section 3.1).
+ *   dtype  NFFT_FP32 or NFFT_FP64.
+ * The plan binds the calling thread's current CUDA device and the legacy default stream; it
+ * owns small device tables (window factors, twiddles, a status word), allocated here. */
+int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const int64_t *n,
+                     int m, int dtype);
+
+/* Release the plan, its tables and any workspace it allocated itself. NULL is accepted. */
+int nfft_destroy(nfft_plan plan);
+
+/* Make every later call enqueue on this CUDA stream (a cudaStream_t; NULL = legacy default). */
+int nfft_set_stream(nfft_plan plan, void *cuda_stream);
+
+/* Device workspace the plan needs: oversampled grids, sorted node records, bin tables. */
+int nfft_workspace_size(nfft_plan plan, size_t *bytes);
+
+/* Hand the plan a caller-owned device workspace of at least nfft_workspace_size() bytes,
+ * aligned to 256 bytes. It must stay valid until the plan is destroyed or given another one.
+ * Without this call, nfft_set_nodes allocates the workspace itself (owned by the plan). */
+int nfft_set_workspace(nfft_plan plan, void *dev_ptr, size_t bytes);
+
+/* Precomputation for a node set (the paper's "precomputation" of Section 4.2, NFFT_SORT_NODES
+ * of Table tab:nfftflags): for every node, the grid cell floor(n_t x_t) and the offset inside
+ * it (computed in FP64 for both precisions), then a counting sort of the nodes into tiles of
+ * the grid. x (M x d, device) may be freed once the stream has passed this call. */
+int nfft_set_nodes(nfft_plan plan, const void *x);
+
+/* Forward NFFT, Algorithm "NFFT": f = B F D fhat. fhat: |I_N| complex, f: M complex. */
+int nfft_trafo(nfft_plan plan, const void *fhat, void *f);
+
+/* Adjoint NFFT, Algorithm "adjoint NFFT": hhat = D^H F^H B^H f. f: M complex,
+ * hhat: |I_N| complex. */
+int nfft_adjoint(nfft_plan plan, const void *f, void *fhat);
+
+/* Node gradient (derivative of the approximation s of Section 2, eq. s_approx, with respect
+ * to the node coordinates): gx[j*d + t] = Re( conj(w_j) * d s_c / d x_t (x_j) ), where s_c is
+ * the NFFT approximation built from the coefficients c (|I_N| complex) and w (M complex) is one
+ * weight per node. For a real loss L of f = NFFT(fhat, x) (PyTorch's convention for complex
+ * gradients), dL/dx = nfft_grad_x(c = fhat, w = dL/df); for hhat = NFFT^H(f, x),
+ * dL/dx = nfft_grad_x(c = dL/dhhat, w = f). gx: M x d reals of the plan's precision. */
+int nfft_grad_x(nfft_plan plan, const void *coef, const void *w, void *gx);
+
+/* Host-buffer versions: copy the inputs from host memory to device buffers owned by the plan
+ * (allocated on first use), run the transform, copy the result back, and wait for the stream.
+ * Pinned host memory makes the copies asynchronous and faster; pageable memory also works. */
+int nfft_set_nodes_host(nfft_plan plan, const void *x_host);
+int nfft_trafo_host(nfft_plan plan, const void *fhat_host, void *f_host);
+int nfft_adjoint_host(nfft_plan plan, const void *f_host, void *fhat_host);
+
+/* Wait for the plan's stream and return the first error any kernel recorded since the last
+ * call (NFFT_OK if none), then clear it. A CUDA error seen while waiting gives NFFT_ECUDA. */
+int nfft_status(nfft_plan plan);
+
+/* Plan parameters after defaults: d, N[3], n[3], M, m, dtype, and the tile (bin) size used to
+ * sort the nodes. Unused trailing entries are 0. */
+typedef struct nfft_info {
+    int d;
+    int m;
+    int dtype;
+    int64_t M;
+    int64_t N[3];
+    int64_t n[3];
+    int64_t bin[3];
+    size_t workspace_bytes;
+} nfft_info;
+int nfft_get_info(nfft_plan plan, nfft_info *info);
+
+/* Per-stage timing with CUDA events recorded on the plan's stream. While enabled, every call
+ * records one event pair around each stage it runs; nfft_profile_read waits for the stream,
+ * adds up the elapsed milliseconds per stage into ms[stage] (and the number of timed calls into
+ * count[stage] when count is not NULL) for stages < nstages, and forgets the recorded pairs.
+ * nfft_profile(plan, 0) stops recording; enabling also forgets earlier pairs. */
+enum nfft_stage {
+    NFFT_STAGE_SET_NODES = 0,   /* node cell/offset + counting sort + subproblem list */
+    NFFT_STAGE_FFT_FORWARD = 1, /* D and F: the pruned forward FFT passes */
+    NFFT_STAGE_INTERP = 2,      /* B: window interpolation */
+    NFFT_STAGE_ZERO_GRID = 3,   /* clearing the grid before spreading */
+    NFFT_STAGE_SPREAD = 4,      /* B^H: tiled spreading */
+    NFFT_STAGE_FFT_ADJOINT = 5, /* F^H and D^H: the pruned inverse FFT passes */
+    NFFT_STAGE_GRAD = 6,        /* node-gradient interpolation */
+    NFFT_NUM_STAGES = 7
+};
+int nfft_profile(nfft_plan plan, int enable);
+int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
+
+/* Static description of an error code. */
+const char *nfft_strerror(int code);
+
+/* Make `device` the calling thread's current CUDA device for this library (the device that the
+ * next nfft_plan_create binds). */
+int nfft_use_device(int device);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBNFFT_H */

@@ -1,0 +1,155 @@
+// Internal declarations shared by the gbnfft CUDA translation units.
+//
+// Notation follows Section 2 of the paper: d dimensions, bandwidths N_t, grid sizes n_t,
+// window cutoff m, M nodes x_j. A node's grid position is n_t x_t = base_t + frac_t with
+// base_t = floor(n_t x_t) and frac_t in [0, 1]; its taps on axis t are the grid points
+// l_t = base_t - m + i, i = 0..2m, of which i = 0 is inside the closed support |n x - l| <= m
+// (eq. Inm) only when frac_t == 0.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gbnfft.h"
+
+namespace gbnfft {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxM = 8;           // window cutoffs 1..8 are instantiated
+constexpr int kMaxSub = 1024;      // nodes per spreading subproblem (one CTA tile)
+
+// Per-axis constants of the normalised window psibar(t) = psi(t) / psi(0), in grid units:
+//   psibar(t) = kscale * sinh(b u) / u,  u = sqrt(m^2 - t^2),  kscale = m / sinh(b m).
+// psi(0) is folded into the deconvolution factors, which keeps FP32 values in range at any m.
+struct AxisWin {
+    double b;       // shape parameter b = pi (2 - 1/sigma)
+    double kscale;  // m / sinh(b m)
+};
+
+// Geometry passed by value to every kernel.
+struct Geom {
+    int d;
+    int m;
+    int n[kMaxDim];        // grid size per axis (power of two)
+    int nlog[kMaxDim];     // log2 n
+    int N[kMaxDim];        // bandwidth per axis
+    int bs[kMaxDim];       // bin (tile) size per axis, power of two
+    int bslog[kMaxDim];
+    int nb[kMaxDim];       // bins per axis
+    AxisWin win[kMaxDim];
+};
+
+// A spreading subproblem: up to kMaxSub consecutive sorted nodes of one bin.
+struct SubProb {
+    int bin;
+    int start;
+    int count;
+    int pad;
+};
+
+// Node record in sorted order. FP32: {cell bits, frac0, frac1, frac2}; FP64: cell in the
+// first 8 bytes, then frac0..2. cell is the row-major index of (base_t mod n_t).
+struct alignas(16) RecF {
+    int cell;
+    float fr[3];
+};
+struct alignas(16) RecD {
+    int cell;
+    int pad;
+    double fr[3];
+};
+template <typename T> struct RecOf;
+template <> struct RecOf<float> { using type = RecF; };
+template <> struct RecOf<double> { using type = RecD; };
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+// Device status word values (a subset of nfft_status_code).
+constexpr int kStatusOk = 0;
+
+// ------------------------------------------------------------------------------------------
+// Launchers (each enqueues on `stream`, returns cudaError_t of the launch)
+// ------------------------------------------------------------------------------------------
+
+// set_nodes: cell / bin / rank per node, then counting sort into bins, then subproblems.
+template <typename T>
+cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *bin_count, int2 *bin_rank,
+                            int *status, cudaStream_t stream);
+cudaError_t launch_bin_scan(const int *bin_count, int *bin_start, int *sub_start, int *nsub_total,
+                            int nbins, cudaStream_t stream);
+template <typename T>
+cudaError_t launch_node_scatter(const Geom &g, const T *x, int64_t M, const int2 *bin_rank,
+                                const int *bin_start, typename RecOf<T>::type *rec, int *perm,
+                                cudaStream_t stream);
+cudaError_t launch_fill_subprobs(const int *bin_count, const int *bin_start, const int *sub_start,
+                                 SubProb *subs, int nbins, cudaStream_t stream);
+
+// One axis pass of the pruned d-variate FFT.
+//   in  : [outer][Lin][inner]   out : [outer][Lout][inner]
+//   pad  (forward, D fused): Lin = N_t, Lout = L = n_t; input index i (k = i - N_t/2) lands at
+//        FFT position k mod n_t after multiplication by deconv[i]; other positions are zero.
+//   crop (adjoint, D^H fused): Lin = L = n_t, Lout = N_t; output i takes FFT position
+//        (i - N_t/2) mod n_t times deconv[i].
+//   sign: -1 forward e^{-2 pi i kl/L}, +1 inverse.
+template <typename T>
+cudaError_t launch_fft_axis(const typename Cplx<T>::type *in, typename Cplx<T>::type *out,
+                            int64_t outer, int64_t inner, int L, int Nt, bool pad_mode, int sign,
+                            const typename Cplx<T>::type *twiddle, const double *deconv,
+                            cudaStream_t stream);
+
+// B: f[perm[s]] = sum over taps of grid * prod psibar.
+template <typename T>
+cudaError_t launch_interp(const Geom &g, const typename Cplx<T>::type *grid,
+                          const typename RecOf<T>::type *rec, const int *perm, int64_t M,
+                          typename Cplx<T>::type *f, cudaStream_t stream);
+
+// B^H: grid += spread of f over subproblems (grid must be zeroed first).
+template <typename T>
+cudaError_t launch_spread(const Geom &g, const typename Cplx<T>::type *f,
+                          const typename RecOf<T>::type *rec, const int *perm,
+                          const SubProb *subs, const int *nsub_total, int max_subs,
+                          typename Cplx<T>::type *grid, cudaStream_t stream);
+
+// Node gradient: gx[perm[s]*d + t] = Re(conj(w[perm[s]]) * n_t * sum grid * dpsibar_t * ...).
+template <typename T>
+cudaError_t launch_grad(const Geom &g, const typename Cplx<T>::type *grid,
+                        const typename RecOf<T>::type *rec, const int *perm, int64_t M,
+                        const typename Cplx<T>::type *w, T *gx, cudaStream_t stream);
+
+// Dispatch on the window cutoff m (kernels are instantiated for m = 1..kMaxM).
+#define GBNFFT_DISPATCH_M(FN, T, D, ...)                                                          \
+    switch (g.m) {                                                                               \
+    case 1: return FN<T, D, 1>(__VA_ARGS__);                                                     \
+    case 2: return FN<T, D, 2>(__VA_ARGS__);                                                     \
+    case 3: return FN<T, D, 3>(__VA_ARGS__);                                                     \
+    case 4: return FN<T, D, 4>(__VA_ARGS__);                                                     \
+    case 5: return FN<T, D, 5>(__VA_ARGS__);                                                     \
+    case 6: return FN<T, D, 6>(__VA_ARGS__);                                                     \
+    case 7: return FN<T, D, 7>(__VA_ARGS__);                                                     \
+    case 8: return FN<T, D, 8>(__VA_ARGS__);                                                     \
+    default: return cudaErrorInvalidValue;                                                       \
+    }
+
+namespace detail {
+// Per-dimension launchers, each instantiated (for float and double) in its own translation
+// unit k_<kernel>_<dtype>_d<D>.cu so that the library compiles in parallel.
+template <typename T, int D>
+cudaError_t interp_d(const Geom &g, const typename Cplx<T>::type *grid,
+                     const typename RecOf<T>::type *rec, const int *perm, int64_t M,
+                     typename Cplx<T>::type *f, cudaStream_t stream);
+template <typename T, int D>
+cudaError_t grad_d(const Geom &g, const typename Cplx<T>::type *grid,
+                   const typename RecOf<T>::type *rec, const int *perm, int64_t M,
+                   const typename Cplx<T>::type *w, T *gx, cudaStream_t stream);
+template <typename T, int D>
+cudaError_t spread_d(const Geom &g, const typename Cplx<T>::type *f,
+                     const typename RecOf<T>::type *rec, const int *perm, const SubProb *subs,
+                     const int *nsub_total, int max_subs, typename Cplx<T>::type *grid,
+                     cudaStream_t stream);
+}  // namespace detail
+
+int num_sms();
+
+}  // namespace gbnfft

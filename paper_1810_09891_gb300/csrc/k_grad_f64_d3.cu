@@ -1,0 +1,8 @@
+// Instantiation unit: grad kernels, double, d = 3, window cutoffs m = 1..kMaxM.
+#include "interp_impl.cuh"
+
+namespace gbnfft {
+namespace detail {
+template cudaError_t grad_d<double, 3>(const Geom &, const double2 *, const RecD *, const int *, int64_t, const double2 *, double *, cudaStream_t);
+}  // namespace detail
+}  // namespace gbnfft

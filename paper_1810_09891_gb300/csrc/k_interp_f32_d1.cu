@@ -1,0 +1,8 @@
+// Instantiation unit: interp kernels, float, d = 1, window cutoffs m = 1..kMaxM.
+#include "interp_impl.cuh"
+
+namespace gbnfft {
+namespace detail {
+template cudaError_t interp_d<float, 1>(const Geom &, const float2 *, const RecF *, const int *, int64_t, float2 *, cudaStream_t);
+}  // namespace detail
+}  // namespace gbnfft

@@ -1,0 +1,191 @@
+// Node precomputation (set_nodes): grid cell and offset of every node, then a counting sort of
+// the nodes into bins (tiles of the oversampled grid), then the list of spreading subproblems.
+// This is the GPU form of the paper's node sorting (Section 3.1, Table tab:nfftflags,
+// NFFT_SORT_NODES): nodes that share a tile are processed together by the interpolation and
+// spreading kernels.
+#include "gbnfft_internal.cuh"
+
+namespace gbnfft {
+
+// |n x| must stay below 2^52 for floor() and the offset to be exact in FP64.
+static constexpr double kMaxAbsNx = 4503599627370496.0;
+
+// Grid position of coordinate t of a node: base = floor(n x) (as an integer), frac = n x - base.
+// frac is computed in FP64 for both precisions. Returns false for NaN, inf or |n x| >= 2^52.
+template <typename T>
+__device__ __forceinline__ bool node_pos(T xt, int n, long long &base, double &frac)
+{
+    const double tt = (double)n * (double)xt;
+    if (!(fabs(tt) < kMaxAbsNx)) {
+        base = 0;
+        frac = 0.5;
+        return false;
+    }
+    const double bf = floor(tt);
+    base = (long long)bf;
+    frac = tt - bf;  // in [0, 1]; equals 1 only when tt is a tiny negative number
+    return true;
+}
+
+template <typename T>
+__global__ void node_bin_kernel(Geom g, const T *__restrict__ x, int M, int *__restrict__ bin_count,
+                                int2 *__restrict__ bin_rank, int *__restrict__ status)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    int bin = 0;
+    bool ok = true;
+    for (int t = 0; t < g.d; t++) {
+        long long base;
+        double frac;
+        ok &= node_pos<T>(x[(long long)j * g.d + t], g.n[t], base, frac);
+        const int b = (int)(base & (long long)(g.n[t] - 1));  // base mod n (two's complement)
+        bin = bin * g.nb[t] + (b >> g.bslog[t]);
+    }
+    if (!ok) atomicCAS(status, kStatusOk, (int)NFFT_EBADNODE);
+    const int rank = atomicAdd(&bin_count[bin], 1);
+    bin_rank[j] = make_int2(bin, rank);
+}
+
+template <typename T>
+cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *bin_count, int2 *bin_rank,
+                            int *status, cudaStream_t stream)
+{
+    if (M == 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (int)((M + threads - 1) / threads);
+    node_bin_kernel<T><<<blocks, threads, 0, stream>>>(g, x, (int)M, bin_count, bin_rank, status);
+    return cudaGetLastError();
+}
+
+// Exclusive scans of the bin counts and of the subproblem counts ceil(count / kMaxSub), in one
+// CTA of 1024 threads (each thread owns a contiguous chunk of bins).
+__global__ void __launch_bounds__(1024)
+    bin_scan_kernel(const int *__restrict__ count, int *__restrict__ start,
+                    int *__restrict__ sub_start, int *__restrict__ nsub_total, int nbins)
+{
+    __shared__ int s_a[1024];
+    __shared__ int s_b[1024];
+    const int tid = threadIdx.x;
+    const int chunk = (nbins + 1023) / 1024;
+    const int lo = min(nbins, tid * chunk), hi = min(nbins, lo + chunk);
+    int a = 0, b = 0;
+    for (int i = lo; i < hi; i++) {
+        const int c = count[i];
+        a += c;
+        b += (c + kMaxSub - 1) / kMaxSub;
+    }
+    s_a[tid] = a;
+    s_b[tid] = b;
+    __syncthreads();
+    // Hillis-Steele inclusive scan over the 1024 partial sums
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int va = tid >= off ? s_a[tid - off] : 0;
+        const int vb = tid >= off ? s_b[tid - off] : 0;
+        __syncthreads();
+        s_a[tid] += va;
+        s_b[tid] += vb;
+        __syncthreads();
+    }
+    int ra = s_a[tid] - a, rb = s_b[tid] - b;  // exclusive prefix of this chunk
+    for (int i = lo; i < hi; i++) {
+        const int c = count[i];
+        start[i] = ra;
+        sub_start[i] = rb;
+        ra += c;
+        rb += (c + kMaxSub - 1) / kMaxSub;
+    }
+    if (tid == 1023) nsub_total[0] = s_b[1023];
+}
+
+cudaError_t launch_bin_scan(const int *bin_count, int *bin_start, int *sub_start, int *nsub_total,
+                            int nbins, cudaStream_t stream)
+{
+    bin_scan_kernel<<<1, 1024, 0, stream>>>(bin_count, bin_start, sub_start, nsub_total, nbins);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void node_scatter_kernel(Geom g, const T *__restrict__ x, int M,
+                                    const int2 *__restrict__ bin_rank,
+                                    const int *__restrict__ bin_start,
+                                    typename RecOf<T>::type *__restrict__ rec, int *__restrict__ perm)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    typename RecOf<T>::type r;
+    r.cell = 0;
+    for (int t = 0; t < kMaxDim; t++) r.fr[t] = (T)0;
+    for (int t = 0; t < g.d; t++) {
+        long long base;
+        double frac;
+        node_pos<T>(x[(long long)j * g.d + t], g.n[t], base, frac);
+        const int b = (int)(base & (long long)(g.n[t] - 1));
+        r.cell = (r.cell << g.nlog[t]) | b;
+        r.fr[t] = (T)frac;
+    }
+    const int2 br = bin_rank[j];
+    const int pos = bin_start[br.x] + br.y;
+    rec[pos] = r;
+    perm[pos] = j;
+}
+
+template <typename T>
+cudaError_t launch_node_scatter(const Geom &g, const T *x, int64_t M, const int2 *bin_rank,
+                                const int *bin_start, typename RecOf<T>::type *rec, int *perm,
+                                cudaStream_t stream)
+{
+    if (M == 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (int)((M + threads - 1) / threads);
+    node_scatter_kernel<T><<<blocks, threads, 0, stream>>>(g, x, (int)M, bin_rank, bin_start, rec,
+                                                           perm);
+    return cudaGetLastError();
+}
+
+__global__ void fill_subprobs_kernel(const int *__restrict__ count, const int *__restrict__ start,
+                                     const int *__restrict__ sub_start, SubProb *__restrict__ subs,
+                                     int nbins)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int c = count[b];
+    const int s0 = sub_start[b];
+    for (int k = 0; k * kMaxSub < c; k++) {
+        SubProb p;
+        p.bin = b;
+        p.start = start[b] + k * kMaxSub;
+        p.count = min(kMaxSub, c - k * kMaxSub);
+        p.pad = 0;
+        subs[s0 + k] = p;
+    }
+}
+
+cudaError_t launch_fill_subprobs(const int *bin_count, const int *bin_start, const int *sub_start,
+                                 SubProb *subs, int nbins, cudaStream_t stream)
+{
+    const int threads = 256;
+    fill_subprobs_kernel<<<(nbins + threads - 1) / threads, threads, 0, stream>>>(
+        bin_count, bin_start, sub_start, subs, nbins);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_node_bin<float>(const Geom &, const float *, int64_t, int *, int2 *,
+                                            int *, cudaStream_t);
+template cudaError_t launch_node_bin<double>(const Geom &, const double *, int64_t, int *, int2 *,
+                                             int *, cudaStream_t);
+template cudaError_t launch_node_scatter<float>(const Geom &, const float *, int64_t, const int2 *,
+                                                const int *, RecF *, int *, cudaStream_t);
+template cudaError_t launch_node_scatter<double>(const Geom &, const double *, int64_t,
+                                                 const int2 *, const int *, RecD *, int *,
+                                                 cudaStream_t);
+
+int num_sms()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return v;
+}
+
+}  // namespace gbnfft

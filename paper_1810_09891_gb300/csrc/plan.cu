@@ -1,0 +1,765 @@
+// C ABI of gbnfft (declared in include/gbnfft.h): plan creation and validation, host-side
+// tables (deconvolution factors and FFT twiddles, both in FP64), workspace layout, and the
+// orchestration of the kernels for set_nodes, the forward NFFT (Algorithm "NFFT": D, F, B),
+// the adjoint NFFT (Algorithm "adjoint NFFT": B^H, F^H, D^H) and the node gradient.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "gbnfft_internal.cuh"
+
+using namespace gbnfft;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int ilog2(int64_t v)
+{
+    int r = 0;
+    while ((int64_t(1) << r) < v) r++;
+    return r;
+}
+
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Modified Bessel function I0 by its power series sum (z^2/4)^j / (j!)^2 (terms all positive).
+double bessel_i0(double z)
+{
+    const double q = 0.25 * z * z;
+    double term = 1.0, sum = 1.0;
+    for (int j = 1; j < 1000; j++) {
+        term *= q / (double(j) * double(j));
+        sum += term;
+        if (term <= 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+// e^{-2 pi i j / L} with the angle reduced to the first octant (exact symmetry) before calling
+// cos / sin, so that the table is correctly rounded up to the host libm's accuracy.
+void twiddle(int64_t j, int64_t L, double *re, double *im)
+{
+    j %= L;
+    const int64_t q = (4 * j) / L;          // quadrant
+    const int64_t r = 4 * j - q * L;        // angle inside the quadrant, in units of (pi/2)/L
+    double cr, sr;
+    if (2 * r <= L) {
+        const double th = 0.5 * kPi * double(r) / double(L);
+        cr = std::cos(th);
+        sr = std::sin(th);
+    } else {
+        const double th = 0.5 * kPi * double(L - r) / double(L);
+        cr = std::sin(th);
+        sr = std::cos(th);
+    }
+    double c, s;  // rotate (cr, sr) by q quarter turns
+    switch (q & 3) {
+    case 0: c = cr; s = sr; break;
+    case 1: c = -sr; s = cr; break;
+    case 2: c = -cr; s = -sr; break;
+    default: c = sr; s = -cr; break;
+    }
+    *re = c;
+    *im = -s;
+}
+
+struct Region {
+    size_t off = 0, bytes = 0;
+};
+
+}  // namespace
+
+struct gbnfft_plan {
+    int device = 0;
+    int d = 0, m = 0, dtype = 0;
+    int64_t N[3] = {0, 0, 0}, n[3] = {0, 0, 0}, M = 0;
+    Geom geom{};
+    cudaStream_t stream = nullptr;
+    size_t csize = 0;  // bytes per complex value
+    size_t rsize = 0;  // bytes per real value
+    int64_t G = 0;     // |I_n|
+    int64_t NN = 0;    // |I_N|
+    int64_t Bsz = 0;   // complex values of the second FFT buffer
+    int nbins = 0;
+    int max_subs = 0;
+    // plan-owned device tables
+    void *tables = nullptr;
+    double *deconv[3] = {nullptr, nullptr, nullptr};
+    void *tw[3] = {nullptr, nullptr, nullptr};
+    int *d_status = nullptr;
+    // workspace
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    Region gA, gB, rec, perm, binrank, bincount, binstart, substart, nsub, subs;
+    size_t ws_need = 0;
+    bool nodes_ready = false;
+    // host-call staging (plan-owned)
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    // per-stage CUDA-event timing (nfft_profile)
+    struct ProfPair {
+        cudaEvent_t a, b;
+        int stage;
+    };
+    bool prof_on = false;
+    std::vector<ProfPair> prof;
+    size_t prof_used = 0;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) return NFFT_ENOMEM;
+    return e == cudaSuccess ? NFFT_OK : NFFT_ECUDA;
+}
+
+#define GB_CHECK(expr)                                                                            \
+    do {                                                                                          \
+        cudaError_t _e = (expr);                                                                  \
+        if (_e != cudaSuccess) return cuda_fail(_e);                                              \
+    } while (0)
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+void layout_workspace(gbnfft_plan *p)
+{
+    size_t off = 0;
+    auto put = [&](Region &r, size_t bytes) {
+        off = align_up(off, 256);
+        r.off = off;
+        r.bytes = bytes;
+        off += bytes;
+    };
+    const size_t recsz = p->dtype == NFFT_FP32 ? sizeof(RecF) : sizeof(RecD);
+    put(p->gA, size_t(p->G) * p->csize);
+    put(p->gB, size_t(p->Bsz) * p->csize);
+    put(p->rec, size_t(p->M) * recsz);
+    put(p->perm, size_t(p->M) * sizeof(int));
+    put(p->binrank, size_t(p->M) * sizeof(int2));
+    put(p->bincount, size_t(p->nbins) * sizeof(int));
+    put(p->binstart, size_t(p->nbins) * sizeof(int));
+    put(p->substart, size_t(p->nbins) * sizeof(int));
+    put(p->nsub, 16);
+    put(p->subs, size_t(p->max_subs) * sizeof(SubProb));
+    p->ws_need = align_up(off, 256);
+}
+
+template <typename R> R *at(gbnfft_plan *p, const Region &r)
+{
+    return reinterpret_cast<R *>(p->ws + r.off);
+}
+
+int ensure_workspace(gbnfft_plan *p)
+{
+    if (p->ws) return NFFT_OK;
+    void *ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, p->ws_need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return NFFT_ENOMEM;
+    }
+    p->ws = static_cast<char *>(ptr);
+    p->ws_bytes = p->ws_need;
+    p->ws_owned = true;
+    return NFFT_OK;
+}
+
+// Stage timing: a pair of events recorded on the plan's stream around one stage.
+int prof_begin(gbnfft_plan *p, int stage)
+{
+    if (!p->prof_on) return -1;
+    if (p->prof_used == p->prof.size()) {
+        gbnfft_plan::ProfPair pp{};
+        if (cudaEventCreate(&pp.a) != cudaSuccess) return -1;
+        if (cudaEventCreate(&pp.b) != cudaSuccess) {
+            cudaEventDestroy(pp.a);
+            return -1;
+        }
+        p->prof.push_back(pp);
+    }
+    const int idx = (int)p->prof_used++;
+    p->prof[idx].stage = stage;
+    cudaEventRecord(p->prof[idx].a, p->stream);
+    return idx;
+}
+
+void prof_end(gbnfft_plan *p, int idx)
+{
+    if (idx >= 0) cudaEventRecord(p->prof[idx].b, p->stream);
+}
+
+struct ProfScope {
+    gbnfft_plan *p;
+    int idx;
+    ProfScope(gbnfft_plan *pp, int stage) : p(pp), idx(prof_begin(pp, stage)) {}
+    ~ProfScope() { prof_end(p, idx); }
+};
+
+// Forward FFT passes with D fused: fhat (centred, |I_N|) -> gA (|I_n|, natural order).
+template <typename T> int forward_grid(gbnfft_plan *p, const void *fhat)
+{
+    using C = typename Cplx<T>::type;
+    const C *in = static_cast<const C *>(fhat);
+    C *A = at<C>(p, p->gA), *B = at<C>(p, p->gB);
+    const int64_t *N = p->N, *n = p->n;
+    auto tw = [&](int t) { return static_cast<const C *>(p->tw[t]); };
+    cudaStream_t s = p->stream;
+    if (p->d == 1) {
+        GB_CHECK(launch_fft_axis<T>(in, A, 1, 1, (int)n[0], (int)N[0], true, -1, tw(0),
+                                    p->deconv[0], s));
+    } else if (p->d == 2) {
+        GB_CHECK(launch_fft_axis<T>(in, B, N[0], 1, (int)n[1], (int)N[1], true, -1, tw(1),
+                                    p->deconv[1], s));
+        GB_CHECK(launch_fft_axis<T>(B, A, 1, n[1], (int)n[0], (int)N[0], true, -1, tw(0),
+                                    p->deconv[0], s));
+    } else {
+        GB_CHECK(launch_fft_axis<T>(in, A, N[0] * N[1], 1, (int)n[2], (int)N[2], true, -1, tw(2),
+                                    p->deconv[2], s));
+        GB_CHECK(launch_fft_axis<T>(A, B, N[0], n[2], (int)n[1], (int)N[1], true, -1, tw(1),
+                                    p->deconv[1], s));
+        GB_CHECK(launch_fft_axis<T>(B, A, 1, n[1] * n[2], (int)n[0], (int)N[0], true, -1, tw(0),
+                                    p->deconv[0], s));
+    }
+    return NFFT_OK;
+}
+
+// Inverse FFT passes with D^H fused: gA (|I_n|) -> fhat (|I_N|). gA is overwritten.
+template <typename T> int adjoint_grid(gbnfft_plan *p, void *fhat)
+{
+    using C = typename Cplx<T>::type;
+    C *out = static_cast<C *>(fhat);
+    C *A = at<C>(p, p->gA), *B = at<C>(p, p->gB);
+    const int64_t *N = p->N, *n = p->n;
+    auto tw = [&](int t) { return static_cast<const C *>(p->tw[t]); };
+    cudaStream_t s = p->stream;
+    if (p->d == 1) {
+        GB_CHECK(launch_fft_axis<T>(A, out, 1, 1, (int)n[0], (int)N[0], false, +1, tw(0),
+                                    p->deconv[0], s));
+    } else if (p->d == 2) {
+        GB_CHECK(launch_fft_axis<T>(A, B, 1, n[1], (int)n[0], (int)N[0], false, +1, tw(0),
+                                    p->deconv[0], s));
+        GB_CHECK(launch_fft_axis<T>(B, out, N[0], 1, (int)n[1], (int)N[1], false, +1, tw(1),
+                                    p->deconv[1], s));
+    } else {
+        GB_CHECK(launch_fft_axis<T>(A, B, 1, n[1] * n[2], (int)n[0], (int)N[0], false, +1, tw(0),
+                                    p->deconv[0], s));
+        GB_CHECK(launch_fft_axis<T>(B, A, N[0], n[2], (int)n[1], (int)N[1], false, +1, tw(1),
+                                    p->deconv[1], s));
+        GB_CHECK(launch_fft_axis<T>(A, out, N[0] * N[1], 1, (int)n[2], (int)N[2], false, +1,
+                                    tw(2), p->deconv[2], s));
+    }
+    return NFFT_OK;
+}
+
+template <typename T> int do_set_nodes(gbnfft_plan *p, const void *x)
+{
+    using Rec = typename RecOf<T>::type;
+    ProfScope ps(p, NFFT_STAGE_SET_NODES);
+    cudaStream_t s = p->stream;
+    int *count = at<int>(p, p->bincount);
+    GB_CHECK(cudaMemsetAsync(count, 0, size_t(p->nbins) * sizeof(int), s));
+    GB_CHECK(launch_node_bin<T>(p->geom, static_cast<const T *>(x), p->M, count,
+                                at<int2>(p, p->binrank), p->d_status, s));
+    GB_CHECK(launch_bin_scan(count, at<int>(p, p->binstart), at<int>(p, p->substart),
+                             at<int>(p, p->nsub), p->nbins, s));
+    GB_CHECK(launch_node_scatter<T>(p->geom, static_cast<const T *>(x), p->M,
+                                    at<int2>(p, p->binrank), at<int>(p, p->binstart),
+                                    at<Rec>(p, p->rec), at<int>(p, p->perm), s));
+    GB_CHECK(launch_fill_subprobs(count, at<int>(p, p->binstart), at<int>(p, p->substart),
+                                  at<SubProb>(p, p->subs), p->nbins, s));
+    return NFFT_OK;
+}
+
+template <typename T> int do_trafo(gbnfft_plan *p, const void *fhat, void *f)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    int rc;
+    {
+        ProfScope ps(p, NFFT_STAGE_FFT_FORWARD);
+        rc = forward_grid<T>(p, fhat);
+    }
+    if (rc) return rc;
+    ProfScope ps(p, NFFT_STAGE_INTERP);
+    GB_CHECK(launch_interp<T>(p->geom, at<C>(p, p->gA), at<Rec>(p, p->rec), at<int>(p, p->perm),
+                              p->M, static_cast<C *>(f), p->stream));
+    return NFFT_OK;
+}
+
+template <typename T> int do_adjoint(gbnfft_plan *p, const void *f, void *fhat)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    {
+        ProfScope ps(p, NFFT_STAGE_ZERO_GRID);
+        GB_CHECK(cudaMemsetAsync(at<C>(p, p->gA), 0, size_t(p->G) * p->csize, p->stream));
+    }
+    {
+        ProfScope ps(p, NFFT_STAGE_SPREAD);
+        GB_CHECK(launch_spread<T>(p->geom, static_cast<const C *>(f), at<Rec>(p, p->rec),
+                                  at<int>(p, p->perm), at<SubProb>(p, p->subs),
+                                  at<int>(p, p->nsub), p->max_subs, at<C>(p, p->gA), p->stream));
+    }
+    ProfScope ps(p, NFFT_STAGE_FFT_ADJOINT);
+    return adjoint_grid<T>(p, fhat);
+}
+
+template <typename T> int do_grad(gbnfft_plan *p, const void *coef, const void *w, void *gx)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    int rc;
+    {
+        ProfScope ps(p, NFFT_STAGE_FFT_FORWARD);
+        rc = forward_grid<T>(p, coef);
+    }
+    if (rc) return rc;
+    ProfScope ps(p, NFFT_STAGE_GRAD);
+    GB_CHECK(launch_grad<T>(p->geom, at<C>(p, p->gA), at<Rec>(p, p->rec), at<int>(p, p->perm),
+                            p->M, static_cast<const C *>(w), static_cast<T *>(gx), p->stream));
+    return NFFT_OK;
+}
+
+int set_device(gbnfft_plan *p)
+{
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return NFFT_ECUDA;
+    if (cur != p->device && cudaSetDevice(p->device) != cudaSuccess) return NFFT_ECUDA;
+    return NFFT_OK;
+}
+
+int check_dev_ptr(const gbnfft_plan *p, const void *ptr, int64_t count)
+{
+    if (count == 0) return NFFT_OK;
+    if (!ptr) return NFFT_EINVAL;
+    if (!aligned(ptr, p->csize)) return NFFT_EINVAL;
+    return NFFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nfft_strerror(int code)
+{
+    switch (code) {
+    case NFFT_OK: return "success";
+    case NFFT_EINVAL: return "invalid argument";
+    case NFFT_ENOMEM: return "out of device memory or workspace too small";
+    case NFFT_ECUDA: return "CUDA runtime error";
+    case NFFT_ENOTREADY: return "nodes not set (call nfft_set_nodes first)";
+    case NFFT_EBADNODE: return "a node coordinate is NaN, infinite or out of range";
+    case NFFT_ETIMEOUT: return "a device-side wait timed out";
+    case NFFT_EUNSUPPORTED: return "parameters valid but not supported by this build";
+    default: return "unknown error";
+    }
+}
+
+int nfft_use_device(int device)
+{
+    return cudaSetDevice(device) == cudaSuccess ? NFFT_OK : NFFT_ECUDA;
+}
+
+int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const int64_t *n, int m,
+                     int dtype)
+{
+    if (!out) return NFFT_EINVAL;
+    *out = nullptr;
+    if (d < 1 || d > 3 || !N) return NFFT_EINVAL;
+    if (dtype != NFFT_FP32 && dtype != NFFT_FP64) return NFFT_EINVAL;
+    if (M < 0 || M > 0x7fffffffLL) return NFFT_EINVAL;
+    if (m <= 0) m = 8;
+    int64_t nn[3] = {0, 0, 0}, NNv[3] = {0, 0, 0};
+    for (int t = 0; t < d; t++) {
+        NNv[t] = N[t];
+        if (N[t] < 2 || (N[t] & 1)) return NFFT_EINVAL;
+        if (N[t] > (int64_t(1) << 30)) return NFFT_EUNSUPPORTED;
+        nn[t] = n ? n[t] : (int64_t(1) << (ilog2(N[t]) + 1));
+        if (nn[t] <= N[t] || (nn[t] & 1)) return NFFT_EINVAL;
+        if (2 * int64_t(m) + 2 > nn[t]) return NFFT_EINVAL;
+    }
+    if (m > kMaxM) return NFFT_EUNSUPPORTED;
+    int64_t G = 1, NN = 1;
+    for (int t = 0; t < d; t++) {
+        if (!is_pow2(nn[t])) return NFFT_EUNSUPPORTED;
+        if (nn[t] > (dtype == NFFT_FP32 ? 16384 : 8192)) return NFFT_EUNSUPPORTED;
+        G *= nn[t];
+        NN *= NNv[t];
+    }
+    if (G > 0x7fffffffLL) return NFFT_EUNSUPPORTED;
+
+    gbnfft_plan *p = new (std::nothrow) gbnfft_plan();
+    if (!p) return NFFT_ENOMEM;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return NFFT_ECUDA;
+    }
+    p->d = d;
+    p->m = m;
+    p->dtype = dtype;
+    p->M = M;
+    p->G = G;
+    p->NN = NN;
+    p->csize = dtype == NFFT_FP32 ? sizeof(float2) : sizeof(double2);
+    p->rsize = dtype == NFFT_FP32 ? sizeof(float) : sizeof(double);
+    for (int t = 0; t < d; t++) {
+        p->N[t] = NNv[t];
+        p->n[t] = nn[t];
+    }
+    // second FFT buffer: the largest intermediate that cannot live in gA
+    if (d == 2) p->Bsz = NNv[0] * nn[1];
+    if (d == 3) p->Bsz = NNv[0] * nn[1] * nn[2];
+
+    // geometry, window constants and bins
+    Geom &g = p->geom;
+    g.d = d;
+    g.m = m;
+    const int64_t bin_default[3][3] = {{1024, 0, 0}, {32, 32, 0}, {8, 8, 8}};
+    int64_t nbins = 1;
+    for (int t = 0; t < kMaxDim; t++) {
+        if (t >= d) {
+            g.n[t] = 1;
+            g.nlog[t] = 0;
+            g.N[t] = 1;
+            g.bs[t] = 1;
+            g.bslog[t] = 0;
+            g.nb[t] = 1;
+            g.win[t] = AxisWin{0.0, 0.0};
+            continue;
+        }
+        g.n[t] = (int)nn[t];
+        g.nlog[t] = ilog2(nn[t]);
+        g.N[t] = (int)NNv[t];
+        int64_t bs = bin_default[d - 1][t];
+        if (bs > nn[t]) bs = nn[t];
+        g.bs[t] = (int)bs;
+        g.bslog[t] = ilog2(bs);
+        g.nb[t] = (int)(nn[t] / bs);
+        nbins *= g.nb[t];
+        const double sigma = double(nn[t]) / double(NNv[t]);
+        const double b = kPi * (2.0 - 1.0 / sigma);
+        g.win[t].b = b;
+        g.win[t].kscale = double(m) / std::sinh(b * double(m));
+    }
+    p->nbins = (int)nbins;
+    p->max_subs = (int)(nbins + (M + kMaxSub - 1) / kMaxSub + 1);
+    layout_workspace(p);
+
+    // tables: deconvolution factors (FP64, per axis) and twiddles (plan precision, per axis)
+    size_t tbytes = 0;
+    size_t off_dc[3] = {0, 0, 0}, off_tw[3] = {0, 0, 0};
+    for (int t = 0; t < d; t++) {
+        off_dc[t] = tbytes;
+        tbytes = align_up(tbytes + size_t(NNv[t]) * sizeof(double), 256);
+        off_tw[t] = tbytes;
+        tbytes = align_up(tbytes + size_t(nn[t]) * p->csize, 256);
+    }
+    const size_t off_status = tbytes;
+    tbytes += 256;
+    char *host = static_cast<char *>(std::calloc(1, tbytes));
+    if (!host) {
+        delete p;
+        return NFFT_ENOMEM;
+    }
+    for (int t = 0; t < d; t++) {
+        // psi_t(0) / (n_t phihat_t(k)) with phihat_t(k) = I0(m sqrt(b^2 - (2 pi k/n)^2)) / n_t:
+        // the per-axis factor of 1/(|I_n| c_k) (Algorithm "NFFT" line 2) for the window
+        // normalised to psibar(0) = 1.
+        const double b = g.win[t].b;
+        const double psi0 = std::sinh(b * m) / (kPi * m);
+        double *dc = reinterpret_cast<double *>(host + off_dc[t]);
+        for (int64_t i = 0; i < NNv[t]; i++) {
+            const double k = double(i - NNv[t] / 2);
+            const double w = 2.0 * kPi * k / double(nn[t]);
+            dc[i] = psi0 / bessel_i0(double(m) * std::sqrt(b * b - w * w));
+        }
+        for (int64_t j = 0; j < nn[t]; j++) {
+            double re, im;
+            twiddle(j, nn[t], &re, &im);
+            if (dtype == NFFT_FP32) {
+                float2 *tw = reinterpret_cast<float2 *>(host + off_tw[t]);
+                tw[j] = make_float2((float)re, (float)im);
+            } else {
+                double2 *tw = reinterpret_cast<double2 *>(host + off_tw[t]);
+                tw[j] = make_double2(re, im);
+            }
+        }
+    }
+    cudaError_t e = cudaMalloc(&p->tables, tbytes);
+    if (e == cudaSuccess) e = cudaMemcpy(p->tables, host, tbytes, cudaMemcpyHostToDevice);
+    std::free(host);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (p->tables) cudaFree(p->tables);
+        delete p;
+        return e == cudaErrorMemoryAllocation ? NFFT_ENOMEM : NFFT_ECUDA;
+    }
+    char *tb = static_cast<char *>(p->tables);
+    for (int t = 0; t < d; t++) {
+        p->deconv[t] = reinterpret_cast<double *>(tb + off_dc[t]);
+        p->tw[t] = tb + off_tw[t];
+    }
+    p->d_status = reinterpret_cast<int *>(tb + off_status);
+    *out = p;
+    return NFFT_OK;
+}
+
+int nfft_destroy(nfft_plan p)
+{
+    if (!p) return NFFT_OK;
+    set_device(p);
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    if (p->tables) cudaFree(p->tables);
+    if (p->ws_owned && p->ws) cudaFree(p->ws);
+    if (p->stage) cudaFree(p->stage);
+    for (auto &pp : p->prof) {
+        cudaEventDestroy(pp.a);
+        cudaEventDestroy(pp.b);
+    }
+    delete p;
+    return NFFT_OK;
+}
+
+int nfft_set_stream(nfft_plan p, void *stream)
+{
+    if (!p) return NFFT_EINVAL;
+    p->stream = static_cast<cudaStream_t>(stream);
+    return NFFT_OK;
+}
+
+int nfft_workspace_size(nfft_plan p, size_t *bytes)
+{
+    if (!p || !bytes) return NFFT_EINVAL;
+    *bytes = p->ws_need;
+    return NFFT_OK;
+}
+
+int nfft_set_workspace(nfft_plan p, void *ptr, size_t bytes)
+{
+    if (!p || !ptr) return NFFT_EINVAL;
+    if (!aligned(ptr, 256)) return NFFT_EINVAL;
+    if (bytes < p->ws_need) return NFFT_ENOMEM;
+    if (p->ws_owned && p->ws) {
+        set_device(p);
+        if (p->stream) cudaStreamSynchronize(p->stream);
+        cudaFree(p->ws);
+    }
+    p->ws = static_cast<char *>(ptr);
+    p->ws_bytes = bytes;
+    p->ws_owned = false;
+    p->nodes_ready = false;  // the sorted node data lived in the old workspace
+    return NFFT_OK;
+}
+
+int nfft_get_info(nfft_plan p, nfft_info *info)
+{
+    if (!p || !info) return NFFT_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->d = p->d;
+    info->m = p->m;
+    info->dtype = p->dtype;
+    info->M = p->M;
+    for (int t = 0; t < p->d; t++) {
+        info->N[t] = p->N[t];
+        info->n[t] = p->n[t];
+        info->bin[t] = p->geom.bs[t];
+    }
+    info->workspace_bytes = p->ws_need;
+    return NFFT_OK;
+}
+
+int nfft_set_nodes(nfft_plan p, const void *x)
+{
+    if (!p) return NFFT_EINVAL;
+    if (p->M > 0 && (!x || !aligned(x, p->rsize))) return NFFT_EINVAL;
+    int rc = set_device(p);
+    if (rc) return rc;
+    rc = ensure_workspace(p);
+    if (rc) return rc;
+    p->nodes_ready = false;
+    rc = p->dtype == NFFT_FP32 ? do_set_nodes<float>(p, x) : do_set_nodes<double>(p, x);
+    if (rc) return rc;
+    p->nodes_ready = true;
+    return NFFT_OK;
+}
+
+int nfft_trafo(nfft_plan p, const void *fhat, void *f)
+{
+    if (!p) return NFFT_EINVAL;
+    if (!p->nodes_ready) return NFFT_ENOTREADY;
+    if (check_dev_ptr(p, fhat, p->NN) || check_dev_ptr(p, f, p->M)) return NFFT_EINVAL;
+    int rc = set_device(p);
+    if (rc) return rc;
+    if (p->M == 0) return NFFT_OK;
+    return p->dtype == NFFT_FP32 ? do_trafo<float>(p, fhat, f) : do_trafo<double>(p, fhat, f);
+}
+
+int nfft_adjoint(nfft_plan p, const void *f, void *fhat)
+{
+    if (!p) return NFFT_EINVAL;
+    if (!p->nodes_ready) return NFFT_ENOTREADY;
+    if (check_dev_ptr(p, f, p->M) || check_dev_ptr(p, fhat, p->NN)) return NFFT_EINVAL;
+    int rc = set_device(p);
+    if (rc) return rc;
+    if (p->M == 0) {
+        GB_CHECK(cudaMemsetAsync(fhat, 0, size_t(p->NN) * p->csize, p->stream));
+        return NFFT_OK;
+    }
+    return p->dtype == NFFT_FP32 ? do_adjoint<float>(p, f, fhat) : do_adjoint<double>(p, f, fhat);
+}
+
+int nfft_grad_x(nfft_plan p, const void *coef, const void *w, void *gx)
+{
+    if (!p) return NFFT_EINVAL;
+    if (!p->nodes_ready) return NFFT_ENOTREADY;
+    if (check_dev_ptr(p, coef, p->NN) || check_dev_ptr(p, w, p->M)) return NFFT_EINVAL;
+    if (p->M > 0 && (!gx || !aligned(gx, p->rsize))) return NFFT_EINVAL;
+    int rc = set_device(p);
+    if (rc) return rc;
+    if (p->M == 0) return NFFT_OK;
+    return p->dtype == NFFT_FP32 ? do_grad<float>(p, coef, w, gx) : do_grad<double>(p, coef, w, gx);
+}
+
+int nfft_status(nfft_plan p)
+{
+    if (!p) return NFFT_EINVAL;
+    int rc = set_device(p);
+    if (rc) return rc;
+    cudaError_t e = p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return NFFT_ECUDA;
+    int h = 0;
+    if (cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return NFFT_ECUDA;
+    if (h != 0) {
+        const int zero = 0;
+        if (cudaMemcpy(p->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            return NFFT_ECUDA;
+    }
+    return h;
+}
+
+int nfft_profile(nfft_plan p, int enable)
+{
+    if (!p) return NFFT_EINVAL;
+    p->prof_on = enable != 0;
+    p->prof_used = 0;
+    return NFFT_OK;
+}
+
+int nfft_profile_read(nfft_plan p, double *ms, int64_t *count, int nstages)
+{
+    if (!p || !ms || nstages < 0) return NFFT_EINVAL;
+    int rc = set_device(p);
+    if (rc) return rc;
+    for (int i = 0; i < nstages; i++) {
+        ms[i] = 0.0;
+        if (count) count[i] = 0;
+    }
+    GB_CHECK(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    for (size_t i = 0; i < p->prof_used; i++) {
+        const auto &pp = p->prof[i];
+        if (pp.stage < 0 || pp.stage >= nstages) continue;
+        float t = 0.f;
+        GB_CHECK(cudaEventElapsedTime(&t, pp.a, pp.b));
+        ms[pp.stage] += t;
+        if (count) count[pp.stage] += 1;
+    }
+    p->prof_used = 0;
+    return NFFT_OK;
+}
+
+// ---------------------------------------------------------------------------- host variants
+
+static int ensure_stage(gbnfft_plan *p)
+{
+    // x (M d reals), fhat (|I_N| complex), f (M complex), each 256-byte aligned
+    const size_t bx = align_up(size_t(p->M) * p->d * p->rsize, 256);
+    const size_t bh = align_up(size_t(p->NN) * p->csize, 256);
+    const size_t bf = align_up(size_t(p->M) * p->csize, 256);
+    const size_t need = bx + bh + bf;
+    if (p->stage && p->stage_bytes >= need) return NFFT_OK;
+    if (p->stage) cudaFree(p->stage);
+    p->stage = nullptr;
+    if (cudaMalloc(&p->stage, need) != cudaSuccess) {
+        cudaGetLastError();
+        p->stage_bytes = 0;
+        return NFFT_ENOMEM;
+    }
+    p->stage_bytes = need;
+    return NFFT_OK;
+}
+
+static char *stage_x(gbnfft_plan *p) { return static_cast<char *>(p->stage); }
+static char *stage_fhat(gbnfft_plan *p)
+{
+    return stage_x(p) + align_up(size_t(p->M) * p->d * p->rsize, 256);
+}
+static char *stage_f(gbnfft_plan *p)
+{
+    return stage_fhat(p) + align_up(size_t(p->NN) * p->csize, 256);
+}
+
+int nfft_set_nodes_host(nfft_plan p, const void *x_host)
+{
+    if (!p) return NFFT_EINVAL;
+    if (p->M > 0 && !x_host) return NFFT_EINVAL;
+    int rc = set_device(p);
+    if (rc) return rc;
+    rc = ensure_stage(p);
+    if (rc) return rc;
+    const size_t bytes = size_t(p->M) * p->d * p->rsize;
+    if (bytes) GB_CHECK(cudaMemcpyAsync(stage_x(p), x_host, bytes, cudaMemcpyHostToDevice,
+                                        p->stream));
+    rc = nfft_set_nodes(p, stage_x(p));
+    if (rc) return rc;
+    GB_CHECK(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    return NFFT_OK;
+}
+
+int nfft_trafo_host(nfft_plan p, const void *fhat_host, void *f_host)
+{
+    if (!p) return NFFT_EINVAL;
+    if (!p->nodes_ready) return NFFT_ENOTREADY;
+    if ((p->NN > 0 && !fhat_host) || (p->M > 0 && !f_host)) return NFFT_EINVAL;
+    int rc = set_device(p);
+    if (rc) return rc;
+    rc = ensure_stage(p);
+    if (rc) return rc;
+    GB_CHECK(cudaMemcpyAsync(stage_fhat(p), fhat_host, size_t(p->NN) * p->csize,
+                             cudaMemcpyHostToDevice, p->stream));
+    rc = nfft_trafo(p, stage_fhat(p), stage_f(p));
+    if (rc) return rc;
+    if (p->M) GB_CHECK(cudaMemcpyAsync(f_host, stage_f(p), size_t(p->M) * p->csize,
+                                       cudaMemcpyDeviceToHost, p->stream));
+    GB_CHECK(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    return NFFT_OK;
+}
+
+int nfft_adjoint_host(nfft_plan p, const void *f_host, void *fhat_host)
+{
+    if (!p) return NFFT_EINVAL;
+    if (!p->nodes_ready) return NFFT_ENOTREADY;
+    if ((p->NN > 0 && !fhat_host) || (p->M > 0 && !f_host)) return NFFT_EINVAL;
+    int rc = set_device(p);
+    if (rc) return rc;
+    rc = ensure_stage(p);
+    if (rc) return rc;
+    if (p->M) GB_CHECK(cudaMemcpyAsync(stage_f(p), f_host, size_t(p->M) * p->csize,
+                                       cudaMemcpyHostToDevice, p->stream));
+    rc = nfft_adjoint(p, stage_f(p), stage_fhat(p));
+    if (rc) return rc;
+    GB_CHECK(cudaMemcpyAsync(fhat_host, stage_fhat(p), size_t(p->NN) * p->csize,
+                             cudaMemcpyDeviceToHost, p->stream));
+    GB_CHECK(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+    return NFFT_OK;
+}
+
+}  // extern "C"
