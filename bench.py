@@ -1,0 +1,517 @@
+#!/usr/bin/env python
+"""Benchmark of the NFFT hot path: forward + adjoint nodes/s on one GB300 (or N replicas).
+
+One step is one forward NFFT (Algorithm "NFFT") plus one adjoint NFFT (Algorithm "adjoint
+NFFT") over the workload's nodes, through the library's C ABI (``nfft_trafo`` /
+``nfft_adjoint``), with inputs already resident in HBM. The default workload is the 2-D radial
+trajectory: N = (512, 512), n = (1024, 1024), m = 4, M = 512 spokes x 2048 samples
+= 1,048,576 nodes, FP32 (complex64). Variants at FP64 and m = 6 are reported beside it.
+
+Printed (rank 0, one JSON line): value = M * K / (sum of the K step times) in nodes/s, the
+relative l2 errors of the measured outputs against the FP64 CPU oracle, the roofline of the
+dominant kernel (per-stage CUDA events recorded by the library on its stream), the oracle timed
+on the host cores (``cpu_baseline``), the end-to-end number through the host-buffer entry points
+(``e2e``), the SM clocks sampled during the timed region, and the number of kernel launches.
+
+``--impl reference`` times the CPU oracle instead (the reference arm of this comparison).
+Under torchrun each rank runs an independent replica of the workload (weak scaling, no
+collective on the data path); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "forward+adjoint NFFT nodes/s, FP32 vs FP64 at stated rel. ℓ2 error; % HBM peak"
+UNIT = "nodes/s"
+
+
+# ------------------------------------------------------------------------------ helpers
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["radial", "clusters"], default="radial")
+    ap.add_argument("--m", type=int, default=4)
+    ap.add_argument("--no-variants", action="store_true", help="skip the FP64 / m=6 variants")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle")
+    ap.add_argument("--no-parity", action="store_true", help="skip the oracle error check")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(name: str, m: int, dtype):
+    from paper_1810_09891_gb300 import workloads as W
+    if name == "radial":
+        return W.config_radial(m=m, dtype=dtype)
+    return W.config_clusters(dtype=dtype, m=m)
+
+
+def algorithmic_bytes(stage: str, d: int, N, n, M: int, p: int) -> float:
+    """Bytes each stage must move at least once (per launch of the stage), FP32 p = 4 / FP64 8.
+
+    Per node: d offsets (d p) + cell index and permutation entry (8) + the complex value (2p).
+    Grid: |I_n| complex values (2p each); read once by B, read and written by B^H (atomic adds).
+    FFT stages: the compact coefficients, the pruned intermediates (written and read once) and the
+    full grid (written once by the forward, read once by the adjoint)."""
+    c = 2 * p
+    G = int(np.prod(n))
+    NN = int(np.prod(N))
+    node = M * (d * p + 8 + c)
+    inter = 0
+    if d == 2:
+        inter = N[0] * n[1]
+    elif d == 3:
+        inter = N[0] * N[1] * n[2] + N[0] * n[1] * n[2]
+    if stage == "interp":
+        return node + G * c
+    if stage == "spread":
+        return node + 2 * G * c
+    if stage in ("fft_forward", "fft_adjoint"):
+        return NN * c + G * c + 2 * inter * c
+    if stage == "zero_grid":
+        return G * c
+    return 0.0
+
+
+def source_sha(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+STAGE_SOURCES = {
+    "spread": ["paper_1810_09891_gb300/csrc/spread_impl.cuh",
+               "paper_1810_09891_gb300/csrc/window.cuh"],
+    "interp": ["paper_1810_09891_gb300/csrc/interp_impl.cuh",
+               "paper_1810_09891_gb300/csrc/window.cuh"],
+    "fft_forward": ["paper_1810_09891_gb300/csrc/fft.cu"],
+    "fft_adjoint": ["paper_1810_09891_gb300/csrc/fft.cu"],
+}
+
+
+def profiled_traffic(stage: str, workload_name: str):
+    """DRAM bytes per launch from a committed ncu summary (profiles/<stage>_<workload>.txt), if
+    it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"{stage}_{workload_name}.txt")
+    if not os.path.exists(path) or stage not in STAGE_SOURCES:
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha") != source_sha(STAGE_SOURCES[stage]):
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 10:
+                    continue
+                if self.uuid and self.uuid not in parts[1]:
+                    continue
+                rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[2]) for r in rows if num(r[2]) is not None]
+        smax = [num(r[3]) for r in rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Maximum of a per-rank number over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(nodes_per_rank: int, steps: int, world: int, total_ms_max: float) -> float:
+    """Whole-job nodes/s: every rank processes its own replica of the workload (weak scaling), so
+    the job moves world * M * K nodes in the slowest rank's time."""
+    return world * nodes_per_rank * steps / (total_ms_max * 1e-3)
+
+
+def rel_l2(a, b) -> float:
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+
+def time_oracle(wl, sample_nodes: int, min_seconds: float, max_reps: int, seed: int = 0):
+    """Oracle forward + adjoint on a sample of the workload's nodes (all of them if
+    sample_nodes >= M), repeated until min_seconds elapsed; returns (nodes/s, reps, seconds)."""
+    import oracle
+    x = np.asarray(wl["x"], dtype=np.float64)
+    M = x.shape[0]
+    if sample_nodes < M:
+        idx = np.sort(np.random.default_rng(seed).choice(M, sample_nodes, replace=False))
+        xs, fs = x[idx], wl["f"][idx]
+    else:
+        xs, fs = x, wl["f"]
+    fh = wl["fhat"].astype(np.complex128)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.nfft(xs, fh, n=wl["n"], m=wl["m"])
+        oracle.nfft_adjoint(xs, fs, wl["N"], n=wl["n"], m=wl["m"])
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= min_seconds or reps >= max_reps:
+            break
+    return xs.shape[0] * reps / el, reps, el
+
+
+def reference_arm(args):
+    """--impl reference: the CPU oracle on the host cores, one step = forward + adjoint on a
+    bounded node sample of the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    wl = workload(args.workload, args.m, np.float32)
+    M = wl["x"].shape[0]
+    sample = int(max(4096, min(M, (1 << 17) * 60 // max(1, args.steps + args.warmup))))
+    for _ in range(args.warmup):
+        time_oracle(wl, sample, 0.0, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        time_oracle(wl, sample, 0.0, 1)
+    el = time.perf_counter() - t0
+    value = sample * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "N": list(wl["N"]), "n": list(wl["n"]), "m": wl["m"],
+                   "M": M, "sample_nodes": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle",
+                         "sample": f"{sample} of the {M} nodes (seeded choice), full grid; "
+                                   "one forward + one adjoint per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------ GPU arm
+
+def run_variant(plan, fh, f, steps, flush, torch):
+    """Times `steps` steps (forward + adjoint) with an L2 flush between steps outside the timed
+    events; returns per-step forward / adjoint / total milliseconds."""
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    outs = None
+    for i in range(steps):
+        flush.zero_()
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        y = plan.trafo(fh)
+        e1.record(stream)
+        h = plan.adjoint(f)
+        e2.record(stream)
+        outs = (y, h)
+    torch.cuda.synchronize()
+    fwd = [a.elapsed_time(b) for a, b, _ in ev]
+    adj = [b.elapsed_time(c) for _, b, c in ev]
+    return fwd, adj, outs
+
+
+def parity(wl, y, h, m, n, sample=4096, seed=1):
+    """Rel. l2 of the GPU outputs vs the FP64 oracle on the same (rounded) inputs: forward on a
+    seeded node sample, adjoint over all coefficients (spreading all M nodes)."""
+    import oracle
+    x = np.asarray(wl["x"], dtype=np.float64)
+    M = x.shape[0]
+    idx = np.sort(np.random.default_rng(seed).choice(M, min(sample, M), replace=False))
+    ref_f = oracle.nfft(x[idx], wl["fhat_r"], n=n, m=m)
+    e_fwd = rel_l2(y[idx], ref_f)
+    ref_h = oracle.nfft_adjoint(x, wl["f_r"], wl["N"], n=n, m=m)
+    e_adj = rel_l2(h, ref_h)
+    return e_fwd, e_adj
+
+
+def ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1810_09891_gb300 import _lib
+    from paper_1810_09891_gb300.nfft import Plan
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    hbm_peak, peak_kind = load_peaks()
+
+    # L2 flush buffer: 256 MiB, larger than the 129 MB L2 (the working set of the radial
+    # workload, ~60 MB, would otherwise stay resident between steps)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def make(dtype_np, dtype_t, m):
+        wl = workload(args.workload, m, dtype_np)
+        cdt = np.complex64 if dtype_np == np.float32 else np.complex128
+        wl["fhat_r"] = wl["fhat"].astype(cdt).astype(np.complex128)
+        wl["f_r"] = wl["f"].astype(cdt).astype(np.complex128)
+        plan = Plan(wl["N"], wl["x"].shape[0], n=wl["n"], m=m, dtype=dtype_t, device=dev)
+        x = torch.tensor(wl["x"], device=dev)
+        fh = torch.tensor(wl["fhat"].astype(cdt), device=dev)
+        f = torch.tensor(wl["f"].astype(cdt), device=dev)
+        return wl, plan, x, fh, f
+
+    wl, plan, x, fh, f = make(np.float32, torch.float32, args.m)
+    M = wl["x"].shape[0]
+    d = len(wl["N"])
+
+    # set_nodes (the paper's "precomputation"), timed separately
+    plan.set_nodes(x)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sn = []
+    for _ in range(5):
+        s0.record()
+        plan.set_nodes(x)
+        s1.record()
+        torch.cuda.synchronize()
+        sn.append(s0.elapsed_time(s1))
+    set_nodes_ms = statistics.median(sn)
+
+    # warm-up, then the timed region: K steps bracketed by barrier + synchronize
+    run_variant(plan, fh, f, max(3, args.warmup), flush, torch)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    fwd, adj, (y, h) = run_variant(plan, fh, f, args.steps, flush, torch)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(float(sum(fwd) + sum(adj)), dev)
+    ms_per_step = total_ms / args.steps
+    value = job_throughput(M, args.steps, world, total_ms)
+    st = plan.status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after the timed region")
+
+    # per-stage times (library events on the plan's stream) over a second pass of K steps
+    L = _lib.lib()
+    import ctypes
+    L.nfft_profile(plan._h, 1)
+    run_variant(plan, fh, f, args.steps, flush, torch)
+    ms = (ctypes.c_double * 7)()
+    cnt = (ctypes.c_int64 * 7)()
+    L.nfft_profile_read(plan._h, ms, cnt, 7)
+    L.nfft_profile(plan._h, 0)
+    stages = {}
+    for i, name in enumerate(_lib.STAGES):
+        if cnt[i]:
+            stages[name] = {"ms_per_launch": ms[i] / cnt[i], "launches": int(cnt[i])}
+    kernel_stages = {k: v for k, v in stages.items() if k in ("fft_forward", "interp", "spread",
+                                                              "fft_adjoint")}
+    step_ms = sum(v["ms_per_launch"] for v in kernel_stages.values())
+    dom = max(kernel_stages, key=lambda k: kernel_stages[k]["ms_per_launch"])
+    alg = algorithmic_bytes(dom, d, wl["N"], wl["n"], M, 4)
+    achieved = alg / (kernel_stages[dom]["ms_per_launch"] * 1e-3) / 1e9
+    for k, v in stages.items():
+        b = algorithmic_bytes(k, d, wl["N"], wl["n"], M, 4)
+        v["algorithmic_bytes"] = b
+        v["GBps"] = b / (v["ms_per_launch"] * 1e-3) / 1e9 if b else None
+        v["share"] = v["ms_per_launch"] / step_ms if k in kernel_stages else None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": profiled_traffic(dom, wl["name"]),
+                "peak_kind": peak_kind}
+
+    # end to end through the host-buffer entry points (pinned host memory)
+    pin_fh = torch.tensor(wl["fhat"].astype(np.complex64)).pin_memory()
+    pin_f = torch.tensor(wl["f"].astype(np.complex64)).pin_memory()
+    out_f = torch.empty(M, dtype=torch.complex64).pin_memory()
+    out_h = torch.empty(tuple(wl["N"]), dtype=torch.complex64).pin_memory()
+    plan.set_nodes_host(torch.tensor(wl["x"]))
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(3):
+        plan.trafo_host(pin_fh, out_f)
+        plan.adjoint_host(pin_f, out_h)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.trafo_host(pin_fh, out_f)
+        plan.adjoint_host(pin_f, out_h)
+    e2e_s = time.perf_counter() - t0
+    nn = int(np.prod(wl["N"]))
+    e2e = {"value": world * M * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 8 * (nn + M), "d2h_bytes_per_step": 8 * (M + nn),
+           "steps": e2e_steps}
+
+    line = None
+    if rank == 0:
+        errors = None
+        if not args.no_parity:
+            e_fwd, e_adj = parity(wl, y.cpu().numpy(), h.cpu().numpy(), args.m, plan.n)
+            errors = {"fwd_rel_l2_vs_oracle_nfft": e_fwd, "adj_rel_l2_vs_oracle_nfft": e_adj,
+                      "fwd_sample_nodes": 4096}
+        variants = []
+        if not args.no_variants:
+            for dt_np, dt_t, mm in [(np.float64, torch.float64, args.m),
+                                    (np.float32, torch.float32, 6),
+                                    (np.float64, torch.float64, 6)]:
+                wv, pv, xv, fhv, fv = make(dt_np, dt_t, mm)
+                pv.set_nodes(xv)
+                run_variant(pv, fhv, fv, 3, flush, torch)
+                kv = max(5, min(args.steps, 100))
+                fw, ad, (yv, hv) = run_variant(pv, fhv, fv, kv, flush, torch)
+                ent = {"dtype": "f64" if dt_t == torch.float64 else "f32", "m": mm,
+                       "nodes_per_s": M * kv / ((sum(fw) + sum(ad)) * 1e-3),
+                       "fwd_nodes_per_s": M * kv / (sum(fw) * 1e-3),
+                       "adj_nodes_per_s": M * kv / (sum(ad) * 1e-3)}
+                if not args.no_parity:
+                    ef, ea = parity(wv, yv.cpu().numpy(), hv.cpu().numpy(), mm, pv.n)
+                    ent.update({"fwd_rel_l2_vs_oracle_nfft": ef, "adj_rel_l2_vs_oracle_nfft": ea})
+                variants.append(ent)
+                pv.close()
+        cpu = None
+        if not args.no_cpu:
+            import oracle
+            oracle.build()
+            v, reps, el = time_oracle(wl, M, 10.0, 3)
+            cpu = {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                   "sample": f"the full workload ({M} nodes) x {reps} forward+adjoint, "
+                             f"{el:.1f} s"}
+        launches_per_step = 2 * d + 2
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "N": list(wl["N"]), "n": list(wl["n"]),
+                       "m": args.m, "M": M, "precision": "FP32 data, FP64 phihat and offsets",
+                       "l2": "flushed (256 MiB write) between timed steps, outside the events",
+                       "parallelism": f"{world} independent replica(s)"},
+            "fwd_nodes_per_s": M * args.steps / (sum(fwd) * 1e-3),
+            "adj_nodes_per_s": M * args.steps / (sum(adj) * 1e-3),
+            "set_nodes_ms": set_nodes_ms,
+            "errors": errors,
+            "roofline": roofline,
+            "stages": stages,
+            "variants": variants,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+        }
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

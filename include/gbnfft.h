@@ -158,6 +158,26 @@ enum nfft_stage {
 int nfft_profile(nfft_plan plan, int enable);
 int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
 
+/* Tuning options (defaults are chosen per plan; the values below change only speed, never the
+ * result beyond rounding).
+ *   NFFT_OPT_SPREAD_METHOD  0 automatic, 1 one thread per node with shared-memory atomics,
+ *                           2 one warp per node with shared-memory atomics,
+ *                           3 one warp per node with a private tile per warp (no atomics).
+ *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node, 2 one warp per node.
+ *   NFFT_OPT_BIN_0..2       bin (tile) size on axis 0..d-1: a power of two, 0 = default.
+ *                           Changing a bin size discards the node precomputation (call
+ *                           nfft_set_nodes again) and may change nfft_workspace_size: a
+ *                           caller-owned workspace that became too small makes nfft_set_nodes
+ *                           return NFFT_ENOMEM. */
+enum nfft_option {
+    NFFT_OPT_SPREAD_METHOD = 1,
+    NFFT_OPT_BIN_0 = 2,
+    NFFT_OPT_BIN_1 = 3,
+    NFFT_OPT_BIN_2 = 4,
+    NFFT_OPT_INTERP_METHOD = 5
+};
+int nfft_set_option(nfft_plan plan, int key, int64_t value);
+
 /* Static description of an error code. */
 const char *nfft_strerror(int code);
 

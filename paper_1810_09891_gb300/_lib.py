@@ -65,9 +65,16 @@ SIGNATURES = {
     "nfft_get_info": ([_P, ctypes.POINTER(NfftInfo)], _I),
     "nfft_strerror": ([_I], ctypes.c_char_p),
     "nfft_use_device": ([_I], _I),
+    "nfft_set_option": ([_P, _I, _I64], _I),
     "nfft_profile": ([_P, _I], _I),
     "nfft_profile_read": ([_P, ctypes.POINTER(ctypes.c_double), _PI64, _I], _I),
 }
+
+OPT_SPREAD_METHOD = 1
+OPT_BIN = (2, 3, 4)
+OPT_INTERP_METHOD = 5
+INTERP_METHODS = {"auto": 0, "thread": 1, "warp": 2}
+SPREAD_METHODS = {"auto": 0, "thread": 1, "warp_atomic": 2, "warp_private": 3}
 
 STAGES = ["set_nodes", "fft_forward", "interp", "zero_grid", "spread", "fft_adjoint", "grad"]
 

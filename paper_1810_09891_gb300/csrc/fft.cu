@@ -261,8 +261,7 @@ cudaError_t launch_fft_axis(const typename Cplx<T>::type *in, typename Cplx<T>::
         blocks = outer * ((inner + P - 1) / P);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(
-            fft_axis_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = ensure_dynamic_smem(fft_axis_kernel<T>, smem);
         if (e != cudaSuccess) return e;
     }
     fft_axis_kernel<T><<<(unsigned)blocks, threads, smem, stream>>>(

@@ -24,12 +24,44 @@ constexpr int kMaxSub = 1024;      // nodes per spreading subproblem (one CTA ti
 struct AxisWin {
     double b;       // shape parameter b = pi (2 - 1/sigma)
     double kscale;  // m / sinh(b m)
+    double edge_w;  // psibar(+-m) = kscale * b (the tap of a node on a grid point)
+    double edge_dw; // d psibar / dt at t = m, = -kscale * m * b^3 / 3
 };
+
+// Window values are evaluated from per-tap polynomials: for a node with offset frac in [0, 1]
+// and tap i in 1..2m, psibar(frac + m - i) = P_i(z), z = 2 frac - 1, a polynomial of degree
+// poly_degree(fp64, m) fitted at plan creation (Chebyshev interpolation in FP64, converted to
+// monomials). The degree keeps the absolute error below ~1e-7 (FP32) / ~4e-15 (FP64) of
+// psibar(0) = 1 for every oversampling factor sigma in (1, 16].
+// Table layout per axis: coefficient k of tap i at [k * kPolyTaps + (i - 1)].
+constexpr int kPolyTaps = 16;  // 2 * kMaxM
+__host__ __device__ constexpr int poly_degree(bool fp64, int m)
+{
+    return fp64 ? (m <= 2 ? 18 : m <= 4 ? 16 : m == 5 ? 15 : 14)
+                : (m <= 1 ? 11 : m == 2 ? 10 : m == 3 ? 9 : 8);
+}
+__host__ __device__ constexpr int poly_axis_stride(bool fp64, int m)
+{
+    return (poly_degree(fp64, m) + 1) * kPolyTaps;
+}
+
+// Spreading methods (see spread_impl.cuh); kSpreadAuto picks by tile size.
+constexpr int kSpreadAuto = 0;
+constexpr int kSpreadThread = 1;
+constexpr int kSpreadWarpAtomic = 2;
+constexpr int kSpreadWarpPrivate = 3;
+
+// Interpolation methods (see interp_impl.cuh).
+constexpr int kInterpAuto = 0;
+constexpr int kInterpThread = 1;
+constexpr int kInterpWarp = 2;
 
 // Geometry passed by value to every kernel.
 struct Geom {
     int d;
     int m;
+    int spread_method;
+    int interp_method;
     int n[kMaxDim];        // grid size per axis (power of two)
     int nlog[kMaxDim];     // log2 n
     int N[kMaxDim];        // bandwidth per axis
@@ -37,6 +69,7 @@ struct Geom {
     int bslog[kMaxDim];
     int nb[kMaxDim];       // bins per axis
     AxisWin win[kMaxDim];
+    const void *poly;      // device table of window polynomials (plan precision), d axes
 };
 
 // A spreading subproblem: up to kMaxSub consecutive sorted nodes of one bin.
@@ -131,6 +164,15 @@ cudaError_t launch_grad(const Geom &g, const typename Cplx<T>::type *grid,
     case 8: return FN<T, D, 8>(__VA_ARGS__);                                                     \
     default: return cudaErrorInvalidValue;                                                       \
     }
+
+// Opt a kernel in to `bytes` of dynamic shared memory (needed whenever static + dynamic shared
+// memory exceeds 48 KB). The setting is per kernel and device; it is made once and raised when
+// a larger size is requested (the cache is keyed by kernel address and device).
+cudaError_t ensure_dynamic_smem_ptr(const void *kernel, size_t bytes);
+template <typename K> cudaError_t ensure_dynamic_smem(K kernel, size_t bytes)
+{
+    return ensure_dynamic_smem_ptr(reinterpret_cast<const void *>(kernel), bytes);
+}
 
 namespace detail {
 // Per-dimension launchers, each instantiated (for float and double) in its own translation

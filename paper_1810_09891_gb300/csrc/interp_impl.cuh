@@ -2,11 +2,15 @@
 //   f_j = sum_{l in I_{n,m}(x_j)} g_{l mod n} prod_t psi_t(n_t x_{j,t} - l_t),
 // and the derivative of the same sum with respect to the node coordinates (node gradient).
 //
-// One thread per node, nodes visited in bin-sorted order so that the threads of a warp read
-// neighbouring grid cells (L1/L2 reuse of the oversampled grid). The window weights of the
-// inner axes are computed once per node into registers; the outermost axis weight is computed
-// in the outer loop. Nodes whose offset on some axis is exactly 0 (a node on a grid point) use
-// 2m+1 taps per axis; all other nodes use 2m (the closed support of eq. Inm).
+// Thread form (default): one thread per node, nodes visited in bin-sorted order so that the
+// threads of a warp read neighbouring grid cells (L1/L2 reuse of the oversampled grid). The
+// window values of the inner axes are evaluated once per node into registers from the per-tap
+// polynomials (tables staged in shared memory, read as warp-wide broadcasts); the outermost
+// axis' value is evaluated in the outer loop. Nodes whose offset on some axis is exactly 0 (a
+// node on a grid point) use 2m+1 taps per axis; all other nodes use 2m (the closed support of
+// eq. Inm).
+//
+// Warp form (option): one warp per node, the lanes cover the node's taps.
 #pragma once
 
 #include "gbnfft_internal.cuh"
@@ -15,37 +19,50 @@
 namespace gbnfft {
 namespace detail {
 
+constexpr int kInterpThreads = 128;
 
+template <typename T, int D>
+__device__ __forceinline__ void decode_node(const Geom &g, const typename RecOf<T>::type &r,
+                                            int *base, T *frac, bool &edge)
+{
+    int cell = r.cell;
+    edge = false;
+#pragma unroll
+    for (int t = D - 1; t >= 0; t--) {
+        base[t] = cell & (g.n[t] - 1);
+        cell >>= g.nlog[t];
+        frac[t] = r.fr[t];
+        edge |= (frac[t] == (T)0);
+    }
+}
 
 template <typename T, int D, int MM, int START>
 __device__ __forceinline__ typename Cplx<T>::type
-interp_node(const Geom &g, const typename Cplx<T>::type *__restrict__ grid, const int *base,
-            const T *frac)
+interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::type *__restrict__ grid,
+            const int *base, const T *frac)
 {
     using C = typename Cplx<T>::type;
     constexpr int NT = 2 * MM + 1;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
     C acc;
     acc.x = (T)0;
     acc.y = (T)0;
     if (D == 1) {
-        const T b0 = (T)g.win[0].b, k0 = (T)g.win[0].kscale;
+        T w0[NT];
+        window_taps<T, MM, START>(tab, frac[0], (T)g.win[0].edge_w, w0);
         const int mask0 = g.n[0] - 1;
 #pragma unroll
         for (int i = START; i < NT; i++) {
-            const T w = psibar_tap<T>(i, MM, frac[0], b0, k0);
             const C v = grid[(base[0] - MM + i) & mask0];
-            acc.x += v.x * w;
-            acc.y += v.y * w;
+            acc.x += v.x * w0[i];
+            acc.y += v.y * w0[i];
         }
     } else if (D == 2) {
         T w1[NT];
-        const T b1 = (T)g.win[1].b, k1 = (T)g.win[1].kscale;
-#pragma unroll
-        for (int i = START; i < NT; i++) w1[i] = psibar_tap<T>(i, MM, frac[1], b1, k1);
-        const T b0 = (T)g.win[0].b, k0 = (T)g.win[0].kscale;
+        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
         const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, sh0 = g.nlog[1];
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = psibar_tap<T>(i0, MM, frac[0], b0, k0);
+            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
             const C *row = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
             C in;
             in.x = (T)0;
@@ -61,18 +78,12 @@ interp_node(const Geom &g, const typename Cplx<T>::type *__restrict__ grid, cons
         }
     } else {
         T w1[NT], w2[NT];
-        const T b1 = (T)g.win[1].b, k1 = (T)g.win[1].kscale;
-        const T b2 = (T)g.win[2].b, k2 = (T)g.win[2].kscale;
-#pragma unroll
-        for (int i = START; i < NT; i++) {
-            w1[i] = psibar_tap<T>(i, MM, frac[1], b1, k1);
-            w2[i] = psibar_tap<T>(i, MM, frac[2], b2, k2);
-        }
-        const T b0 = (T)g.win[0].b, k0 = (T)g.win[0].kscale;
+        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
+        window_taps<T, MM, START>(tab + 2 * AS, frac[2], (T)g.win[2].edge_w, w2);
         const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, mask2 = g.n[2] - 1;
         const int sh1 = g.nlog[2], sh0 = g.nlog[1] + g.nlog[2];
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = psibar_tap<T>(i0, MM, frac[0], b0, k0);
+            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
             const C *plane = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
             C pl;
             pl.x = (T)0;
@@ -99,27 +110,14 @@ interp_node(const Geom &g, const typename Cplx<T>::type *__restrict__ grid, cons
     return acc;
 }
 
-template <typename T, int D>
-__device__ __forceinline__ void decode_node(const Geom &g, const typename RecOf<T>::type &r,
-                                            int *base, T *frac, bool &edge)
-{
-    int cell = r.cell;
-    edge = false;
-#pragma unroll
-    for (int t = D - 1; t >= 0; t--) {
-        base[t] = cell & (g.n[t] - 1);
-        cell >>= g.nlog[t];
-        frac[t] = r.fr[t];
-        edge |= (frac[t] == (T)0);
-    }
-}
-
 template <typename T, int D, int MM>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kInterpThreads)
     interp_kernel(Geom g, const typename Cplx<T>::type *__restrict__ grid,
                   const typename RecOf<T>::type *__restrict__ rec, const int *__restrict__ perm,
                   int M, typename Cplx<T>::type *__restrict__ f)
 {
+    __shared__ __align__(16) T tab[kMaxDim * poly_axis_stride(sizeof(T) == 8, MM)];
+    load_window_tables<T, MM>(tab, g.poly, D);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= M) return;
     const typename RecOf<T>::type r = rec[s];
@@ -129,49 +127,138 @@ __global__ void __launch_bounds__(128)
     decode_node<T, D>(g, r, base, frac, edge);
     typename Cplx<T>::type v;
     if (!edge)
-        v = interp_node<T, D, MM, 1>(g, grid, base, frac);
+        v = interp_node<T, D, MM, 1>(g, tab, grid, base, frac);
     else
-        v = interp_node<T, D, MM, 0>(g, grid, base, frac);
+        v = interp_node<T, D, MM, 0>(g, tab, grid, base, frac);
     f[perm[s]] = v;
 }
 
-// Node gradient: accumulates, per axis t, sum_l g_l dpsibar_t(.) prod_{u != t} psibar_u(.).
+// ------------------------------------------------------------------------- warp form of B
+// One warp per node: the lanes cover the node's taps (last axis fastest, so a warp load touches
+// a few contiguous grid rows instead of 32 scattered ones), each per-axis window value is
+// evaluated by one lane and broadcast with shuffles, and the partial sums are reduced across
+// the warp.
+constexpr int kInterpWarps = 8;
+
 template <typename T, int D, int MM, int START>
-__device__ __forceinline__ void grad_node(const Geom &g,
+__device__ __forceinline__ typename Cplx<T>::type
+interp_warp_taps(const Geom &g, const typename Cplx<T>::type *__restrict__ grid, const int *base,
+                 T wa, T wb, int lane)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int NT = 2 * MM + 1;
+    constexpr int NW = D * NT;
+    constexpr int PER = NT - START;
+    constexpr int TAPS = D == 1 ? PER : (D == 2 ? PER * PER : PER * PER * PER);
+    C acc;
+    acc.x = (T)0;
+    acc.y = (T)0;
+#pragma unroll 2
+    for (int b0 = 0; b0 < TAPS; b0 += 32) {
+        const int q = b0 + lane;
+        int rem = q < TAPS ? q : 0;
+        T w = (T)1;
+        size_t gi = 0;
+        int shift = 0;
+#pragma unroll
+        for (int t = D - 1; t >= 0; t--) {
+            const int a = rem % PER;
+            rem /= PER;
+            const int src = t * NT + a + START;
+            const T wa_s = __shfl_sync(0xffffffffu, wa, src & 31);
+            T wt = wa_s;
+            if (NW > 32) {
+                const T wb_s = __shfl_sync(0xffffffffu, wb, src & 31);
+                wt = src < 32 ? wa_s : wb_s;
+            }
+            w *= wt;
+            gi |= (size_t)((base[t] - MM + a + START) & (g.n[t] - 1)) << shift;
+            shift += g.nlog[t];
+        }
+        if (q < TAPS) {
+            const C v = grid[gi];
+            acc.x += v.x * w;
+            acc.y += v.y * w;
+        }
+    }
+    return acc;
+}
+
+template <typename T, int D, int MM>
+__global__ void __launch_bounds__(32 * kInterpWarps)
+    interp_warp_kernel(Geom g, const typename Cplx<T>::type *__restrict__ grid,
+                       const typename RecOf<T>::type *__restrict__ rec,
+                       const int *__restrict__ perm, int M, typename Cplx<T>::type *__restrict__ f)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int NT = 2 * MM + 1;
+    constexpr int NW = D * NT;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    __shared__ __align__(16) T tab[kMaxDim * AS];
+    load_window_tables<T, MM>(tab, g.poly, D);
+    const int lane = threadIdx.x & 31;
+    const int s = blockIdx.x * kInterpWarps + (threadIdx.x >> 5);
+    if (s >= M) return;  // the whole warp leaves together
+    const typename RecOf<T>::type r = rec[s];
+    int base[D];
+    T frac[D];
+    bool edge;
+    decode_node<T, D>(g, r, base, frac, edge);
+    T wa = (T)0, wb = (T)0;
+    if (lane < NW) {
+        const int t = lane / NT, i = lane - (lane / NT) * NT;
+        wa = window_tap<T, MM>(tab + t * AS, i, frac[t], (T)g.win[t].edge_w);
+    }
+    if (NW > 32 && lane + 32 < NW) {
+        const int q = lane + 32, t = q / NT, i = q - (q / NT) * NT;
+        wb = window_tap<T, MM>(tab + t * AS, i, frac[t], (T)g.win[t].edge_w);
+    }
+    C acc = edge ? interp_warp_taps<T, D, MM, 0>(g, grid, base, wa, wb, lane)
+                 : interp_warp_taps<T, D, MM, 1>(g, grid, base, wa, wb, lane);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (lane == 0) f[perm[s]] = acc;
+}
+
+// ------------------------------------------------------------------------- node gradient
+// Accumulates, per axis t, sum_l g_l dpsibar_t(.) prod_{u != t} psibar_u(.).
+template <typename T, int D, int MM, int START>
+__device__ __forceinline__ void grad_node(const Geom &g, const T *__restrict__ tab,
                                           const typename Cplx<T>::type *__restrict__ grid,
                                           const int *base, const T *frac,
                                           typename Cplx<T>::type *acc)
 {
     using C = typename Cplx<T>::type;
     constexpr int NT = 2 * MM + 1;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
 #pragma unroll
     for (int t = 0; t < D; t++) {
         acc[t].x = (T)0;
         acc[t].y = (T)0;
     }
     if (D == 1) {
-        const T b0 = (T)g.win[0].b, k0 = (T)g.win[0].kscale;
         const int mask0 = g.n[0] - 1;
 #pragma unroll
         for (int i = START; i < NT; i++) {
-            const T dw = dpsibar_tap<T>(i, MM, frac[0], b0, k0);
+            T w, dw;
+            window_tap_d<T, MM>(tab, i, frac[0], (T)g.win[0].edge_w, (T)g.win[0].edge_dw, w, dw);
             const C v = grid[(base[0] - MM + i) & mask0];
             acc[0].x += v.x * dw;
             acc[0].y += v.y * dw;
         }
     } else if (D == 2) {
         T w1[NT], d1[NT];
-        const T b1 = (T)g.win[1].b, k1 = (T)g.win[1].kscale;
 #pragma unroll
-        for (int i = START; i < NT; i++) {
-            w1[i] = psibar_tap<T>(i, MM, frac[1], b1, k1);
-            d1[i] = dpsibar_tap<T>(i, MM, frac[1], b1, k1);
-        }
-        const T b0 = (T)g.win[0].b, k0 = (T)g.win[0].kscale;
+        for (int i = START; i < NT; i++)
+            window_tap_d<T, MM>(tab + AS, i, frac[1], (T)g.win[1].edge_w, (T)g.win[1].edge_dw,
+                                w1[i], d1[i]);
         const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, sh0 = g.nlog[1];
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = psibar_tap<T>(i0, MM, frac[0], b0, k0);
-            const T d0 = dpsibar_tap<T>(i0, MM, frac[0], b0, k0);
+            T w0, d0;
+            window_tap_d<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w, (T)g.win[0].edge_dw, w0, d0);
             const C *row = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
             C s0, s1;
             s0.x = s0.y = s1.x = s1.y = (T)0;
@@ -190,21 +277,18 @@ __device__ __forceinline__ void grad_node(const Geom &g,
         }
     } else {
         T w1[NT], d1[NT], w2[NT], d2[NT];
-        const T b1 = (T)g.win[1].b, k1 = (T)g.win[1].kscale;
-        const T b2 = (T)g.win[2].b, k2 = (T)g.win[2].kscale;
 #pragma unroll
         for (int i = START; i < NT; i++) {
-            w1[i] = psibar_tap<T>(i, MM, frac[1], b1, k1);
-            d1[i] = dpsibar_tap<T>(i, MM, frac[1], b1, k1);
-            w2[i] = psibar_tap<T>(i, MM, frac[2], b2, k2);
-            d2[i] = dpsibar_tap<T>(i, MM, frac[2], b2, k2);
+            window_tap_d<T, MM>(tab + AS, i, frac[1], (T)g.win[1].edge_w, (T)g.win[1].edge_dw,
+                                w1[i], d1[i]);
+            window_tap_d<T, MM>(tab + 2 * AS, i, frac[2], (T)g.win[2].edge_w,
+                                (T)g.win[2].edge_dw, w2[i], d2[i]);
         }
-        const T b0 = (T)g.win[0].b, k0 = (T)g.win[0].kscale;
         const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, mask2 = g.n[2] - 1;
         const int sh1 = g.nlog[2], sh0 = g.nlog[1] + g.nlog[2];
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = psibar_tap<T>(i0, MM, frac[0], b0, k0);
-            const T d0 = dpsibar_tap<T>(i0, MM, frac[0], b0, k0);
+            T w0, d0;
+            window_tap_d<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w, (T)g.win[0].edge_dw, w0, d0);
             const C *plane = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
             C p0, p1, p2;  // plane sums for the three partial derivatives
             p0.x = p0.y = p1.x = p1.y = p2.x = p2.y = (T)0;
@@ -239,11 +323,13 @@ __device__ __forceinline__ void grad_node(const Geom &g,
 }
 
 template <typename T, int D, int MM>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kInterpThreads)
     grad_kernel(Geom g, const typename Cplx<T>::type *__restrict__ grid,
                 const typename RecOf<T>::type *__restrict__ rec, const int *__restrict__ perm,
                 int M, const typename Cplx<T>::type *__restrict__ w, T *__restrict__ gx)
 {
+    __shared__ __align__(16) T tab[kMaxDim * poly_axis_stride(sizeof(T) == 8, MM)];
+    load_window_tables<T, MM>(tab, g.poly, D);
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= M) return;
     const typename RecOf<T>::type r = rec[s];
@@ -253,9 +339,9 @@ __global__ void __launch_bounds__(128)
     decode_node<T, D>(g, r, base, frac, edge);
     typename Cplx<T>::type acc[D];
     if (!edge)
-        grad_node<T, D, MM, 1>(g, grid, base, frac, acc);
+        grad_node<T, D, MM, 1>(g, tab, grid, base, frac, acc);
     else
-        grad_node<T, D, MM, 0>(g, grid, base, frac, acc);
+        grad_node<T, D, MM, 0>(g, tab, grid, base, frac, acc);
     const int j = perm[s];
     const typename Cplx<T>::type wj = w[j];
 #pragma unroll
@@ -270,9 +356,17 @@ cudaError_t launch_interp_m(const Geom &g, const typename Cplx<T>::type *grid,
                             const typename RecOf<T>::type *rec, const int *perm, int64_t M,
                             typename Cplx<T>::type *f, cudaStream_t stream)
 {
-    const int threads = 128;
-    interp_kernel<T, D, MM><<<(unsigned)((M + threads - 1) / threads), threads, 0, stream>>>(
-        g, grid, rec, perm, (int)M, f);
+    int method = g.interp_method;
+    if (method == kInterpAuto) method = kInterpThread;
+    if (method == kInterpWarp) {
+        const int64_t blocks = (M + kInterpWarps - 1) / kInterpWarps;
+        interp_warp_kernel<T, D, MM><<<(unsigned)blocks, 32 * kInterpWarps, 0, stream>>>(
+            g, grid, rec, perm, (int)M, f);
+    } else {
+        const int64_t blocks = (M + kInterpThreads - 1) / kInterpThreads;
+        interp_kernel<T, D, MM><<<(unsigned)blocks, kInterpThreads, 0, stream>>>(g, grid, rec,
+                                                                                 perm, (int)M, f);
+    }
     return cudaGetLastError();
 }
 
@@ -281,13 +375,11 @@ cudaError_t launch_grad_m(const Geom &g, const typename Cplx<T>::type *grid,
                           const typename RecOf<T>::type *rec, const int *perm, int64_t M,
                           const typename Cplx<T>::type *w, T *gx, cudaStream_t stream)
 {
-    const int threads = 128;
-    grad_kernel<T, D, MM><<<(unsigned)((M + threads - 1) / threads), threads, 0, stream>>>(
-        g, grid, rec, perm, (int)M, w, gx);
+    const int64_t blocks = (M + kInterpThreads - 1) / kInterpThreads;
+    grad_kernel<T, D, MM><<<(unsigned)blocks, kInterpThreads, 0, stream>>>(g, grid, rec, perm,
+                                                                           (int)M, w, gx);
     return cudaGetLastError();
 }
-
-
 
 template <typename T, int D>
 cudaError_t interp_d(const Geom &g, const typename Cplx<T>::type *grid,

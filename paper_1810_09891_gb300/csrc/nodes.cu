@@ -3,9 +3,30 @@
 // This is the GPU form of the paper's node sorting (Section 3.1, Table tab:nfftflags,
 // NFFT_SORT_NODES): nodes that share a tile are processed together by the interpolation and
 // spreading kernels.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "gbnfft_internal.cuh"
 
 namespace gbnfft {
+
+cudaError_t ensure_dynamic_smem_ptr(const void *kernel, size_t bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, size_t> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_pair(kernel, dev);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    done[key] = bytes;
+    return cudaSuccess;
+}
 
 // |n x| must stay below 2^52 for floor() and the offset to be exact in FP64.
 static constexpr double kMaxAbsNx = 4503599627370496.0;

@@ -68,6 +68,48 @@ void twiddle(int64_t j, int64_t L, double *re, double *im)
     *im = -s;
 }
 
+// Normalised window psibar(t) = m sinh(b u) / (u sinh(b m)), u = sqrt(m^2 - t^2), |t| <= m.
+double psibar_host(double t, int m, double b)
+{
+    const double s = (double(m) - t) * (double(m) + t);
+    if (s < 0.0) return 0.0;
+    const double kscale = double(m) / std::sinh(b * double(m));
+    if (s == 0.0) return kscale * b;
+    const double u = std::sqrt(s);
+    return kscale * std::sinh(b * u) / u;
+}
+
+// Monomial coefficients (in z = 2 frac - 1) of the degree-deg Chebyshev interpolant of
+// frac -> psibar(frac + m - i) on [0, 1] (interpolation at the deg + 1 Chebyshev points).
+void fit_tap_poly(int m, double b, int i, int deg, double *mono)
+{
+    const int n = deg + 1;
+    double f[32], c[32], Tprev[32], Tcur[32], Tnext[32];
+    for (int k = 0; k < n; k++) {
+        const double z = std::cos(kPi * (k + 0.5) / n);
+        f[k] = psibar_host(0.5 * (z + 1.0) + double(m) - double(i), m, b);
+    }
+    for (int j = 0; j < n; j++) {
+        double acc = 0.0;
+        for (int k = 0; k < n; k++) acc += f[k] * std::cos(kPi * j * (k + 0.5) / n);
+        c[j] = 2.0 * acc / n;
+    }
+    c[0] *= 0.5;
+    for (int k = 0; k < n; k++) mono[k] = Tprev[k] = Tcur[k] = 0.0;
+    Tprev[0] = 1.0;  // T_0
+    Tcur[1] = 1.0;   // T_1
+    mono[0] = c[0];
+    if (n > 1) mono[1] += c[1];
+    for (int j = 2; j < n; j++) {
+        for (int k = 0; k < n; k++) Tnext[k] = (k > 0 ? 2.0 * Tcur[k - 1] : 0.0) - Tprev[k];
+        for (int k = 0; k < n; k++) {
+            mono[k] += c[j] * Tnext[k];
+            Tprev[k] = Tcur[k];
+            Tcur[k] = Tnext[k];
+        }
+    }
+}
+
 struct Region {
     size_t off = 0, bytes = 0;
 };
@@ -87,6 +129,7 @@ struct gbnfft_plan {
     int64_t Bsz = 0;   // complex values of the second FFT buffer
     int nbins = 0;
     int max_subs = 0;
+    int64_t bin_req[3] = {0, 0, 0};  // requested bin sizes (0 = default)
     // plan-owned device tables
     void *tables = nullptr;
     double *deconv[3] = {nullptr, nullptr, nullptr};
@@ -149,6 +192,32 @@ void layout_workspace(gbnfft_plan *p)
     put(p->nsub, 16);
     put(p->subs, size_t(p->max_subs) * sizeof(SubProb));
     p->ws_need = align_up(off, 256);
+}
+
+// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 16 x 16,
+// 3-D 8 x 8 x 8), clipped to n_t. Recomputes the bin counts and the workspace layout.
+void setup_bins(gbnfft_plan *p)
+{
+    Geom &g = p->geom;
+    const int64_t bin_default[3][3] = {{1024, 0, 0}, {16, 16, 0}, {8, 8, 8}};
+    int64_t nbins = 1;
+    for (int t = 0; t < kMaxDim; t++) {
+        if (t >= p->d) {
+            g.bs[t] = 1;
+            g.bslog[t] = 0;
+            g.nb[t] = 1;
+            continue;
+        }
+        int64_t bs = p->bin_req[t] > 0 ? p->bin_req[t] : bin_default[p->d - 1][t];
+        if (bs > p->n[t]) bs = p->n[t];
+        g.bs[t] = (int)bs;
+        g.bslog[t] = ilog2(bs);
+        g.nb[t] = (int)(p->n[t] / bs);
+        nbins *= g.nb[t];
+    }
+    p->nbins = (int)nbins;
+    p->max_subs = (int)(nbins + (p->M + kMaxSub - 1) / kMaxSub + 1);
+    layout_workspace(p);
 }
 
 template <typename R> R *at(gbnfft_plan *p, const Region &r)
@@ -421,36 +490,27 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
     Geom &g = p->geom;
     g.d = d;
     g.m = m;
-    const int64_t bin_default[3][3] = {{1024, 0, 0}, {32, 32, 0}, {8, 8, 8}};
-    int64_t nbins = 1;
+    g.spread_method = kSpreadAuto;
+    g.interp_method = kInterpAuto;
     for (int t = 0; t < kMaxDim; t++) {
         if (t >= d) {
             g.n[t] = 1;
             g.nlog[t] = 0;
             g.N[t] = 1;
-            g.bs[t] = 1;
-            g.bslog[t] = 0;
-            g.nb[t] = 1;
             g.win[t] = AxisWin{0.0, 0.0};
             continue;
         }
         g.n[t] = (int)nn[t];
         g.nlog[t] = ilog2(nn[t]);
         g.N[t] = (int)NNv[t];
-        int64_t bs = bin_default[d - 1][t];
-        if (bs > nn[t]) bs = nn[t];
-        g.bs[t] = (int)bs;
-        g.bslog[t] = ilog2(bs);
-        g.nb[t] = (int)(nn[t] / bs);
-        nbins *= g.nb[t];
         const double sigma = double(nn[t]) / double(NNv[t]);
         const double b = kPi * (2.0 - 1.0 / sigma);
         g.win[t].b = b;
         g.win[t].kscale = double(m) / std::sinh(b * double(m));
+        g.win[t].edge_w = g.win[t].kscale * b;
+        g.win[t].edge_dw = -g.win[t].kscale * double(m) * b * b * b / 3.0;
     }
-    p->nbins = (int)nbins;
-    p->max_subs = (int)(nbins + (M + kMaxSub - 1) / kMaxSub + 1);
-    layout_workspace(p);
+    setup_bins(p);
 
     // tables: deconvolution factors (FP64, per axis) and twiddles (plan precision, per axis)
     size_t tbytes = 0;
@@ -461,6 +521,11 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
         off_tw[t] = tbytes;
         tbytes = align_up(tbytes + size_t(nn[t]) * p->csize, 256);
     }
+    const bool fp64 = dtype == NFFT_FP64;
+    const int deg = poly_degree(fp64, m);
+    const size_t poly_axis = size_t(poly_axis_stride(fp64, m));
+    const size_t off_poly = tbytes;
+    tbytes = align_up(tbytes + size_t(d) * poly_axis * p->rsize, 256);
     const size_t off_status = tbytes;
     tbytes += 256;
     char *host = static_cast<char *>(std::calloc(1, tbytes));
@@ -479,6 +544,18 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
             const double k = double(i - NNv[t] / 2);
             const double w = 2.0 * kPi * k / double(nn[t]);
             dc[i] = psi0 / bessel_i0(double(m) * std::sqrt(b * b - w * w));
+        }
+        // window polynomials of this axis: coefficient k of tap i at [k * kPolyTaps + i - 1]
+        for (int i = 1; i <= 2 * m; i++) {
+            double mono[32];
+            fit_tap_poly(m, b, i, deg, mono);
+            for (int k = 0; k <= deg; k++) {
+                const size_t e = size_t(t) * poly_axis + size_t(k) * kPolyTaps + size_t(i - 1);
+                if (fp64)
+                    reinterpret_cast<double *>(host + off_poly)[e] = mono[k];
+                else
+                    reinterpret_cast<float *>(host + off_poly)[e] = (float)mono[k];
+            }
         }
         for (int64_t j = 0; j < nn[t]; j++) {
             double re, im;
@@ -507,6 +584,7 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
         p->tw[t] = tb + off_tw[t];
     }
     p->d_status = reinterpret_cast<int *>(tb + off_status);
+    g.poly = tb + off_poly;
     *out = p;
     return NFFT_OK;
 }
@@ -584,6 +662,7 @@ int nfft_set_nodes(nfft_plan p, const void *x)
     if (rc) return rc;
     rc = ensure_workspace(p);
     if (rc) return rc;
+    if (p->ws_bytes < p->ws_need) return NFFT_ENOMEM;
     p->nodes_ready = false;
     rc = p->dtype == NFFT_FP32 ? do_set_nodes<float>(p, x) : do_set_nodes<double>(p, x);
     if (rc) return rc;
@@ -644,6 +723,61 @@ int nfft_status(nfft_plan p)
             return NFFT_ECUDA;
     }
     return h;
+}
+
+int nfft_set_option(nfft_plan p, int key, int64_t value)
+{
+    if (!p) return NFFT_EINVAL;
+    switch (key) {
+    case NFFT_OPT_SPREAD_METHOD:
+        if (value < kSpreadAuto || value > kSpreadWarpPrivate) return NFFT_EINVAL;
+        p->geom.spread_method = (int)value;
+        return NFFT_OK;
+    case NFFT_OPT_INTERP_METHOD:
+        if (value < kInterpAuto || value > kInterpWarp) return NFFT_EINVAL;
+        p->geom.interp_method = (int)value;
+        return NFFT_OK;
+    case NFFT_OPT_BIN_0:
+    case NFFT_OPT_BIN_1:
+    case NFFT_OPT_BIN_2: {
+        const int t = key - NFFT_OPT_BIN_0;
+        if (t >= p->d) return NFFT_EINVAL;
+        if (value < 0 || (value > 0 && !is_pow2(value))) return NFFT_EINVAL;
+        {
+            // the spreading tile (bin + 2m halo per axis, complex) must fit in shared memory
+            size_t cells = 1;
+            for (int u = 0; u < p->d; u++) {
+                int64_t bs = u == t ? value : p->geom.bs[u];
+                if (u == t && value == 0) bs = 0;  // default: always fits
+                if (bs == 0) {
+                    cells = 0;
+                    break;
+                }
+                if (bs > p->n[u]) bs = p->n[u];
+                cells *= size_t(bs + 2 * p->m);
+            }
+            // 227 KB per CTA minus the window tables kept beside the tile
+            const size_t tables = size_t(kMaxDim) * poly_axis_stride(p->dtype == NFFT_FP64, p->m) *
+                                  p->rsize;
+            if (cells * p->csize > 227 * 1024 - tables) return NFFT_EINVAL;
+        }
+        p->bin_req[t] = value;
+        const size_t old_need = p->ws_need;
+        setup_bins(p);
+        p->nodes_ready = false;  // the node order depends on the bins
+        if (p->ws_owned && p->ws && p->ws_need > old_need) {
+            set_device(p);
+            if (p->stream) cudaStreamSynchronize(p->stream);
+            cudaFree(p->ws);
+            p->ws = nullptr;
+            p->ws_bytes = 0;
+            p->ws_owned = false;
+        }
+        return NFFT_OK;
+    }
+    default:
+        return NFFT_EINVAL;
+    }
 }
 
 int nfft_profile(nfft_plan p, int enable)

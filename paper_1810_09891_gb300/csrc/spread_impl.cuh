@@ -3,10 +3,19 @@
 // GPU form of the paper's blockwise adjoint (Section 3.1, Table tab:nfftflags,
 // NFFT_OMP_BLOCKWISE_ADJOINT): the grid is cut into bins, and each CTA takes one subproblem
 // (at most kMaxSub sorted nodes of one bin). It accumulates their contributions into a
-// shared-memory tile covering the bin plus a halo of m cells on each side (shared-memory
-// atomics), then adds the tile into the global grid with one vector atomic per complex cell.
-// The kernel is persistent: a grid of a few CTAs per SM walks the subproblem list, whose
-// length is read from device memory (it is only known on the device after the sort).
+// shared-memory tile covering the bin plus a halo of m cells on each side, then adds the tile
+// into the global grid with one vector atomic per complex cell. The kernels are persistent: a
+// grid of a few CTAs per SM walks the subproblem list, whose length is read from device memory
+// (it is only known on the device after the sort).
+//
+// Three ways to fill the tile (Geom::spread_method):
+//   kSpreadThread  one thread per node, shared-memory atomics (interleaved re/im tile);
+//   kSpreadWarpAtomic  one warp per node, the lanes cover the node's taps (so a warp never
+//                  writes one cell twice), shared-memory atomics into one tile (re and im planes);
+//   kSpreadWarpPrivate one warp per node as above, but every warp owns a private tile and adds
+//                  with plain loads and stores (no atomics); the tiles are summed at the flush.
+// Coincident and clustered nodes (a radial trajectory puts every spoke through the origin) make
+// the atomics of the first form collide; the warp forms do not.
 #pragma once
 
 #include "gbnfft_internal.cuh"
@@ -28,27 +37,26 @@ static __device__ __forceinline__ void global_add(double2 *p, double re, double 
 }
 
 template <typename T, int D, int MM, int START>
-__device__ __forceinline__ void spread_node(const Geom &g, T *tile, const int *tdim,
-                                            const int *loc, const T *frac, T vr, T vi)
+__device__ __forceinline__ void spread_node(const Geom &g, const T *__restrict__ tab, T *tile,
+                                            const int *tdim, const int *loc, const T *frac, T vr,
+                                            T vi)
 {
     constexpr int NT = 2 * MM + 1;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
     if (D == 1) {
-        const T b0 = (T)g.win[0].b, k0 = (T)g.win[0].kscale;
+        T w0[NT];
+        window_taps<T, MM, START>(tab, frac[0], (T)g.win[0].edge_w, w0);
 #pragma unroll
         for (int i = START; i < NT; i++) {
-            const T w = psibar_tap<T>(i, MM, frac[0], b0, k0);
             T *c = tile + 2 * (loc[0] + i);
-            atomicAdd(c, vr * w);
-            atomicAdd(c + 1, vi * w);
+            atomicAdd(c, vr * w0[i]);
+            atomicAdd(c + 1, vi * w0[i]);
         }
     } else if (D == 2) {
         T w1[NT];
-        const T b1 = (T)g.win[1].b, k1 = (T)g.win[1].kscale;
-#pragma unroll
-        for (int i = START; i < NT; i++) w1[i] = psibar_tap<T>(i, MM, frac[1], b1, k1);
-        const T b0 = (T)g.win[0].b, k0 = (T)g.win[0].kscale;
+        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = psibar_tap<T>(i0, MM, frac[0], b0, k0);
+            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
             const T ar = vr * w0, ai = vi * w0;
             T *row = tile + 2 * ((loc[0] + i0) * tdim[1] + loc[1]);
 #pragma unroll
@@ -59,16 +67,10 @@ __device__ __forceinline__ void spread_node(const Geom &g, T *tile, const int *t
         }
     } else {
         T w1[NT], w2[NT];
-        const T b1 = (T)g.win[1].b, k1 = (T)g.win[1].kscale;
-        const T b2 = (T)g.win[2].b, k2 = (T)g.win[2].kscale;
-#pragma unroll
-        for (int i = START; i < NT; i++) {
-            w1[i] = psibar_tap<T>(i, MM, frac[1], b1, k1);
-            w2[i] = psibar_tap<T>(i, MM, frac[2], b2, k2);
-        }
-        const T b0 = (T)g.win[0].b, k0 = (T)g.win[0].kscale;
+        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
+        window_taps<T, MM, START>(tab + 2 * AS, frac[2], (T)g.win[2].edge_w, w2);
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = psibar_tap<T>(i0, MM, frac[0], b0, k0);
+            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
             const T ar = vr * w0, ai = vi * w0;
             T *plane = tile + 2 * ((loc[0] + i0) * tdim[1] * tdim[2]);
 #pragma unroll
@@ -94,6 +96,8 @@ __global__ void __launch_bounds__(256)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) T tab[kMaxDim * poly_axis_stride(sizeof(T) == 8, MM)];
+    load_window_tables<T, MM>(tab, g.poly, D);
     T *tile = reinterpret_cast<T *>(smem_raw);
     int tdim[D];
     int cells = 1;
@@ -133,9 +137,9 @@ __global__ void __launch_bounds__(256)
                 edge |= (frac[t] == (T)0);
             }
             if (!edge)
-                spread_node<T, D, MM, 1>(g, tile, tdim, loc, frac, v.x, v.y);
+                spread_node<T, D, MM, 1>(g, tab, tile, tdim, loc, frac, v.x, v.y);
             else
-                spread_node<T, D, MM, 0>(g, tile, tdim, loc, frac, v.x, v.y);
+                spread_node<T, D, MM, 0>(g, tab, tile, tdim, loc, frac, v.x, v.y);
         }
         __syncthreads();
 
@@ -160,6 +164,226 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ----------------------------------------------------------------------------- warp forms
+
+constexpr int kSpreadWarps = 8;  // warps per CTA of the warp forms
+
+// Shared memory of the warp forms: the tile(s), then a staging area for one chunk of
+// kSpreadChunk sorted nodes (their records and values, loaded with coalesced reads while the
+// previous chunk is being spread).
+constexpr int kSpreadChunk = 32 * kSpreadWarps;
+
+template <typename T>
+__host__ __device__ constexpr size_t spread_stage_bytes()
+{
+    return kSpreadChunk * (sizeof(typename RecOf<T>::type) + sizeof(typename Cplx<T>::type));
+}
+
+// The taps of one node, 32 at a time across the lanes of a warp. Tap q enumerates the
+// (2m + 1 - START)^d box row-major (last axis fastest, so neighbouring lanes hit neighbouring
+// cells); its weight is the product of the per-axis window values held by lanes t*NT + i.
+template <typename T, int D, int MM, bool PRIVATE, int START>
+__device__ __forceinline__ void spread_warp_taps(T *re, T *im, const int *tdim, const int *loc,
+                                                 T wa, T wb, typename Cplx<T>::type v, int lane)
+{
+    constexpr int NT = 2 * MM + 1;
+    constexpr int NW = D * NT;
+    constexpr int PER = NT - START;
+    constexpr int TAPS = D == 1 ? PER : (D == 2 ? PER * PER : PER * PER * PER);
+#pragma unroll 1
+    for (int base = 0; base < TAPS; base += 32) {
+        const int q = base + lane;
+        int rem = q < TAPS ? q : 0;
+        T w = (T)1;
+        int idx = 0, mult = 1;
+#pragma unroll
+        for (int t = D - 1; t >= 0; t--) {
+            const int a = rem % PER;
+            rem /= PER;
+            const int src = t * NT + a + START;
+            const T wa_s = __shfl_sync(0xffffffffu, wa, src & 31);
+            T wt = wa_s;
+            if (NW > 32) {
+                const T wb_s = __shfl_sync(0xffffffffu, wb, src & 31);
+                wt = src < 32 ? wa_s : wb_s;
+            }
+            w *= wt;
+            idx += (loc[t] + a + START) * mult;
+            mult *= tdim[t];
+        }
+        if (q < TAPS) {
+            if (PRIVATE) {
+                re[idx] += w * v.x;
+                im[idx] += w * v.y;
+            } else {
+                atomicAdd(re + idx, w * v.x);
+                atomicAdd(im + idx, w * v.y);
+            }
+        }
+    }
+}
+
+template <typename T, int D, int MM, bool PRIVATE>
+__global__ void __launch_bounds__(32 * kSpreadWarps)
+    spread_warp_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
+                       const typename RecOf<T>::type *__restrict__ rec,
+                       const int *__restrict__ perm, const SubProb *__restrict__ subs,
+                       const int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    constexpr int NT = 2 * MM + 1;        // tap slots per axis (slot 0 only on a grid point)
+    constexpr int NW = D * NT;            // window values per node
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) T tab[kMaxDim * AS];
+    load_window_tables<T, MM>(tab, g.poly, D);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    int tdim[D];
+    int cells = 1;
+#pragma unroll
+    for (int t = 0; t < D; t++) {
+        tdim[t] = g.bs[t] + 2 * MM;
+        cells *= tdim[t];
+    }
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const size_t tile_reals = (size_t)2 * cells * (PRIVATE ? kSpreadWarps : 1);
+    Rec *st_rec = reinterpret_cast<Rec *>(smem_raw + ((tile_reals * sizeof(T) + 15) / 16) * 16);
+    C *st_val = reinterpret_cast<C *>(st_rec + kSpreadChunk);
+    // re plane then im plane; one pair per warp (private) or one pair per CTA (atomic)
+    T *re = sm + (PRIVATE ? (size_t)warp * 2 * cells : 0);
+    T *im = re + cells;
+    const int nsub = *nsub_total;
+    for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+        const SubProb P = subs[sp];
+        int origin[D];
+        {
+            int b = P.bin;
+#pragma unroll
+            for (int t = D - 1; t >= 0; t--) {
+                origin[t] = (b % g.nb[t]) * g.bs[t];
+                b /= g.nb[t];
+            }
+        }
+        // first chunk of node data in flight while the tile is cleared
+        Rec r_next;
+        C v_next;
+        if (tid < P.count) {
+            r_next = rec[P.start + tid];
+            v_next = f[perm[P.start + tid]];
+        }
+        if (PRIVATE) {
+            for (int e = lane; e < 2 * cells; e += 32) re[e] = (T)0;
+        } else {
+            for (int e = tid; e < 2 * cells; e += blockDim.x) sm[e] = (T)0;
+        }
+
+        for (int c0 = 0; c0 < P.count; c0 += kSpreadChunk) {
+            const int cnt = min(kSpreadChunk, P.count - c0);
+            if (tid < cnt) {
+                st_rec[tid] = r_next;
+                st_val[tid] = v_next;
+            }
+            __syncthreads();
+            {
+                const int nx = c0 + kSpreadChunk + tid;  // prefetch the next chunk
+                if (nx < P.count) {
+                    r_next = rec[P.start + nx];
+                    v_next = f[perm[P.start + nx]];
+                }
+            }
+            for (int k = warp; k < cnt; k += kSpreadWarps) {
+                const Rec r = st_rec[k];
+                const C v = st_val[k];
+                int cell = r.cell;
+                int loc[D];
+                T frac[D];
+                bool edge = false;
+#pragma unroll
+                for (int t = D - 1; t >= 0; t--) {
+                    loc[t] = (cell & (g.n[t] - 1)) - origin[t];
+                    cell >>= g.nlog[t];
+                    frac[t] = r.fr[t];
+                    edge |= (frac[t] == (T)0);
+                }
+                // lane (t * NT + i) holds psibar of tap i on axis t (two rounds when NW > 32)
+                T wa = (T)0, wb = (T)0;
+                {
+                    const int q = lane;
+                    if (q < NW) {
+                        const int t = q / NT, i = q - (q / NT) * NT;
+                        wa = window_tap<T, MM>(tab + t * AS, i, frac[t], (T)g.win[t].edge_w);
+                    }
+                    const int q2 = lane + 32;
+                    if (NW > 32 && q2 < NW) {
+                        const int t = q2 / NT, i = q2 - (q2 / NT) * NT;
+                        wb = window_tap<T, MM>(tab + t * AS, i, frac[t], (T)g.win[t].edge_w);
+                    }
+                }
+                if (edge)  // warp-uniform (one node per warp)
+                    spread_warp_taps<T, D, MM, PRIVATE, 0>(re, im, tdim, loc, wa, wb, v, lane);
+                else
+                    spread_warp_taps<T, D, MM, PRIVATE, 1>(re, im, tdim, loc, wa, wb, v, lane);
+                if (PRIVATE) __syncwarp();
+            }
+            __syncthreads();
+        }
+        if (P.count == 0) __syncthreads();
+
+        // flush: tile cell (a_0..a_{d-1}) is grid point (origin_t - m + a_t) mod n_t
+        for (int e = tid; e < cells; e += blockDim.x) {
+            T vr, vi;
+            if (PRIVATE) {
+                vr = (T)0;
+                vi = (T)0;
+#pragma unroll
+                for (int w = 0; w < kSpreadWarps; w++) {
+                    vr += sm[(size_t)w * 2 * cells + e];
+                    vi += sm[(size_t)w * 2 * cells + cells + e];
+                }
+            } else {
+                vr = sm[e];
+                vi = sm[cells + e];
+            }
+            if (vr == (T)0 && vi == (T)0) continue;
+            int rem = e;
+            size_t gi = 0;
+            int a[D];
+#pragma unroll
+            for (int t = D - 1; t >= 0; t--) {
+                a[t] = rem % tdim[t];
+                rem /= tdim[t];
+            }
+#pragma unroll
+            for (int t = 0; t < D; t++)
+                gi = (gi << g.nlog[t]) | (size_t)((origin[t] - MM + a[t]) & (g.n[t] - 1));
+            global_add(grid + gi, vr, vi);
+        }
+        __syncthreads();
+    }
+}
+
+// Shared memory left for the dynamic part once the static window tables are placed.
+template <typename T, int MM> constexpr size_t spread_dyn_limit()
+{
+    return 227 * 1024 - kMaxDim * poly_axis_stride(sizeof(T) == 8, MM) * sizeof(T);
+}
+
+template <typename K>
+static cudaError_t launch_persistent(K kernel, size_t smem, int threads, int max_subs, int &blocks)
+{
+    cudaError_t e0 = ensure_dynamic_smem(kernel, smem);
+    if (e0 != cudaSuccess) return e0;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidValue;
+    blocks = num_sms() * per_sm;
+    if (blocks > max_subs) blocks = max_subs;
+    if (blocks < 1) blocks = 1;
+    return cudaSuccess;
+}
+
 template <typename T, int D, int MM>
 cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
                             const typename RecOf<T>::type *rec, const int *perm,
@@ -168,23 +392,41 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
 {
     size_t cells = 1;
     for (int t = 0; t < D; t++) cells *= (size_t)(g.bs[t] + 2 * MM);
-    const size_t smem = cells * 2 * sizeof(T);
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(spread_kernel<T, D, MM>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    const size_t tile = cells * 2 * sizeof(T);
+    int method = g.spread_method;
+    if (method == kSpreadAuto)
+        method = tile * kSpreadWarps <= 64 * 1024 ? kSpreadWarpPrivate : kSpreadWarpAtomic;
+    // a form whose shared memory does not fit falls back to the one-tile form
+    constexpr size_t limit = spread_dyn_limit<T, MM>();
+    if (method == kSpreadWarpPrivate && tile * kSpreadWarps + 16 + spread_stage_bytes<T>() > limit)
+        method = kSpreadWarpAtomic;
+    if (method == kSpreadWarpAtomic && tile + 16 + spread_stage_bytes<T>() > limit)
+        method = kSpreadThread;
+    if (tile > limit) return cudaErrorInvalidValue;
+    int blocks = 0;
+    cudaError_t e;
+    if (method == kSpreadThread) {
+        e = launch_persistent(spread_kernel<T, D, MM>, tile, 256, max_subs, blocks);
         if (e != cudaSuccess) return e;
-    }
-    const int threads = 256;
-    int per_sm = (int)((200 * 1024) / (smem + 1024));
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;
-    int blocks = num_sms() * per_sm;
-    if (blocks > max_subs) blocks = max_subs;
-    if (blocks < 1) blocks = 1;
-    spread_kernel<T, D, MM><<<blocks, threads, smem, stream>>>(g, f, rec, perm, subs, nsub_total,
+        spread_kernel<T, D, MM><<<blocks, 256, tile, stream>>>(g, f, rec, perm, subs, nsub_total,
                                                                grid);
+    } else if (method == kSpreadWarpAtomic) {
+        const size_t smem = (tile + 15) / 16 * 16 + spread_stage_bytes<T>();
+        e = launch_persistent(spread_warp_kernel<T, D, MM, false>, smem, 32 * kSpreadWarps,
+                              max_subs, blocks);
+        if (e != cudaSuccess) return e;
+        spread_warp_kernel<T, D, MM, false><<<blocks, 32 * kSpreadWarps, smem, stream>>>(
+            g, f, rec, perm, subs, nsub_total, grid);
+    } else if (method == kSpreadWarpPrivate) {
+        const size_t smem = (tile * kSpreadWarps + 15) / 16 * 16 + spread_stage_bytes<T>();
+        e = launch_persistent(spread_warp_kernel<T, D, MM, true>, smem, 32 * kSpreadWarps,
+                              max_subs, blocks);
+        if (e != cudaSuccess) return e;
+        spread_warp_kernel<T, D, MM, true><<<blocks, 32 * kSpreadWarps, smem, stream>>>(
+            g, f, rec, perm, subs, nsub_total, grid);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -5,58 +5,85 @@
 //   psibar(t) = psi(t) / psi(0) = kscale * sinh(b u) / u,  kscale = m / sinh(b m).
 //
 // The factor psi(0) moves into the deconvolution table, so sums of products of d weights stay
-// in range in FP32 for every m. Each tap evaluates the window at t = frac + m - i for
-// i = 0..2m; m^2 - t^2 is formed as (i - frac)(2m - i + frac), which has no cancellation near
-// the support edge. i = 0 lies inside the closed support only when frac == 0.
+// in range in FP32 for every m. A node with offset frac has taps t = frac + m - i, i = 0..2m;
+// i = 0 lies inside the closed support only when frac == 0 (value psibar(m) = kscale b). For
+// i = 1..2m the kernels evaluate psibar(frac + m - i) from a per-tap polynomial in frac (the
+// window is an entire function of m^2 - t^2 inside the support, so low degrees suffice); the
+// polynomials are fitted on the host at plan creation (see gbnfft_internal.cuh).
 #pragma once
 
 #include <cuda_runtime.h>
 
+#include "gbnfft_internal.cuh"
+
 namespace gbnfft {
 
-__device__ __forceinline__ float kb_sinh(float z) { return sinhf(z); }
-__device__ __forceinline__ double kb_sinh(double z) { return sinh(z); }
-__device__ __forceinline__ float kb_cosh(float z) { return coshf(z); }
-__device__ __forceinline__ double kb_cosh(double z) { return cosh(z); }
-__device__ __forceinline__ float kb_sqrt(float z) { return sqrtf(z); }
-__device__ __forceinline__ double kb_sqrt(double z) { return sqrt(z); }
+// ------------------------------------------------------------------------ polynomial form
+template <typename T, int MM> struct PolyDeg {
+    static constexpr int value = poly_degree(sizeof(T) == 8, MM);
+};
 
-// psibar at tap i of a node with offset frac (t = frac + m - i).
-template <typename T>
-__device__ __forceinline__ T psibar_tap(int i, int m, T frac, T b, T kscale)
+// All taps of one axis: w[i] = psibar(frac + m - i) for i = START..2m. c is the axis' table
+// (shared or global memory); w[0] (START = 0) is the edge tap, nonzero only when frac == 0.
+template <typename T, int MM, int START>
+__device__ __forceinline__ void window_taps(const T *__restrict__ c, T frac, T edge_w, T *w)
 {
-    const T s = ((T)i - frac) * ((T)(2 * m - i) + frac);  // m^2 - t^2
-    if (s > (T)0) {
-        const T u = kb_sqrt(s);
-        return kscale * kb_sinh(b * u) / u;
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    const T z = (T)2 * frac - (T)1;
+#pragma unroll
+    for (int i = 1; i <= 2 * MM; i++) w[i] = c[DEG * kPolyTaps + i - 1];
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; k--) {
+#pragma unroll
+        for (int i = 1; i <= 2 * MM; i++) w[i] = fma(w[i], z, c[k * kPolyTaps + i - 1]);
     }
-    return s == (T)0 ? kscale * b : (T)0;  // limit sinh(b u)/u -> b at the edge
+    if (START == 0) w[0] = frac == (T)0 ? edge_w : (T)0;
 }
 
-// d psibar / dt at tap i:  -kscale * t * (b u cosh(b u) - sinh(b u)) / u^3.
-// For small z = b u the bracket over u^3 is b^3/3 (1 + z^2/10 + z^4/280 + z^6/15120) (its
-// Taylor series); the switch point keeps both branches accurate in the given precision.
-template <typename T> struct DpsiSwitch;
-template <> struct DpsiSwitch<float> { static constexpr float z = 0.5f; };
-template <> struct DpsiSwitch<double> { static constexpr double z = 0.05; };
-
-template <typename T>
-__device__ __forceinline__ T dpsibar_tap(int i, int m, T frac, T b, T kscale)
+// One tap i (0..2m) of one axis.
+template <typename T, int MM>
+__device__ __forceinline__ T window_tap(const T *__restrict__ c, int i, T frac, T edge_w)
 {
-    const T s = ((T)i - frac) * ((T)(2 * m - i) + frac);
-    if (s < (T)0) return (T)0;
-    const T t = (T)(m - i) + frac;
-    const T u = kb_sqrt(s);
-    const T z = b * u;
-    T g;
-    if (z < DpsiSwitch<T>::z) {
-        const T z2 = z * z;
-        g = b * b * b / (T)3 *
-            ((T)1 + z2 * ((T)0.1 + z2 * ((T)1 / (T)280 + z2 * ((T)1 / (T)15120))));
-    } else {
-        g = (z * kb_cosh(z) - kb_sinh(z)) / (u * u * u);
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    if (i == 0) return frac == (T)0 ? edge_w : (T)0;
+    const T z = (T)2 * frac - (T)1;
+    T acc = c[DEG * kPolyTaps + i - 1];
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; k--) acc = fma(acc, z, c[k * kPolyTaps + i - 1]);
+    return acc;
+}
+
+// Value and t-derivative of one tap: d psibar / dt = d P / d frac = 2 dP/dz.
+template <typename T, int MM>
+__device__ __forceinline__ void window_tap_d(const T *__restrict__ c, int i, T frac, T edge_w,
+                                             T edge_dw, T &w, T &dw)
+{
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    if (i == 0) {
+        const bool on = frac == (T)0;
+        w = on ? edge_w : (T)0;
+        dw = on ? edge_dw : (T)0;
+        return;
     }
-    return -kscale * t * g;
+    const T z = (T)2 * frac - (T)1;
+    T p = c[DEG * kPolyTaps + i - 1], dp = (T)0;
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; k--) {
+        dp = fma(dp, z, p);
+        p = fma(p, z, c[k * kPolyTaps + i - 1]);
+    }
+    w = p;
+    dw = (T)2 * dp;
+}
+
+// Copy the window tables (d axes) into shared memory; every thread of the CTA must call it.
+template <typename T, int MM>
+__device__ __forceinline__ void load_window_tables(T *dst, const void *src, int d)
+{
+    const T *s = static_cast<const T *>(src);
+    const int n = d * poly_axis_stride(sizeof(T) == 8, MM);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) dst[e] = s[e];
+    __syncthreads();
 }
 
 }  // namespace gbnfft

@@ -106,6 +106,37 @@ class Plan:
             pass
 
     # ------------------------------------------------------------------ API
+    def set_option(self, key: str, value) -> None:
+        """Tuning: ``spread_method`` in {auto, thread, warp_atomic, warp_private},
+        ``interp_method`` in {auto, thread, warp}, or
+        ``bin0`` / ``bin1`` / ``bin2`` (power-of-two bin sizes). Changing a bin size discards the
+        node precomputation; set the nodes again afterwards."""
+        L = _lib.lib()
+        if key == "spread_method":
+            check(L.nfft_set_option(self._h, _lib.OPT_SPREAD_METHOD,
+                                    _lib.SPREAD_METHODS[value]), "nfft_set_option")
+            return
+        if key == "interp_method":
+            check(L.nfft_set_option(self._h, _lib.OPT_INTERP_METHOD,
+                                    _lib.INTERP_METHODS[value]), "nfft_set_option")
+            return
+        if key in ("bin0", "bin1", "bin2"):
+            t = int(key[-1])
+            check(L.nfft_set_option(self._h, _lib.OPT_BIN[t], int(value)), "nfft_set_option")
+            info = _lib.NfftInfo()
+            check(L.nfft_get_info(self._h, ctypes.byref(info)), "nfft_get_info")
+            self.bin = tuple(int(info.bin[u]) for u in range(self.d))
+            self.workspace_bytes = int(info.workspace_bytes)
+            if self.workspace_bytes > self._ws.numel():
+                torch.cuda.current_stream(self.device).synchronize()
+                self._ws = torch.empty(self.workspace_bytes, dtype=torch.uint8,
+                                       device=self.device)
+                check(L.nfft_set_workspace(self._h, _ptr(self._ws), self._ws.numel()),
+                      "nfft_set_workspace")
+            self._nodes_key = None
+            return
+        raise KeyError(key)
+
     def set_nodes(self, x: torch.Tensor) -> None:
         """Precompute for the nodes x (shape (M, d), plan dtype, on the plan's device)."""
         if x.device != self.device or x.dtype != self.dtype:

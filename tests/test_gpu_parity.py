@@ -17,9 +17,13 @@ pytestmark = pytest.mark.gpu
 DTYPES = [torch.float64, torch.float32]
 
 
-def _run(N, n, m, x, fh, f, dtype):
+def _run(N, n, m, x, fh, f, dtype, interp=None, spread=None):
     M = x.shape[0]
     plan = Plan(N, M, n=n, m=m, dtype=dtype, device=DEV)
+    if interp:
+        plan.set_option("interp_method", interp)
+    if spread:
+        plan.set_option("spread_method", spread)
     plan.set_nodes(to_dev(x, dtype))
     out_f = plan.trafo(to_dev(fh, dtype)).cpu().numpy()
     out_h = plan.adjoint(to_dev(f, dtype)).cpu().numpy()
@@ -77,14 +81,16 @@ def test_uniform_nodes(N, n, m, M, dtype):
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("d", [1, 2, 3])
 @pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 6, 7, 8])
-def test_every_window_cutoff(d, m, dtype):
+@pytest.mark.parametrize("forms", [("thread", "thread"), ("warp", "warp_atomic"),
+                                   ("warp", "warp_private")])
+def test_every_window_cutoff(d, m, dtype, forms):
     N = {1: (40,), 2: (20, 24), 3: (12, 8, 10)}[d]
     n = {1: (128,), 2: (64, 64), 3: (32, 32, 32)}[d]
     M = 1500
     x = W.uniform_nodes(M, d, seed_offset=400 + m)
     fh = W.gaussian_fhat(N, seed_offset=401 + m)
     f = W.gaussian_values(M, seed_offset=402 + m)
-    out_f, ref_f, out_h, ref_h, *_ = _run(N, n, m, x, fh, f, dtype)
+    out_f, ref_f, out_h, ref_h, *_ = _run(N, n, m, x, fh, f, dtype, *forms)
     tol = TOL[dtype] if (dtype == torch.float64 or m <= 6) else 3e-5
     assert rel_l2(out_f, ref_f) <= tol
     assert rel_l2(out_h, ref_h) <= tol
@@ -92,7 +98,9 @@ def test_every_window_cutoff(d, m, dtype):
 
 @pytest.mark.parametrize("dtype", DTYPES)
 @pytest.mark.parametrize("d", [1, 2, 3])
-def test_nodes_on_grid_points_and_edges(d, dtype):
+@pytest.mark.parametrize("forms", [("thread", "thread"), ("warp", "warp_atomic"),
+                                   ("warp", "warp_private")])
+def test_nodes_on_grid_points_and_edges(d, dtype, forms):
     """Nodes exactly on grid points (2m+1 taps), at -1/2, coincident nodes, and nodes outside
     the torus (any real is taken modulo 1)."""
     N = {1: (32,), 2: (16, 24), 3: (8, 12, 8)}[d]
@@ -110,7 +118,7 @@ def test_nodes_on_grid_points_and_edges(d, dtype):
     ])
     fh = W.gaussian_fhat(N, seed_offset=11)
     f = W.gaussian_values(x.shape[0], seed_offset=12)
-    out_f, ref_f, out_h, ref_h, *_ = _run(N, n, m, x, fh, f, dtype)
+    out_f, ref_f, out_h, ref_h, *_ = _run(N, n, m, x, fh, f, dtype, *forms)
     assert rel_l2(out_f, ref_f) <= TOL[dtype]
     assert rel_l2(out_h, ref_h) <= TOL[dtype]
 

@@ -1,0 +1,141 @@
+"""GPU parity on the workloads the benchmark times: the 2-D golden-angle radial trajectory
+(coincident nodes at the origin, density ~ 1/r) and the 3-D clustered node set, at reduced sizes
+element by element for every spreading method, and at full size on sampled outputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1810_09891_gb300 import workloads as W
+from paper_1810_09891_gb300.nfft import Plan
+
+from gpu_helpers import DEV, TOL, rel_l2, rounded, to_dev
+
+pytestmark = pytest.mark.gpu
+
+METHODS = ["thread", "warp_atomic", "warp_private"]
+INTERP = ["thread", "warp"]
+
+
+def _plan(N, n, m, M, dtype, method=None, bins=None, interp=None):
+    plan = Plan(N, M, n=n, m=m, dtype=dtype, device=DEV)
+    if method:
+        plan.set_option("spread_method", method)
+    if interp:
+        plan.set_option("interp_method", interp)
+    for t, b in enumerate(bins or ()):
+        plan.set_option(f"bin{t}", b)
+    return plan
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("interp", INTERP)
+@pytest.mark.parametrize("m", [4, 6])
+def test_radial_reduced(dtype, method, interp, m):
+    N = (128, 128)
+    n = (256, 256)
+    x = W.round_nodes(W.radial_nodes(64, 512), np.float32 if dtype == torch.float32 else
+                      np.float64)
+    M = x.shape[0]
+    fh = W.gaussian_fhat(N, 600)
+    f = W.gaussian_values(M, 601)
+    plan = _plan(N, n, m, M, dtype, method, interp=interp)
+    plan.set_nodes(to_dev(x, dtype))
+    yf = plan.trafo(to_dev(fh, dtype)).cpu().numpy()
+    yh = plan.adjoint(to_dev(f, dtype)).cpu().numpy()
+    assert plan.status() == 0
+    xr, fhr, fr = rounded(x, dtype), rounded(fh, dtype), rounded(f, dtype)
+    assert rel_l2(yf, oracle.nfft(xr, fhr, n=n, m=m)) <= TOL[dtype]
+    assert rel_l2(yh, oracle.nfft_adjoint(xr, fr, N, n=n, m=m)) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("interp", INTERP)
+def test_clusters_reduced(dtype, method, interp):
+    N = (32, 32, 32)
+    n = (64, 64, 64)
+    m = 4
+    x = W.round_nodes(W.clustered_nodes(120000, 3, seed_offset=602),
+                      np.float32 if dtype == torch.float32 else np.float64)
+    M = x.shape[0]
+    fh = W.gaussian_fhat(N, 603)
+    f = W.gaussian_values(M, 604)
+    plan = _plan(N, n, m, M, dtype, method, interp=interp)
+    plan.set_nodes(to_dev(x, dtype))
+    yf = plan.trafo(to_dev(fh, dtype)).cpu().numpy()
+    yh = plan.adjoint(to_dev(f, dtype)).cpu().numpy()
+    assert plan.status() == 0
+    xr, fhr, fr = rounded(x, dtype), rounded(fh, dtype), rounded(f, dtype)
+    idx = np.arange(0, M, 7)
+    assert rel_l2(yf[idx], oracle.nfft(xr[idx], fhr, n=n, m=m)) <= TOL[dtype]
+    assert rel_l2(yh, oracle.nfft_adjoint(xr, fr, N, n=n, m=m)) <= TOL[dtype]
+
+
+def test_bin_size_too_large_for_shared_memory_is_rejected():
+    from paper_1810_09891_gb300._lib import NfftError
+    plan = Plan((64, 64), 10, n=(128, 128), m=4, dtype=torch.float64, device=DEV)
+    plan.set_option("bin0", 128)
+    with pytest.raises(NfftError, match="NFFT_EINVAL"):
+        plan.set_option("bin1", 128)  # (128 + 8)^2 complex128 > 227 KB
+
+
+@pytest.mark.parametrize("bins", [(4, 64), (64, 8), (32, 64), (1, 1)])
+def test_bin_sizes(bins):
+    """Any power-of-two bin size gives the same transform (only the work split changes)."""
+    N, n, m = (64, 64), (128, 128), 4
+    x = W.radial_nodes(32, 256)
+    M = x.shape[0]
+    fh = W.gaussian_fhat(N, 605)
+    f = W.gaussian_values(M, 606)
+    for method in METHODS:
+        plan = _plan(N, n, m, M, torch.float64, method, bins)
+        assert plan.bin == tuple(min(b, v) for b, v in zip(bins, n))
+        plan.set_nodes(to_dev(x, torch.float64))
+        yf = plan.trafo(to_dev(fh, torch.float64)).cpu().numpy()
+        yh = plan.adjoint(to_dev(f, torch.float64)).cpu().numpy()
+        assert rel_l2(yf, oracle.nfft(x, fh, n=n, m=m)) <= 1e-12
+        assert rel_l2(yh, oracle.nfft_adjoint(x, f, N, n=n, m=m)) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_radial_full_size(dtype):
+    """N = (512, 512), n = (1024, 1024), m = 4, M = 1,048,576 radial nodes, the benchmark's
+    launch configuration: forward on 4096 sampled nodes, adjoint on every coefficient."""
+    c = W.config_radial(m=4, dtype=np.float32 if dtype == torch.float32 else np.float64)
+    M = c["x"].shape[0]
+    plan = Plan(c["N"], M, n=c["n"], m=4, dtype=dtype, device=DEV)
+    plan.set_nodes(to_dev(c["x"], dtype))
+    yf = plan.trafo(to_dev(c["fhat"], dtype)).cpu().numpy()
+    yh = plan.adjoint(to_dev(c["f"], dtype)).cpu().numpy()
+    assert plan.status() == 0
+    xr, fhr, fr = rounded(c["x"], dtype), rounded(c["fhat"], dtype), rounded(c["f"], dtype)
+    idx = np.sort(np.random.default_rng(1).choice(M, 4096, replace=False))
+    idx[0] = 1024  # spoke 0, sample 1024: the origin, shared by every spoke
+    assert rel_l2(yf[idx], oracle.nfft(xr[idx], fhr, n=c["n"], m=4)) <= TOL[dtype]
+    assert rel_l2(yh, oracle.nfft_adjoint(xr, fr, c["N"], n=c["n"], m=4)) <= TOL[dtype]
+
+
+def test_clusters_full_size_fp32():
+    """N = (128,)*3, n = 2N, m = 4, M = 4,194,304 clustered nodes, FP32: forward on sampled nodes;
+    adjoint of a vector that is zero except on a 20000-node sample (the full plan spreads all
+    M nodes), against the oracle adjoint of the sample."""
+    c = W.config_clusters(dtype=np.float32)
+    M = c["x"].shape[0]
+    plan = Plan(c["N"], M, n=c["n"], m=4, dtype=torch.float32, device=DEV)
+    plan.set_nodes(to_dev(c["x"], torch.float32))
+    yf = plan.trafo(to_dev(c["fhat"], torch.float32)).cpu().numpy()
+    rng = np.random.default_rng(2)
+    idx = np.sort(rng.choice(M, 20000, replace=False))
+    fz = np.zeros(M, dtype=np.complex128)
+    fz[idx] = c["f"][idx]
+    yh = plan.adjoint(to_dev(fz, torch.float32)).cpu().numpy()
+    assert plan.status() == 0
+    xr = rounded(c["x"], torch.float32)
+    fhr = rounded(c["fhat"], torch.float32)
+    fr = rounded(fz, torch.float32)
+    s = idx[:4096]
+    assert rel_l2(yf[s], oracle.nfft(xr[s], fhr, n=c["n"], m=4)) <= TOL[torch.float32]
+    assert rel_l2(yh, oracle.nfft_adjoint(xr[idx], fr[idx], c["N"], n=c["n"], m=4)) <= \
+        TOL[torch.float32]
