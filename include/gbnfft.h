@@ -61,7 +61,8 @@ enum nfft_status_code {
     NFFT_ENOTREADY = 4,   /* a transform was requested before nfft_set_nodes */
     NFFT_EBADNODE = 5,    /* a node coordinate was NaN, infinite or too large (|n x| >= 2^52) */
     NFFT_ETIMEOUT = 6,    /* reserved: a bounded device-side wait gave up */
-    NFFT_EUNSUPPORTED = 7 /* valid for the paper's method but not built here (see below) */
+    NFFT_EUNSUPPORTED = 7, /* valid for the paper's method but not built here (see below) */
+    NFFT_ESCRATCH = 8      /* larger than the fixed scratch of nfft_trafo_1d_noalloc */
 };
 
 /* Plan creation: Section 3.1, Table tab:params (N, M, n, m) plus the precision.
@@ -184,6 +185,35 @@ const char *nfft_strerror(int code);
 /* Make `device` the calling thread's current CUDA device for this library (the device that the
  * next nfft_plan_create binds). */
 int nfft_use_device(int device);
+
+/* Forward 1-D NFFT in FP64 that allocates no device memory (the paper has no counterpart: its
+ * library always allocates through its plan).
+ *
+ * For callers that must not call cudaMalloc where they transform: code running while a CUDA
+ * graph is captured, code whose device memory belongs to another allocator, and latency-bound
+ * loops that cannot take the device synchronisation that cudaMalloc / cudaFree imply. The
+ * planned path cannot serve them, because nfft_plan_create and nfft_set_nodes allocate.
+ *
+ * Computes f_j ~ sum_{k=-N/2}^{N/2-1} fhat_k e^{-2 pi i k x_j} (Algorithm "NFFT", d = 1), the
+ * same transform as nfft_trafo on a 1-D NFFT_FP64 plan with the same N, n, m, up to rounding.
+ *   N       even bandwidth, 2 <= N <= 4096.
+ *   M       number of nodes, 0 <= M < 2^31.
+ *   n       pointer to the FFT length (power of two, N < n <= 8192, 2m + 2 <= n), or NULL for
+ *           the default 2^(ceil(log2 N) + 1).
+ *   m       window cutoff 1..8 (<= 0 selects 8).
+ *   x       M node coordinates (device, FP64, any finite real, taken mod 1).
+ *   fhat    N complex128 coefficients, index k + N/2 (device, 16-byte aligned).
+ *   f       M complex128 outputs (device, 16-byte aligned); a non-finite node gives NaN.
+ *   stream  cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Scratch: a fixed 288 KiB array in device memory inside the library, held by every GPU that
+ * loads the library until the process exits. Sizes beyond it (n > 8192 or N > 4096) return
+ * NFFT_ESCRATCH. Nothing in it has to start at zero: each call rewrites what it reads. All calls
+ * share the array: calls that overlap on the GPU (other streams, other threads) race and give
+ * wrong results, so serialise them.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture begins. Returns without waiting for the GPU. */
+int nfft_trafo_1d_noalloc(int64_t N, int64_t M, const int64_t *n, int m, const double *x,
+                          const void *fhat, void *f, void *stream);
 
 #ifdef __cplusplus
 }

@@ -25,6 +25,7 @@ STATUS = {
     5: "NFFT_EBADNODE",
     6: "NFFT_ETIMEOUT",
     7: "NFFT_EUNSUPPORTED",
+    8: "NFFT_ESCRATCH",
 }
 
 # Every symbol include/gbnfft.h declares, with (argtypes, restype).
@@ -68,6 +69,7 @@ SIGNATURES = {
     "nfft_set_option": ([_P, _I, _I64], _I),
     "nfft_profile": ([_P, _I], _I),
     "nfft_profile_read": ([_P, ctypes.POINTER(ctypes.c_double), _PI64, _I], _I),
+    "nfft_trafo_1d_noalloc": ([_I64, _I64, _PI64, _I, _P, _P, _P, _P], _I),
 }
 
 OPT_SPREAD_METHOD = 1

@@ -427,6 +427,7 @@ const char *nfft_strerror(int code)
     case NFFT_EBADNODE: return "a node coordinate is NaN, infinite or out of range";
     case NFFT_ETIMEOUT: return "a device-side wait timed out";
     case NFFT_EUNSUPPORTED: return "parameters valid but not supported by this build";
+    case NFFT_ESCRATCH: return "problem larger than the fixed scratch of the no-allocation entry point";
     default: return "unknown error";
     }
 }
