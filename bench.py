@@ -118,8 +118,8 @@ STAGE_SOURCES = {
                "paper_1810_09891_gb300/csrc/window.cuh"],
     "interp": ["paper_1810_09891_gb300/csrc/interp_impl.cuh",
                "paper_1810_09891_gb300/csrc/window.cuh"],
-    "fft_forward": ["paper_1810_09891_gb300/csrc/fft.cu"],
-    "fft_adjoint": ["paper_1810_09891_gb300/csrc/fft.cu"],
+    "fft_forward": ["paper_1810_09891_gb300/csrc/fft_impl.cuh"],
+    "fft_adjoint": ["paper_1810_09891_gb300/csrc/fft_impl.cuh"],
 }
 
 

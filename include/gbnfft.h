@@ -164,7 +164,9 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *   NFFT_OPT_SPREAD_METHOD  0 automatic, 1 one thread per node with shared-memory atomics,
  *                           2 one warp per node with shared-memory atomics,
  *                           3 one warp per node with a private tile per warp (no atomics).
- *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node, 2 one warp per node.
+ *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node (gathers from the grid),
+ *                           2 one warp per node, 3 one thread per node gathering from a
+ *                           shared-memory tile of the node's bin.
  *   NFFT_OPT_BIN_0..2       bin (tile) size on axis 0..d-1: a power of two, 0 = default.
  *                           Changing a bin size discards the node precomputation (call
  *                           nfft_set_nodes again) and may change nfft_workspace_size: a

@@ -1,0 +1,7 @@
+// Instantiation unit: FFT axis passes, double.
+#include "fft_impl.cuh"
+
+namespace gbnfft {
+template cudaError_t launch_fft_axis<double>(const double2 *, double2 *, int64_t, int64_t, int, int, bool, int,
+                                         const double2 *, const double *, cudaStream_t);
+}  // namespace gbnfft

@@ -55,6 +55,7 @@ constexpr int kSpreadWarpPrivate = 3;
 constexpr int kInterpAuto = 0;
 constexpr int kInterpThread = 1;
 constexpr int kInterpWarp = 2;
+constexpr int kInterpTile = 3;
 
 // Geometry passed by value to every kernel.
 struct Geom {
@@ -121,6 +122,7 @@ cudaError_t launch_fill_subprobs(const int *bin_count, const int *bin_start, con
 
 // One axis pass of the pruned d-variate FFT.
 //   in  : [outer][Lin][inner]   out : [outer][Lout][inner]
+//   deconv: the per-axis factors, computed in FP64 and stored in the plan's precision.
 //   pad  (forward, D fused): Lin = N_t, Lout = L = n_t; input index i (k = i - N_t/2) lands at
 //        FFT position k mod n_t after multiplication by deconv[i]; other positions are zero.
 //   crop (adjoint, D^H fused): Lin = L = n_t, Lout = N_t; output i takes FFT position
@@ -129,13 +131,15 @@ cudaError_t launch_fill_subprobs(const int *bin_count, const int *bin_start, con
 template <typename T>
 cudaError_t launch_fft_axis(const typename Cplx<T>::type *in, typename Cplx<T>::type *out,
                             int64_t outer, int64_t inner, int L, int Nt, bool pad_mode, int sign,
-                            const typename Cplx<T>::type *twiddle, const double *deconv,
+                            const typename Cplx<T>::type *twiddle, const T *deconv,
                             cudaStream_t stream);
 
-// B: f[perm[s]] = sum over taps of grid * prod psibar.
+// B: f[perm[s]] = sum over taps of grid * prod psibar. The tiled form walks the subproblem list
+// built by set_nodes (subs, nsub_total, at most max_subs entries).
 template <typename T>
 cudaError_t launch_interp(const Geom &g, const typename Cplx<T>::type *grid,
                           const typename RecOf<T>::type *rec, const int *perm, int64_t M,
+                          const SubProb *subs, const int *nsub_total, int max_subs,
                           typename Cplx<T>::type *f, cudaStream_t stream);
 
 // B^H: grid += spread of f over subproblems (grid must be zeroed first).
@@ -180,6 +184,7 @@ namespace detail {
 template <typename T, int D>
 cudaError_t interp_d(const Geom &g, const typename Cplx<T>::type *grid,
                      const typename RecOf<T>::type *rec, const int *perm, int64_t M,
+                     const SubProb *subs, const int *nsub_total, int max_subs,
                      typename Cplx<T>::type *f, cudaStream_t stream);
 template <typename T, int D>
 cudaError_t grad_d(const Geom &g, const typename Cplx<T>::type *grid,

@@ -133,6 +133,167 @@ __global__ void __launch_bounds__(kInterpThreads)
     f[perm[s]] = v;
 }
 
+
+// ------------------------------------------------------------------------- tiled form of B
+// One CTA per subproblem (up to kMaxSub sorted nodes of one bin, the list built by set_nodes):
+// the bin's grid tile plus a halo of m cells per side is staged in shared memory with
+// row-coalesced loads, then every thread interpolates its nodes from the tile. Gathers from
+// shared memory replace the scattered L1 sector lookups of the thread form.
+constexpr int kInterpTileThreads = 256;
+
+template <typename T, int D, int MM, int START>
+__device__ __forceinline__ typename Cplx<T>::type
+interp_tile_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::type *tile,
+                 const int *st, const int *loc, const T *frac)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int NT = 2 * MM + 1;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    C acc;
+    acc.x = (T)0;
+    acc.y = (T)0;
+    if (D == 1) {
+        T w0[NT];
+        window_taps<T, MM, START>(tab, frac[0], (T)g.win[0].edge_w, w0);
+        const C *row = tile + loc[0];
+#pragma unroll
+        for (int i = START; i < NT; i++) {
+            const C v = row[i];
+            acc.x += v.x * w0[i];
+            acc.y += v.y * w0[i];
+        }
+    } else if (D == 2) {
+        T w1[NT];
+        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
+        for (int i0 = START; i0 < NT; i0++) {
+            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
+            const C *row = tile + (loc[0] + i0) * st[0] + loc[1];
+            C in;
+            in.x = (T)0;
+            in.y = (T)0;
+#pragma unroll
+            for (int i1 = START; i1 < NT; i1++) {
+                const C v = row[i1];
+                in.x += v.x * w1[i1];
+                in.y += v.y * w1[i1];
+            }
+            acc.x += in.x * w0;
+            acc.y += in.y * w0;
+        }
+    } else {
+        T w1[NT], w2[NT];
+        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
+        window_taps<T, MM, START>(tab + 2 * AS, frac[2], (T)g.win[2].edge_w, w2);
+        for (int i0 = START; i0 < NT; i0++) {
+            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
+            const C *plane = tile + (loc[0] + i0) * st[0];
+            C pl;
+            pl.x = (T)0;
+            pl.y = (T)0;
+#pragma unroll
+            for (int i1 = START; i1 < NT; i1++) {
+                const C *row = plane + (loc[1] + i1) * st[1] + loc[2];
+                C in;
+                in.x = (T)0;
+                in.y = (T)0;
+#pragma unroll
+                for (int i2 = START; i2 < NT; i2++) {
+                    const C v = row[i2];
+                    in.x += v.x * w2[i2];
+                    in.y += v.y * w2[i2];
+                }
+                pl.x += in.x * w1[i1];
+                pl.y += in.y * w1[i1];
+            }
+            acc.x += pl.x * w0;
+            acc.y += pl.y * w0;
+        }
+    }
+    return acc;
+}
+
+template <typename T, int D, int MM>
+__global__ void __launch_bounds__(kInterpTileThreads)
+    interp_tile_kernel(Geom g, const typename Cplx<T>::type *__restrict__ grid,
+                       const typename RecOf<T>::type *__restrict__ rec,
+                       const int *__restrict__ perm, const SubProb *__restrict__ subs,
+                       const int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ f)
+{
+    using C = typename Cplx<T>::type;
+    __shared__ __align__(16) T tab[kMaxDim * poly_axis_stride(sizeof(T) == 8, MM)];
+    load_window_tables<T, MM>(tab, g.poly, D);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *tile = reinterpret_cast<C *>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NWARP = kInterpTileThreads / 32;
+    int tdim[D], st[D];
+    int cells = 1;
+#pragma unroll
+    for (int t = 0; t < D; t++) {
+        tdim[t] = g.bs[t] + 2 * MM;
+        cells *= tdim[t];
+    }
+    st[D - 1] = 1;
+#pragma unroll
+    for (int t = D - 2; t >= 0; t--) st[t] = st[t + 1] * tdim[t + 1];
+    const int rows = cells / tdim[D - 1];
+    const int nsub = *nsub_total;
+    for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+        const SubProb P = subs[sp];
+        int origin[D];
+        {
+            int b = P.bin;
+#pragma unroll
+            for (int t = D - 1; t >= 0; t--) {
+                origin[t] = (b % g.nb[t]) * g.bs[t];
+                b /= g.nb[t];
+            }
+        }
+        // stage the tile: cell (a_0..a_{d-1}) holds grid point (origin_t - m + a_t) mod n_t
+        for (int row = warp; row < rows; row += NWARP) {
+            size_t gbase = 0;
+            {
+                int rem = row;
+                int a[D];
+                a[D - 1] = 0;
+#pragma unroll
+                for (int t = D - 2; t >= 0; t--) {
+                    a[t] = rem % tdim[t];
+                    rem /= tdim[t];
+                }
+#pragma unroll
+                for (int t = 0; t < D - 1; t++)
+                    gbase = (gbase << g.nlog[t]) |
+                            (size_t)((origin[t] - MM + a[t]) & (g.n[t] - 1));
+                gbase <<= g.nlog[D - 1];
+            }
+            for (int a = lane; a < tdim[D - 1]; a += 32)
+                tile[row * tdim[D - 1] + a] =
+                    grid[gbase | (size_t)((origin[D - 1] - MM + a) & (g.n[D - 1] - 1))];
+        }
+        __syncthreads();
+        for (int k = tid; k < P.count; k += kInterpTileThreads) {
+            const int s = P.start + k;
+            const typename RecOf<T>::type r = rec[s];
+            int cell = r.cell;
+            int loc[D];
+            T frac[D];
+            bool edge = false;
+#pragma unroll
+            for (int t = D - 1; t >= 0; t--) {
+                loc[t] = (cell & (g.n[t] - 1)) - origin[t];  // in [0, bs_t)
+                cell >>= g.nlog[t];
+                frac[t] = r.fr[t];
+                edge |= (frac[t] == (T)0);
+            }
+            const C v = edge ? interp_tile_node<T, D, MM, 0>(g, tab, tile, st, loc, frac)
+                             : interp_tile_node<T, D, MM, 1>(g, tab, tile, st, loc, frac);
+            f[perm[s]] = v;
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------------- warp form of B
 // One warp per node: the lanes cover the node's taps (last axis fastest, so a warp load touches
 // a few contiguous grid rows instead of 32 scattered ones), each per-axis window value is
@@ -354,11 +515,30 @@ __global__ void __launch_bounds__(kInterpThreads)
 template <typename T, int D, int MM>
 cudaError_t launch_interp_m(const Geom &g, const typename Cplx<T>::type *grid,
                             const typename RecOf<T>::type *rec, const int *perm, int64_t M,
+                            const SubProb *subs, const int *nsub_total, int max_subs,
                             typename Cplx<T>::type *f, cudaStream_t stream)
 {
+    using C = typename Cplx<T>::type;
+    size_t cells = 1;
+    for (int t = 0; t < D; t++) cells *= (size_t)(g.bs[t] + 2 * MM);
+    const size_t tile = cells * sizeof(C);
+    constexpr size_t tables = kMaxDim * poly_axis_stride(sizeof(T) == 8, MM) * sizeof(T);
     int method = g.interp_method;
-    if (method == kInterpAuto) method = kInterpThread;
-    if (method == kInterpWarp) {
+    if (method == kInterpAuto) method = kInterpThread;  // measured fastest on the GB300
+    if (method == kInterpTile && tile + tables > 227 * 1024) method = kInterpThread;
+    if (method == kInterpTile) {
+        cudaError_t e = ensure_dynamic_smem(interp_tile_kernel<T, D, MM>, tile);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, interp_tile_kernel<T, D, MM>,
+                                                          kInterpTileThreads, tile);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidValue;
+        int blocks = num_sms() * per_sm;
+        if (blocks > max_subs) blocks = max_subs;
+        interp_tile_kernel<T, D, MM><<<blocks, kInterpTileThreads, tile, stream>>>(
+            g, grid, rec, perm, subs, nsub_total, f);
+    } else if (method == kInterpWarp) {
         const int64_t blocks = (M + kInterpWarps - 1) / kInterpWarps;
         interp_warp_kernel<T, D, MM><<<(unsigned)blocks, 32 * kInterpWarps, 0, stream>>>(
             g, grid, rec, perm, (int)M, f);
@@ -384,9 +564,11 @@ cudaError_t launch_grad_m(const Geom &g, const typename Cplx<T>::type *grid,
 template <typename T, int D>
 cudaError_t interp_d(const Geom &g, const typename Cplx<T>::type *grid,
                      const typename RecOf<T>::type *rec, const int *perm, int64_t M,
+                     const SubProb *subs, const int *nsub_total, int max_subs,
                      typename Cplx<T>::type *f, cudaStream_t stream)
 {
-    GBNFFT_DISPATCH_M(launch_interp_m, T, D, g, grid, rec, perm, M, f, stream)
+    GBNFFT_DISPATCH_M(launch_interp_m, T, D, g, grid, rec, perm, M, subs, nsub_total, max_subs,
+                      f, stream)
 }
 
 template <typename T, int D>

@@ -3,6 +3,6 @@
 
 namespace gbnfft {
 namespace detail {
-template cudaError_t interp_d<float, 3>(const Geom &, const float2 *, const RecF *, const int *, int64_t, float2 *, cudaStream_t);
+template cudaError_t interp_d<float, 3>(const Geom &, const float2 *, const RecF *, const int *, int64_t, const SubProb *, const int *, int, float2 *, cudaStream_t);
 }  // namespace detail
 }  // namespace gbnfft

@@ -132,7 +132,7 @@ struct gbnfft_plan {
     int64_t bin_req[3] = {0, 0, 0};  // requested bin sizes (0 = default)
     // plan-owned device tables
     void *tables = nullptr;
-    double *deconv[3] = {nullptr, nullptr, nullptr};
+    void *deconv[3] = {nullptr, nullptr, nullptr};  // plan precision
     void *tw[3] = {nullptr, nullptr, nullptr};
     int *d_status = nullptr;
     // workspace
@@ -282,19 +282,19 @@ template <typename T> int forward_grid(gbnfft_plan *p, const void *fhat)
     cudaStream_t s = p->stream;
     if (p->d == 1) {
         GB_CHECK(launch_fft_axis<T>(in, A, 1, 1, (int)n[0], (int)N[0], true, -1, tw(0),
-                                    p->deconv[0], s));
+                                    static_cast<const T *>(p->deconv[0]), s));
     } else if (p->d == 2) {
         GB_CHECK(launch_fft_axis<T>(in, B, N[0], 1, (int)n[1], (int)N[1], true, -1, tw(1),
-                                    p->deconv[1], s));
+                                    static_cast<const T *>(p->deconv[1]), s));
         GB_CHECK(launch_fft_axis<T>(B, A, 1, n[1], (int)n[0], (int)N[0], true, -1, tw(0),
-                                    p->deconv[0], s));
+                                    static_cast<const T *>(p->deconv[0]), s));
     } else {
         GB_CHECK(launch_fft_axis<T>(in, A, N[0] * N[1], 1, (int)n[2], (int)N[2], true, -1, tw(2),
-                                    p->deconv[2], s));
+                                    static_cast<const T *>(p->deconv[2]), s));
         GB_CHECK(launch_fft_axis<T>(A, B, N[0], n[2], (int)n[1], (int)N[1], true, -1, tw(1),
-                                    p->deconv[1], s));
+                                    static_cast<const T *>(p->deconv[1]), s));
         GB_CHECK(launch_fft_axis<T>(B, A, 1, n[1] * n[2], (int)n[0], (int)N[0], true, -1, tw(0),
-                                    p->deconv[0], s));
+                                    static_cast<const T *>(p->deconv[0]), s));
     }
     return NFFT_OK;
 }
@@ -310,19 +310,19 @@ template <typename T> int adjoint_grid(gbnfft_plan *p, void *fhat)
     cudaStream_t s = p->stream;
     if (p->d == 1) {
         GB_CHECK(launch_fft_axis<T>(A, out, 1, 1, (int)n[0], (int)N[0], false, +1, tw(0),
-                                    p->deconv[0], s));
+                                    static_cast<const T *>(p->deconv[0]), s));
     } else if (p->d == 2) {
         GB_CHECK(launch_fft_axis<T>(A, B, 1, n[1], (int)n[0], (int)N[0], false, +1, tw(0),
-                                    p->deconv[0], s));
+                                    static_cast<const T *>(p->deconv[0]), s));
         GB_CHECK(launch_fft_axis<T>(B, out, N[0], 1, (int)n[1], (int)N[1], false, +1, tw(1),
-                                    p->deconv[1], s));
+                                    static_cast<const T *>(p->deconv[1]), s));
     } else {
         GB_CHECK(launch_fft_axis<T>(A, B, 1, n[1] * n[2], (int)n[0], (int)N[0], false, +1, tw(0),
-                                    p->deconv[0], s));
+                                    static_cast<const T *>(p->deconv[0]), s));
         GB_CHECK(launch_fft_axis<T>(B, A, N[0], n[2], (int)n[1], (int)N[1], false, +1, tw(1),
-                                    p->deconv[1], s));
+                                    static_cast<const T *>(p->deconv[1]), s));
         GB_CHECK(launch_fft_axis<T>(A, out, N[0] * N[1], 1, (int)n[2], (int)N[2], false, +1,
-                                    tw(2), p->deconv[2], s));
+                                    tw(2), static_cast<const T *>(p->deconv[2]), s));
     }
     return NFFT_OK;
 }
@@ -358,7 +358,8 @@ template <typename T> int do_trafo(gbnfft_plan *p, const void *fhat, void *f)
     if (rc) return rc;
     ProfScope ps(p, NFFT_STAGE_INTERP);
     GB_CHECK(launch_interp<T>(p->geom, at<C>(p, p->gA), at<Rec>(p, p->rec), at<int>(p, p->perm),
-                              p->M, static_cast<C *>(f), p->stream));
+                              p->M, at<SubProb>(p, p->subs), at<int>(p, p->nsub), p->max_subs,
+                              static_cast<C *>(f), p->stream));
     return NFFT_OK;
 }
 
@@ -518,7 +519,7 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
     size_t off_dc[3] = {0, 0, 0}, off_tw[3] = {0, 0, 0};
     for (int t = 0; t < d; t++) {
         off_dc[t] = tbytes;
-        tbytes = align_up(tbytes + size_t(NNv[t]) * sizeof(double), 256);
+        tbytes = align_up(tbytes + size_t(NNv[t]) * p->rsize, 256);
         off_tw[t] = tbytes;
         tbytes = align_up(tbytes + size_t(nn[t]) * p->csize, 256);
     }
@@ -540,11 +541,14 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
         // normalised to psibar(0) = 1.
         const double b = g.win[t].b;
         const double psi0 = std::sinh(b * m) / (kPi * m);
-        double *dc = reinterpret_cast<double *>(host + off_dc[t]);
         for (int64_t i = 0; i < NNv[t]; i++) {
             const double k = double(i - NNv[t] / 2);
             const double w = 2.0 * kPi * k / double(nn[t]);
-            dc[i] = psi0 / bessel_i0(double(m) * std::sqrt(b * b - w * w));
+            const double dc = psi0 / bessel_i0(double(m) * std::sqrt(b * b - w * w));
+            if (dtype == NFFT_FP64)
+                reinterpret_cast<double *>(host + off_dc[t])[i] = dc;
+            else
+                reinterpret_cast<float *>(host + off_dc[t])[i] = (float)dc;
         }
         // window polynomials of this axis: coefficient k of tap i at [k * kPolyTaps + i - 1]
         for (int i = 1; i <= 2 * m; i++) {
@@ -581,7 +585,7 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
     }
     char *tb = static_cast<char *>(p->tables);
     for (int t = 0; t < d; t++) {
-        p->deconv[t] = reinterpret_cast<double *>(tb + off_dc[t]);
+        p->deconv[t] = tb + off_dc[t];
         p->tw[t] = tb + off_tw[t];
     }
     p->d_status = reinterpret_cast<int *>(tb + off_status);
@@ -735,7 +739,7 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
         p->geom.spread_method = (int)value;
         return NFFT_OK;
     case NFFT_OPT_INTERP_METHOD:
-        if (value < kInterpAuto || value > kInterpWarp) return NFFT_EINVAL;
+        if (value < kInterpAuto || value > kInterpTile) return NFFT_EINVAL;
         p->geom.interp_method = (int)value;
         return NFFT_OK;
     case NFFT_OPT_BIN_0:

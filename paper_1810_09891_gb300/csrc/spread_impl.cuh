@@ -182,43 +182,91 @@ __host__ __device__ constexpr size_t spread_stage_bytes()
 // The taps of one node, 32 at a time across the lanes of a warp. Tap q enumerates the
 // (2m + 1 - START)^d box row-major (last axis fastest, so neighbouring lanes hit neighbouring
 // cells); its weight is the product of the per-axis window values held by lanes t*NT + i.
-template <typename T, int D, int MM, bool PRIVATE, int START>
-__device__ __forceinline__ void spread_warp_taps(T *re, T *im, const int *tdim, const int *loc,
-                                                 T wa, T wb, typename Cplx<T>::type v, int lane)
+// `off` is the tile index of the box corner (loc_t + START on every axis); `st` the tile strides.
+template <typename T, int D, int MM, int START>
+__device__ __forceinline__ void tap_of_lane(int q, const int *st, T wa, T wb, T &w, int &rel)
 {
     constexpr int NT = 2 * MM + 1;
     constexpr int NW = D * NT;
     constexpr int PER = NT - START;
-    constexpr int TAPS = D == 1 ? PER : (D == 2 ? PER * PER : PER * PER * PER);
-#pragma unroll 1
-    for (int base = 0; base < TAPS; base += 32) {
-        const int q = base + lane;
-        int rem = q < TAPS ? q : 0;
-        T w = (T)1;
-        int idx = 0, mult = 1;
+    int rem = q;
+    w = (T)1;
+    rel = 0;
 #pragma unroll
-        for (int t = D - 1; t >= 0; t--) {
-            const int a = rem % PER;
-            rem /= PER;
-            const int src = t * NT + a + START;
-            const T wa_s = __shfl_sync(0xffffffffu, wa, src & 31);
-            T wt = wa_s;
-            if (NW > 32) {
-                const T wb_s = __shfl_sync(0xffffffffu, wb, src & 31);
-                wt = src < 32 ? wa_s : wb_s;
-            }
-            w *= wt;
-            idx += (loc[t] + a + START) * mult;
-            mult *= tdim[t];
+    for (int t = D - 1; t >= 0; t--) {
+        const int a = rem % PER;
+        rem /= PER;
+        const int src = t * NT + a + START;
+        const T wa_s = __shfl_sync(0xffffffffu, wa, src & 31);
+        T wt = wa_s;
+        if (NW > 32) {
+            const T wb_s = __shfl_sync(0xffffffffu, wb, src & 31);
+            wt = src < 32 ? wa_s : wb_s;
         }
-        if (q < TAPS) {
-            if (PRIVATE) {
-                re[idx] += w * v.x;
-                im[idx] += w * v.y;
-            } else {
-                atomicAdd(re + idx, w * v.x);
-                atomicAdd(im + idx, w * v.y);
+        w *= wt;
+        rel += a * st[t];
+    }
+}
+
+// Private tile of complex values: plain read-modify-write, one 8- or 16-byte access per tap.
+template <typename T, int D, int MM, int START>
+__device__ __forceinline__ void spread_warp_taps_private(typename Cplx<T>::type *tile,
+                                                         const int *st, int off, T wa, T wb,
+                                                         typename Cplx<T>::type v, int lane)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int PER = 2 * MM + 1 - START;
+    constexpr int TAPS = D == 1 ? PER : (D == 2 ? PER * PER : PER * PER * PER);
+    constexpr int ITER = (TAPS + 31) / 32;
+    if (ITER <= 8) {
+#pragma unroll
+        for (int k = 0; k < ITER; k++) {
+            const int q = 32 * k + lane;
+            T w;
+            int rel;
+            tap_of_lane<T, D, MM, START>(q < TAPS ? q : 0, st, wa, wb, w, rel);
+            if (q < TAPS) {
+                C c = tile[off + rel];
+                c.x += w * v.x;
+                c.y += w * v.y;
+                tile[off + rel] = c;
             }
+        }
+    } else {
+#pragma unroll 1
+        for (int k = 0; k < ITER; k++) {
+            const int q = 32 * k + lane;
+            T w;
+            int rel;
+            tap_of_lane<T, D, MM, START>(q < TAPS ? q : 0, st, wa, wb, w, rel);
+            if (q < TAPS) {
+                C c = tile[off + rel];
+                c.x += w * v.x;
+                c.y += w * v.y;
+                tile[off + rel] = c;
+            }
+        }
+    }
+}
+
+// One tile for the CTA, real and imaginary planes, shared-memory atomics.
+template <typename T, int D, int MM, int START>
+__device__ __forceinline__ void spread_warp_taps_atomic(T *re, T *im, const int *st, int off,
+                                                        T wa, T wb, typename Cplx<T>::type v,
+                                                        int lane)
+{
+    constexpr int PER = 2 * MM + 1 - START;
+    constexpr int TAPS = D == 1 ? PER : (D == 2 ? PER * PER : PER * PER * PER);
+    constexpr int ITER = (TAPS + 31) / 32;
+#pragma unroll 4
+    for (int k = 0; k < ITER; k++) {
+        const int q = 32 * k + lane;
+        T w;
+        int rel;
+        tap_of_lane<T, D, MM, START>(q < TAPS ? q : 0, st, wa, wb, w, rel);
+        if (q < TAPS) {
+            atomicAdd(re + off + rel, w * v.x);
+            atomicAdd(im + off + rel, w * v.y);
         }
     }
 }
@@ -239,6 +287,27 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
     __shared__ __align__(16) T tab[kMaxDim * AS];
     load_window_tables<T, MM>(tab, g.poly, D);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    // Lane (t * NT + i) evaluates the window of tap i on axis t for every node (lanes + 32 for
+    // the second set when NW > 32): its polynomial coefficients stay in registers.
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    T ca[DEG + 1], cb[DEG + 1];
+    int ta = 0, ia = 0, tb = 0, ib = 0;
+    T ea = (T)0, eb = (T)0;
+    {
+        const int qa = lane < NW ? lane : 0;
+        ta = qa / NT;
+        ia = qa - ta * NT;
+        const int qb = (NW > 32 && lane + 32 < NW) ? lane + 32 : 0;
+        tb = qb / NT;
+        ib = qb - tb * NT;
+#pragma unroll
+        for (int k = 0; k <= DEG; k++) {
+            ca[k] = ia > 0 ? tab[ta * AS + k * kPolyTaps + ia - 1] : (T)0;
+            cb[k] = (NW > 32 && ib > 0) ? tab[tb * AS + k * kPolyTaps + ib - 1] : (T)0;
+        }
+        ea = (T)g.win[ta].edge_w;
+        eb = (T)g.win[tb].edge_w;
+    }
     int tdim[D];
     int cells = 1;
 #pragma unroll
@@ -250,9 +319,14 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
     const size_t tile_reals = (size_t)2 * cells * (PRIVATE ? kSpreadWarps : 1);
     Rec *st_rec = reinterpret_cast<Rec *>(smem_raw + ((tile_reals * sizeof(T) + 15) / 16) * 16);
     C *st_val = reinterpret_cast<C *>(st_rec + kSpreadChunk);
-    // re plane then im plane; one pair per warp (private) or one pair per CTA (atomic)
-    T *re = sm + (PRIVATE ? (size_t)warp * 2 * cells : 0);
-    T *im = re + cells;
+    // private: one complex tile per warp; atomic: one re plane and one im plane per CTA
+    C *ptile = reinterpret_cast<C *>(sm) + (size_t)warp * cells;
+    T *re = sm;
+    T *im = sm + cells;
+    int st[D];  // tile strides
+    st[D - 1] = 1;
+#pragma unroll
+    for (int t = D - 2; t >= 0; t--) st[t] = st[t + 1] * tdim[t + 1];
     const int nsub = *nsub_total;
     for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
         const SubProb P = subs[sp];
@@ -273,7 +347,8 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
             v_next = f[perm[P.start + tid]];
         }
         if (PRIVATE) {
-            for (int e = lane; e < 2 * cells; e += 32) re[e] = (T)0;
+            T *pz = reinterpret_cast<T *>(ptile);
+            for (int e = lane; e < 2 * cells; e += 32) pz[e] = (T)0;
         } else {
             for (int e = tid; e < 2 * cells; e += blockDim.x) sm[e] = (T)0;
         }
@@ -309,55 +384,83 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
                 // lane (t * NT + i) holds psibar of tap i on axis t (two rounds when NW > 32)
                 T wa = (T)0, wb = (T)0;
                 {
-                    const int q = lane;
-                    if (q < NW) {
-                        const int t = q / NT, i = q - (q / NT) * NT;
-                        wa = window_tap<T, MM>(tab + t * AS, i, frac[t], (T)g.win[t].edge_w);
+                    T fa = frac[0], fb = frac[0];
+#pragma unroll
+                    for (int t = 1; t < D; t++) {
+                        if (ta == t) fa = frac[t];
+                        if (tb == t) fb = frac[t];
                     }
-                    const int q2 = lane + 32;
-                    if (NW > 32 && q2 < NW) {
-                        const int t = q2 / NT, i = q2 - (q2 / NT) * NT;
-                        wb = window_tap<T, MM>(tab + t * AS, i, frac[t], (T)g.win[t].edge_w);
-                    }
+                    if (lane < NW) wa = ia > 0 ? poly_horner<T, DEG>(ca, (T)2 * fa - (T)1)
+                                               : (fa == (T)0 ? ea : (T)0);
+                    if (NW > 32 && lane + 32 < NW)
+                        wb = ib > 0 ? poly_horner<T, DEG>(cb, (T)2 * fb - (T)1)
+                                    : (fb == (T)0 ? eb : (T)0);
                 }
-                if (edge)  // warp-uniform (one node per warp)
-                    spread_warp_taps<T, D, MM, PRIVATE, 0>(re, im, tdim, loc, wa, wb, v, lane);
-                else
-                    spread_warp_taps<T, D, MM, PRIVATE, 1>(re, im, tdim, loc, wa, wb, v, lane);
+                int off = 0;
+#pragma unroll
+                for (int t = 0; t < D; t++) off += loc[t] * st[t];
+                if (edge) {  // warp-uniform (one node per warp)
+                    if (PRIVATE)
+                        spread_warp_taps_private<T, D, MM, 0>(ptile, st, off, wa, wb, v, lane);
+                    else
+                        spread_warp_taps_atomic<T, D, MM, 0>(re, im, st, off, wa, wb, v, lane);
+                } else {
+                    int off1 = off;
+#pragma unroll
+                    for (int t = 0; t < D; t++) off1 += st[t];  // first tap slot is 1
+                    if (PRIVATE)
+                        spread_warp_taps_private<T, D, MM, 1>(ptile, st, off1, wa, wb, v, lane);
+                    else
+                        spread_warp_taps_atomic<T, D, MM, 1>(re, im, st, off1, wa, wb, v, lane);
+                }
                 if (PRIVATE) __syncwarp();
             }
             __syncthreads();
         }
         if (P.count == 0) __syncthreads();
 
-        // flush: tile cell (a_0..a_{d-1}) is grid point (origin_t - m + a_t) mod n_t
-        for (int e = tid; e < cells; e += blockDim.x) {
-            T vr, vi;
-            if (PRIVATE) {
-                vr = (T)0;
-                vi = (T)0;
+        // flush: tile cell (a_0..a_{d-1}) is grid point (origin_t - m + a_t) mod n_t; one warp
+        // per tile row, lanes along the contiguous last axis
+        const int rows = cells / tdim[D - 1];
+        for (int row = warp; row < rows; row += kSpreadWarps) {
+            size_t gbase = 0;
+            {
+                int rem = row;
+                int a[D];
+                a[D - 1] = 0;
 #pragma unroll
-                for (int w = 0; w < kSpreadWarps; w++) {
-                    vr += sm[(size_t)w * 2 * cells + e];
-                    vi += sm[(size_t)w * 2 * cells + cells + e];
+                for (int t = D - 2; t >= 0; t--) {
+                    a[t] = rem % tdim[t];
+                    rem /= tdim[t];
                 }
-            } else {
-                vr = sm[e];
-                vi = sm[cells + e];
-            }
-            if (vr == (T)0 && vi == (T)0) continue;
-            int rem = e;
-            size_t gi = 0;
-            int a[D];
 #pragma unroll
-            for (int t = D - 1; t >= 0; t--) {
-                a[t] = rem % tdim[t];
-                rem /= tdim[t];
+                for (int t = 0; t < D - 1; t++)
+                    gbase = (gbase << g.nlog[t]) |
+                            (size_t)((origin[t] - MM + a[t]) & (g.n[t] - 1));
+                gbase <<= g.nlog[D - 1];
             }
+            for (int a = lane; a < tdim[D - 1]; a += 32) {
+                const int e = row * tdim[D - 1] + a;
+                T vr, vi;
+                if (PRIVATE) {
+                    vr = (T)0;
+                    vi = (T)0;
+                    const C *all = reinterpret_cast<const C *>(sm);
 #pragma unroll
-            for (int t = 0; t < D; t++)
-                gi = (gi << g.nlog[t]) | (size_t)((origin[t] - MM + a[t]) & (g.n[t] - 1));
-            global_add(grid + gi, vr, vi);
+                    for (int w = 0; w < kSpreadWarps; w++) {
+                        const C c = all[(size_t)w * cells + e];
+                        vr += c.x;
+                        vi += c.y;
+                    }
+                } else {
+                    vr = sm[e];
+                    vi = sm[cells + e];
+                }
+                if (vr == (T)0 && vi == (T)0) continue;
+                const size_t gi =
+                    gbase | (size_t)((origin[D - 1] - MM + a) & (g.n[D - 1] - 1));
+                global_add(grid + gi, vr, vi);
+            }
         }
         __syncthreads();
     }

@@ -76,6 +76,16 @@ __device__ __forceinline__ void window_tap_d(const T *__restrict__ c, int i, T f
     dw = (T)2 * dp;
 }
 
+// Horner evaluation with the coefficients in registers (c[0..DEG], lowest degree first).
+template <typename T, int DEG>
+__device__ __forceinline__ T poly_horner(const T *c, T z)
+{
+    T acc = c[DEG];
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; k--) acc = fma(acc, z, c[k]);
+    return acc;
+}
+
 // Copy the window tables (d axes) into shared memory; every thread of the CTA must call it.
 template <typename T, int MM>
 __device__ __forceinline__ void load_window_tables(T *dst, const void *src, int d)

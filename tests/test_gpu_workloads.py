@@ -14,7 +14,7 @@ from gpu_helpers import DEV, TOL, rel_l2, rounded, to_dev
 pytestmark = pytest.mark.gpu
 
 METHODS = ["thread", "warp_atomic", "warp_private"]
-INTERP = ["thread", "warp"]
+INTERP = ["thread", "warp", "tile"]
 
 
 def _plan(N, n, m, M, dtype, method=None, bins=None, interp=None):
