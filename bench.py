@@ -44,7 +44,7 @@ UNIT = "nodes/s"
 def parse_args(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["radial", "clusters"], default="radial")
@@ -52,6 +52,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64 / m=6 variants")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle")
     ap.add_argument("--no-parity", action="store_true", help="skip the oracle error check")
+    ap.add_argument("--ncu-step", action="store_true",
+                    help="only build the workload's plan and run --steps untimed forward + adjoint "
+                         "pairs (a short program for ncu captures of the timed kernels)")
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32",
+                    help="precision used by --ncu-step (the benchmark line itself reports FP32 with FP64 variants)")
     return ap.parse_args(argv)
 
 
@@ -146,7 +151,8 @@ def profiled_traffic(stage: str, workload_name: str):
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
 
-    FIELDS = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,uuid,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -159,12 +165,13 @@ class ClockSampler:
         try:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                   "-lms", "100"]
+                   "-lms", "20"]
             self.proc = subprocess.Popen(cmd, stdout=self.tmp, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
+        """Stop sampling; summarise the samples taken between wall-clock times t0 and t1."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         self.proc.terminate()
@@ -177,11 +184,20 @@ class ClockSampler:
         with open(self.tmp.name) as fh:
             for line in fh:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 10:
+                if len(parts) < 11:
                     continue
-                if self.uuid and self.uuid not in parts[1]:
+                if self.uuid and self.uuid not in parts[2]:
                     continue
-                rows.append(parts)
+                if t0 is not None:
+                    try:
+                        ts = time.mktime(time.strptime(parts[0].split(".")[0],
+                                                       "%Y/%m/%d %H:%M:%S"))
+                        ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                    except (ValueError, IndexError):
+                        ts = None
+                    if ts is not None and not (t0 - 0.05 <= ts <= t1 + 0.05):
+                        continue
+                rows.append(parts[1:])
         os.unlink(self.tmp.name)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
@@ -377,14 +393,17 @@ def ours(args):
         pass
     clocks = ClockSampler(uuid)
     clocks.start()
+    run_variant(plan, fh, f, 200, flush, torch)  # keeps the GPU busy while the sampler starts
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    t_start = time.time()
     fwd, adj, (y, h) = run_variant(plan, fh, f, args.steps, flush, torch)
     torch.cuda.synchronize()
+    t_end = time.time()
     if world > 1:
         dist.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_start, t_end)
     total_ms = max_over_ranks(float(sum(fwd) + sum(adj)), dev)
     ms_per_step = total_ms / args.steps
     value = job_throughput(M, args.steps, world, total_ms)
@@ -506,10 +525,38 @@ def ours(args):
     return 0
 
 
+def ncu_step(args):
+    """The timed kernels of the workload, untimed: set_nodes once, then --steps forward +
+    adjoint pairs on the same plan and inputs as the benchmark."""
+    import torch
+
+    from paper_1810_09891_gb300.nfft import Plan
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    npdt, tdt, cdt = ((np.float32, torch.float32, np.complex64) if args.dtype == "f32" else
+                      (np.float64, torch.float64, np.complex128))
+    wl = workload(args.workload, args.m, npdt)
+    plan = Plan(wl["N"], wl["x"].shape[0], n=wl["n"], m=args.m, dtype=tdt, device=dev)
+    plan.set_nodes(torch.tensor(wl["x"], device=dev))
+    fh = torch.tensor(wl["fhat"].astype(cdt), device=dev)
+    f = torch.tensor(wl["f"].astype(cdt), device=dev)
+    for _ in range(max(1, args.steps)):
+        plan.trafo(fh)
+        plan.adjoint(f)
+    torch.cuda.synchronize()
+    st = plan.status()
+    plan.close()
+    if st != 0:
+        raise RuntimeError(f"device status {st}")
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.ncu_step:
+        return ncu_step(args)
     return ours(args)
 
 

@@ -163,7 +163,8 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  * result beyond rounding).
  *   NFFT_OPT_SPREAD_METHOD  0 automatic, 1 one thread per node with shared-memory atomics,
  *                           2 one warp per node with shared-memory atomics,
- *                           3 one warp per node with a private tile per warp (no atomics).
+ *                           3 one warp per node with a private tile per warp (no atomics),
+ *                           4 (d = 2) eight lanes per node, a private tile per eight lanes.
  *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node (gathers from the grid),
  *                           2 one warp per node, 3 one thread per node gathering from a
  *                           shared-memory tile of the node's bin.

@@ -76,7 +76,7 @@ OPT_SPREAD_METHOD = 1
 OPT_BIN = (2, 3, 4)
 OPT_INTERP_METHOD = 5
 INTERP_METHODS = {"auto": 0, "thread": 1, "warp": 2, "tile": 3}
-SPREAD_METHODS = {"auto": 0, "thread": 1, "warp_atomic": 2, "warp_private": 3}
+SPREAD_METHODS = {"auto": 0, "thread": 1, "warp_atomic": 2, "warp_private": 3, "octet": 4}
 
 STAGES = ["set_nodes", "fft_forward", "interp", "zero_grid", "spread", "fft_adjoint", "grad"]
 

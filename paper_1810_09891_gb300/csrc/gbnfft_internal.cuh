@@ -50,6 +50,7 @@ constexpr int kSpreadAuto = 0;
 constexpr int kSpreadThread = 1;
 constexpr int kSpreadWarpAtomic = 2;
 constexpr int kSpreadWarpPrivate = 3;
+constexpr int kSpreadOctet = 4;
 
 // Interpolation methods (see interp_impl.cuh).
 constexpr int kInterpAuto = 0;

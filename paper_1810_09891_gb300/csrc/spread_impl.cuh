@@ -466,6 +466,160 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
     }
 }
 
+// ----------------------------------------------------------------------------- octet form (d = 2)
+// Eight lanes per node, four nodes per warp, 32 private complex tiles per CTA. Lane l of a group
+// owns the tap rows a0 = l, l + 8, ... of its node (each a run of 2m (+1) contiguous tile cells)
+// and adds them with plain read-modify-write; the column weights are evaluated once per lane
+// (taps l and l + 8) and shared inside the group with shuffles. Per node this costs about a
+// quarter of the warp form's instructions.
+constexpr int kOctets = 4 * kSpreadWarps;  // groups (and private tiles) per CTA
+
+// Cells between consecutive private tiles: for FP32 an odd multiple of 8 cells (half the 32
+// banks), so that the four groups of a warp, each touching 8 contiguous cells of its own tile,
+// fall in alternating bank halves; FP64 groups already fill all banks.
+template <typename T> __host__ __device__ inline int octet_tile_stride(int cells)
+{
+    if (sizeof(T) == 8) return cells;
+    return cells + ((8 - cells % 16) + 16) % 16;
+}
+
+template <typename T, int MM, int START>
+__device__ __forceinline__ void spread_octet_node(typename Cplx<T>::type *tile, int st0, int off,
+                                                  T frac0, T frac1, const T *ca, T ea,
+                                                  const T *cb, T eb,
+                                                  typename Cplx<T>::type v, int l,
+                                                  unsigned mask)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    constexpr int NT = 2 * MM + 1;
+    constexpr int PER = NT - START;
+    const T z0 = (T)2 * frac0 - (T)1, z1 = (T)2 * frac1 - (T)1;
+    // this lane's columns a1 = l and l + 8, and the row weights a0 = l, l + 8 it broadcasts
+    T w1a = (T)0, w1b = (T)0, w0a = (T)0, w0b = (T)0;
+    if (l < PER) {
+        const int i = START + l;
+        w1a = i == 0 ? (frac1 == (T)0 ? eb : (T)0) : poly_horner_tap<T, DEG>(cb, i, z1);
+        w0a = i == 0 ? (frac0 == (T)0 ? ea : (T)0) : poly_horner_tap<T, DEG>(ca, i, z0);
+    }
+    if (PER > 8 && l + 8 < PER) {
+        const int i = START + l + 8;
+        w1b = poly_horner_tap<T, DEG>(cb, i, z1);
+        w0b = poly_horner_tap<T, DEG>(ca, i, z0);
+    }
+    const T ar = w1a * v.x, ai = w1a * v.y, br = w1b * v.x, bi = w1b * v.y;
+    C *col = tile + off + l;
+#pragma unroll
+    for (int a0 = 0; a0 < PER; a0++) {
+        const T w0 = __shfl_sync(mask, a0 < 8 ? w0a : w0b, a0 & 7, 8);
+        C *row = col + a0 * st0;
+        if (l < PER) {
+            C c = row[0];
+            c.x += w0 * ar;
+            c.y += w0 * ai;
+            row[0] = c;
+        }
+        if (PER > 8 && l + 8 < PER) {
+            C c = row[8];
+            c.x += w0 * br;
+            c.y += w0 * bi;
+            row[8] = c;
+        }
+    }
+}
+
+template <typename T, int MM>
+__global__ void __launch_bounds__(32 * kSpreadWarps)
+    spread_octet_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
+                        const typename RecOf<T>::type *__restrict__ rec,
+                        const int *__restrict__ perm, const SubProb *__restrict__ subs,
+                        const int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    __shared__ __align__(16) T tab[kMaxDim * AS];
+    load_window_tables<T, MM>(tab, g.poly, 2);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int l = lane & 7, oct = tid >> 3;
+    const unsigned mask = 0xffu << (lane & 24);
+    const int td0 = g.bs[0] + 2 * MM, td1 = g.bs[1] + 2 * MM;
+    const int cells = td0 * td1;
+    const int tstride = octet_tile_stride<T>(cells);  // staggers the tiles over the banks
+    C *tiles = reinterpret_cast<C *>(smem_raw);
+    C *mine = tiles + (size_t)oct * tstride;
+    Rec *st_rec = reinterpret_cast<Rec *>(smem_raw + (size_t)kOctets * tstride * sizeof(C));
+    C *st_val = reinterpret_cast<C *>(st_rec + kSpreadChunk);
+    const T *ca = tab, *cb = tab + AS;
+    const T ea = (T)g.win[0].edge_w, eb = (T)g.win[1].edge_w;
+    const int nsub = *nsub_total;
+    for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+        const SubProb P = subs[sp];
+        const int org1 = (P.bin % g.nb[1]) * g.bs[1];
+        const int org0 = (P.bin / g.nb[1]) * g.bs[0];
+        Rec r_next;
+        C v_next;
+        if (tid < P.count) {
+            r_next = rec[P.start + tid];
+            v_next = f[perm[P.start + tid]];
+        }
+        {
+            T *pz = reinterpret_cast<T *>(mine);
+            for (int e = l; e < 2 * cells; e += 8) pz[e] = (T)0;
+        }
+        for (int c0 = 0; c0 < P.count; c0 += kSpreadChunk) {
+            const int cnt = min(kSpreadChunk, P.count - c0);
+            if (tid < cnt) {
+                st_rec[tid] = r_next;
+                st_val[tid] = v_next;
+            }
+            __syncthreads();
+            {
+                const int nx = c0 + kSpreadChunk + tid;
+                if (nx < P.count) {
+                    r_next = rec[P.start + nx];
+                    v_next = f[perm[P.start + nx]];
+                }
+            }
+            for (int k = oct; k < cnt; k += kOctets) {
+                const Rec r = st_rec[k];
+                const C v = st_val[k];
+                const int loc1 = (r.cell & (g.n[1] - 1)) - org1;
+                const int loc0 = ((r.cell >> g.nlog[1]) & (g.n[0] - 1)) - org0;
+                const T fr0 = r.fr[0], fr1 = r.fr[1];
+                if (fr0 == (T)0 || fr1 == (T)0)  // uniform inside the group (one node)
+                    spread_octet_node<T, MM, 0>(mine, td1, loc0 * td1 + loc1, fr0, fr1, ca, ea,
+                                                cb, eb, v, l, mask);
+                else
+                    spread_octet_node<T, MM, 1>(mine, td1, (loc0 + 1) * td1 + loc1 + 1, fr0,
+                                                fr1, ca, ea, cb, eb, v, l, mask);
+                __syncwarp(mask);
+            }
+            __syncthreads();
+        }
+
+        // flush: cell (a0, a1) of the tile is grid point ((org0 - m + a0) mod n0,
+        // (org1 - m + a1) mod n1); one warp per tile row, lanes along the row
+        for (int a0 = warp; a0 < td0; a0 += kSpreadWarps) {
+            const size_t gbase = (size_t)((org0 - MM + a0) & (g.n[0] - 1)) << g.nlog[1];
+            for (int a1 = lane; a1 < td1; a1 += 32) {
+                const int e = a0 * td1 + a1;
+                T vr = (T)0, vi = (T)0;
+#pragma unroll 8
+                for (int o = 0; o < kOctets; o++) {
+                    const C c = tiles[(size_t)o * tstride + e];
+                    vr += c.x;
+                    vi += c.y;
+                }
+                if (vr == (T)0 && vi == (T)0) continue;
+                global_add(grid + (gbase | (size_t)((org1 - MM + a1) & (g.n[1] - 1))), vr, vi);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Shared memory left for the dynamic part once the static window tables are placed.
 template <typename T, int MM> constexpr size_t spread_dyn_limit()
 {
@@ -501,6 +655,11 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
         method = tile * kSpreadWarps <= 64 * 1024 ? kSpreadWarpPrivate : kSpreadWarpAtomic;
     // a form whose shared memory does not fit falls back to the one-tile form
     constexpr size_t limit = spread_dyn_limit<T, MM>();
+    const size_t octet_tiles =
+        (size_t)octet_tile_stride<T>((int)cells) * sizeof(typename Cplx<T>::type) * kOctets;
+    if (method == kSpreadOctet &&
+        (D != 2 || 2 * MM + 1 > 16 || octet_tiles + spread_stage_bytes<T>() > limit))
+        method = kSpreadWarpPrivate;
     if (method == kSpreadWarpPrivate && tile * kSpreadWarps + 16 + spread_stage_bytes<T>() > limit)
         method = kSpreadWarpAtomic;
     if (method == kSpreadWarpAtomic && tile + 16 + spread_stage_bytes<T>() > limit)
@@ -520,6 +679,15 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
         if (e != cudaSuccess) return e;
         spread_warp_kernel<T, D, MM, false><<<blocks, 32 * kSpreadWarps, smem, stream>>>(
             g, f, rec, perm, subs, nsub_total, grid);
+    } else if (method == kSpreadOctet) {
+        if constexpr (D == 2) {
+            const size_t smem = octet_tiles + spread_stage_bytes<T>();
+            e = launch_persistent(spread_octet_kernel<T, MM>, smem, 32 * kSpreadWarps, max_subs,
+                                  blocks);
+            if (e != cudaSuccess) return e;
+            spread_octet_kernel<T, MM><<<blocks, 32 * kSpreadWarps, smem, stream>>>(
+                g, f, rec, perm, subs, nsub_total, grid);
+        }
     } else if (method == kSpreadWarpPrivate) {
         const size_t smem = (tile * kSpreadWarps + 15) / 16 * 16 + spread_stage_bytes<T>();
         e = launch_persistent(spread_warp_kernel<T, D, MM, true>, smem, 32 * kSpreadWarps,

@@ -86,6 +86,16 @@ __device__ __forceinline__ T poly_horner(const T *c, T z)
     return acc;
 }
 
+// Tap i (1..2m) of one axis from a table in shared memory (c = the axis' table).
+template <typename T, int DEG>
+__device__ __forceinline__ T poly_horner_tap(const T *c, int i, T z)
+{
+    T acc = c[DEG * kPolyTaps + i - 1];
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; k--) acc = fma(acc, z, c[k * kPolyTaps + i - 1]);
+    return acc;
+}
+
 // Copy the window tables (d axes) into shared memory; every thread of the CTA must call it.
 template <typename T, int MM>
 __device__ __forceinline__ void load_window_tables(T *dst, const void *src, int d)
