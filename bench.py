@@ -47,7 +47,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["radial", "clusters"], default="radial")
+    ap.add_argument("--workload", choices=["radial", "clusters", "batched"], default="radial",
+                    help="radial: the 2-D radial benchmark (default); clusters: 3-D clustered "
+                         "nodes; batched: 64 uneven 2-D problems in one CUDA graph")
+    ap.add_argument("--tune", action="store_true", help="batched: autotune every plan first")
     ap.add_argument("--m", type=int, default=4)
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64 / m=6 variants")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle")
@@ -78,9 +81,9 @@ def load_peaks():
 
 def workload(name: str, m: int, dtype):
     from paper_1810_09891_gb300 import workloads as W
-    if name == "radial":
-        return W.config_radial(m=m, dtype=dtype)
-    return W.config_clusters(dtype=dtype, m=m)
+    if name == "clusters":
+        return W.config_clusters(dtype=dtype, m=m)
+    return W.config_radial(m=m, dtype=dtype)
 
 
 def algorithmic_bytes(stage: str, d: int, N, n, M: int, p: int) -> float:
@@ -551,12 +554,63 @@ def ncu_step(args):
     return 0
 
 
+def batched(args):
+    """64 independent 2-D problems (N_i per axis from {64, ..., 512}, M_i log-uniform in
+    [1e4, 1e6], uniform nodes, FP32, m = 4): forward + adjoint of the whole batch captured in one
+    CUDA graph; value = sum of M_i per step / step time."""
+    import torch
+
+    from paper_1810_09891_gb300 import workloads as W
+    from paper_1810_09891_gb300.batch import PlanBatch, batched_specs
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    specs = batched_specs()
+    b = PlanBatch(specs, dtype=torch.float32, device=dev)
+    xs = [torch.tensor(W.round_nodes(W.uniform_nodes(s["M"], 2, seed_offset=1000 + i),
+                                     np.float32), device=dev) for i, s in enumerate(specs)]
+    fhs = [torch.tensor(W.gaussian_fhat(s["N"], 2000 + i).astype(np.complex64), device=dev)
+           for i, s in enumerate(specs)]
+    fs = [torch.tensor(W.gaussian_values(s["M"], 3000 + i).astype(np.complex64), device=dev)
+          for i, s in enumerate(specs)]
+    b.set_nodes(xs)
+    tuned = b.tune(fhs, fs) if args.tune else None
+    b.capture(fhs, fs)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        b.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for a, c in ev:
+        flush.zero_()
+        a.record()
+        b.replay()
+        c.record()
+    torch.cuda.synchronize()
+    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+    nodes = sum(s["M"] for s in specs)
+    line = {"metric": METRIC, "value": nodes * args.steps / (total_ms * 1e-3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched_64x2d_uneven", "problems": len(specs),
+                       "nodes_per_step": nodes, "m": 4, "graph": "one CUDA graph per step",
+                       "tuned": bool(args.tune),
+                       "l2": "flushed (256 MiB write) between timed steps"},
+            "tuning": [{"N": list(s["N"]), "M": s["M"], "spread": t["spread_method"],
+                        "bins": t["bins"]} for s, t in zip(specs, tuned)] if tuned else None}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return reference_arm(args)
     if args.ncu_step:
         return ncu_step(args)
+    if args.workload == "batched":
+        return batched(args)
     return ours(args)
 
 

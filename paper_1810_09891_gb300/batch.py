@@ -1,0 +1,182 @@
+"""Many NFFTs of uneven size at once: a batch of plans, captured in one CUDA graph, with
+per-plan tuning by measurement.
+
+``PlanBatch`` owns one ``Plan`` per problem (its own N, M, n, m, precision). ``trafo`` /
+``adjoint`` run every plan's kernels on the current stream; ``capture`` records the forward and
+the adjoint of the whole batch into one CUDA graph over static input and output buffers, and
+``replay`` launches the batch with a single graph launch (no per-kernel host overhead).
+``autotune`` chooses, per plan, the spreading method and bin sizes by timing candidates on the
+plan's own nodes (the measured counterpart of the plan search the paper's FFTW flags select,
+Section 3.1, Table tab:fttwflags). Every candidate computes the same transform up to rounding.
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+import statistics
+
+import torch
+
+from .nfft import Plan
+
+# Candidate options per dimension: (spread_method, bins)
+CANDIDATES = {
+    1: [(s, (b,)) for s in ("warp_private", "warp_atomic") for b in (256, 1024, 4096)],
+    2: [(s, b) for s in ("warp_private", "warp_atomic", "octet")
+        for b in ((8, 8), (8, 16), (16, 16), (32, 32))],
+    3: [(s, b) for s in ("warp_atomic", "warp_private", "thread")
+        for b in ((8, 8, 8), (4, 8, 8), (8, 8, 16))],
+}
+
+
+def _apply(plan: Plan, spread: str, bins) -> None:
+    plan.set_option("spread_method", spread)
+    for t, b in enumerate(bins):
+        plan.set_option(f"bin{t}", int(b))
+
+
+def time_step(plan: Plan, x: torch.Tensor, fhat: torch.Tensor, f: torch.Tensor,
+              steps: int = 5) -> float:
+    """Median milliseconds of one forward + one adjoint on the plan's stream (CUDA events)."""
+    plan.set_nodes(x)
+    plan.trafo(fhat)
+    plan.adjoint(f)
+    times = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.trafo(fhat)
+        plan.adjoint(f)
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def autotune(plan: Plan, x: torch.Tensor, fhat: torch.Tensor, f: torch.Tensor,
+             candidates=None, steps: int = 5) -> dict:
+    """Try every candidate (spread_method, bins) on this plan and these inputs; keep the fastest
+    (the plan ends configured with it, nodes set). Returns {"spread_method", "bins", "ms",
+    "tried": [(spread, bins, ms), ...]}. Candidates that do not fit the hardware are skipped."""
+    cands = candidates if candidates is not None else CANDIDATES[plan.d]
+    tried = []
+    for spread, bins in cands:
+        bins = tuple(min(int(b), nn) for b, nn in zip(bins, plan.n))
+        try:
+            _apply(plan, spread, bins)
+            ms = time_step(plan, x, fhat, f, steps)
+        except RuntimeError:
+            continue
+        tried.append((spread, bins, ms))
+    if not tried:
+        raise RuntimeError("autotune: no candidate ran")
+    spread, bins, ms = min(tried, key=lambda t: t[2])
+    _apply(plan, spread, bins)
+    plan.set_nodes(x)
+    return {"spread_method": spread, "bins": list(bins), "ms": ms, "tried": tried}
+
+
+class TuningCache:
+    """Chosen options keyed by (d, N, n, m, precision, M), optionally persisted as JSON."""
+
+    def __init__(self, path: str | None = None):
+        self.path = path
+        self.table = {}
+        if path and os.path.exists(path):
+            with open(path) as fh:
+                self.table = json.load(fh)
+
+    @staticmethod
+    def key(plan: Plan) -> str:
+        return json.dumps([plan.d, list(plan.N), list(plan.n), plan.m, str(plan.dtype), plan.M])
+
+    def get(self, plan: Plan):
+        return self.table.get(self.key(plan))
+
+    def put(self, plan: Plan, choice: dict) -> None:
+        self.table[self.key(plan)] = {"spread_method": choice["spread_method"],
+                                      "bins": list(choice["bins"]), "ms": choice["ms"]}
+        if self.path:
+            with open(self.path, "w") as fh:
+                json.dump(self.table, fh, indent=1)
+
+
+class PlanBatch:
+    """A batch of independent NFFT problems (uneven N and M) on one device."""
+
+    def __init__(self, specs, dtype=torch.float32, device=None):
+        """specs: iterable of dicts with keys N, M and optionally n, m (default 4)."""
+        self.plans = [Plan(s["N"], s["M"], n=s.get("n"), m=s.get("m", 4), dtype=dtype,
+                           device=device) for s in specs]
+        self.device = self.plans[0].device if self.plans else device
+        self.dtype = dtype
+        self.graph = None
+
+    def __len__(self):
+        return len(self.plans)
+
+    def set_nodes(self, xs) -> None:
+        for p, x in zip(self.plans, xs):
+            p.set_nodes(x)
+        self._x = list(xs)
+
+    def tune(self, fhats, fs, cache: TuningCache | None = None, steps: int = 3) -> list:
+        """Autotune every plan (or reuse a cached choice for its signature)."""
+        out = []
+        for p, x, fh, f in zip(self.plans, self._x, fhats, fs):
+            choice = cache.get(p) if cache is not None else None
+            if choice is None:
+                choice = autotune(p, x, fh, f, steps=steps)
+                if cache is not None:
+                    cache.put(p, choice)
+            else:
+                _apply(p, choice["spread_method"], choice["bins"])
+                p.set_nodes(x)
+            out.append(choice)
+        return out
+
+    def trafo(self, fhats) -> list:
+        return [p.trafo(fh) for p, fh in zip(self.plans, fhats)]
+
+    def adjoint(self, fs) -> list:
+        return [p.adjoint(f) for p, f in zip(self.plans, fs)]
+
+    def capture(self, fhats, fs) -> None:
+        """Record forward(fhats) and adjoint(fs) of the whole batch into one CUDA graph. The
+        graph reads the given input tensors and writes ``self.out_f`` / ``self.out_h``; copy new
+        inputs into ``fhats`` / ``fs`` before each ``replay``. Nodes must be set beforehand."""
+        self.in_fhat = list(fhats)
+        self.in_f = list(fs)
+        s = torch.cuda.Stream(self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):  # warm-up outside the capture (kernel attributes, caches)
+            self.trafo(self.in_fhat)
+            self.adjoint(self.in_f)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.out_f = self.trafo(self.in_fhat)
+            self.out_h = self.adjoint(self.in_f)
+        self.graph = g
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        self.graph.replay()
+        return self.out_f, self.out_h
+
+
+def batched_specs(count: int = 64, seed_offset: int = 40, sizes=(64, 128, 256, 512),
+                  log_m=(4.0, 6.0)):
+    """Problem sizes of the batched workload: N_i per axis drawn from `sizes` independently,
+    M_i log-uniform in [10^log_m[0], 10^log_m[1]] (seeded)."""
+    from .workloads import rng
+
+    g = rng(seed_offset)
+    specs = []
+    for _ in range(count):
+        N = tuple(int(g.choice(sizes)) for _ in range(2))
+        M = int(10 ** g.uniform(*log_m))
+        specs.append({"N": N, "M": M, "m": 4})
+    return specs

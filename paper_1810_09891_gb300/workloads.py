@@ -133,3 +133,54 @@ def config_clusters(M: int = 4_194_304, dtype=np.float32, N=(128, 128, 128), m: 
     fhat = gaussian_fhat(N, seed_offset=102)
     f = gaussian_values(x.shape[0], seed_offset=202)
     return dict(name=f"3d_clusters_N{N[0]}_M{M}", N=N, n=n, m=m, x=x, fhat=fhat, f=f)
+
+
+def spiral_nodes(arms: int = 32, samples: int = 8192, turns: float = 4.0) -> np.ndarray:
+    """Interleaved Archimedean spiral: arm a, sample s at radius 0.5 s / samples and angle
+    2 pi turns s / samples + 2 pi a / arms; arm-major order, FP64, shape (arms * samples, 2)."""
+    s = np.arange(samples, dtype=np.float64)
+    r = 0.5 * s / samples
+    th = 2.0 * np.pi * turns * s / samples
+    a = np.arange(arms, dtype=np.float64)[:, None]
+    ang = th[None, :] + 2.0 * np.pi * a / arms
+    x0 = (r[None, :] * np.cos(ang)).reshape(-1)
+    x1 = (r[None, :] * np.sin(ang)).reshape(-1)
+    return wrap(np.stack([x0, x1], axis=1))
+
+
+def ellipse_phantom_fhat(N, count: int = 20, seed_offset: int = 5) -> np.ndarray:
+    """Fourier coefficients fhat_k = int f(x) e^{+2 pi i k.x} dx of a sum of `count` random
+    ellipse indicators f = sum_e rho_e 1_{E_e} on [-1/2, 1/2)^2 (so that
+    f(x) = sum_k fhat_k e^{-2 pi i k.x}). Ellipse e: density rho ~ U[0.1, 1], semi-axes
+    a, b ~ U[0.05, 0.3], centre c ~ U[-0.3, 0.3]^2, rotation ~ U[0, pi). For the unit disc the
+    transform is J1(2 pi |k|) / |k|; an ellipse scales and rotates k and adds the phase of c."""
+    from scipy.special import j1
+
+    g = rng(seed_offset)
+    k0, k1 = np.meshgrid(*centred_k(N), indexing="ij")
+    k0 = k0.astype(np.float64)
+    k1 = k1.astype(np.float64)
+    out = np.zeros(tuple(int(v) for v in N), dtype=np.complex128)
+    for _ in range(count):
+        rho = g.uniform(0.1, 1.0)
+        a, b = g.uniform(0.05, 0.3, size=2)
+        c = g.uniform(-0.3, 0.3, size=2)
+        al = g.uniform(0.0, np.pi)
+        u = a * (np.cos(al) * k0 + np.sin(al) * k1)
+        v = b * (-np.sin(al) * k0 + np.cos(al) * k1)
+        q = np.sqrt(u * u + v * v)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            disc = np.where(q > 0, j1(2.0 * np.pi * q) / np.where(q > 0, q, 1.0), np.pi)
+        out += rho * a * b * disc * np.exp(2j * np.pi * (k0 * c[0] + k1 * c[1]))
+    return out
+
+
+def config_spiral(dtype=np.float32, N=(256, 256), m: int = 4, arms: int = 32,
+                  samples: int = 8192):
+    """2-D reconstruction workload: N = (256, 256), n = 2N, m = 4, M = 32 x 8192 spiral nodes,
+    fhat_true an ellipse phantom."""
+    N = tuple(int(v) for v in N)
+    n = tuple(2 * v for v in N)
+    x = round_nodes(spiral_nodes(arms, samples), dtype)
+    return dict(name=f"2d_spiral_N{N[0]}_M{x.shape[0]}_m{m}", N=N, n=n, m=m, x=x,
+                fhat_true=ellipse_phantom_fhat(N))
