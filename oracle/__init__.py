@@ -80,6 +80,19 @@ def _load():
             "ora_nfft": ([Int, P, P, Int, I64, P, P, P], Int),
             "ora_nfft_adjoint": ([Int, P, P, Int, I64, P, P, P], Int),
             "ora_nfft_grad_x": ([Int, P, P, Int, I64, P, P, P, P], Int),
+            "ora_bspline": ([Int, D], D),
+            "ora_window_param": ([Int, I64, I64, Int], D),
+            "ora_window_psi": ([Int, D, Int, D], D),
+            "ora_window_dpsi": ([Int, D, Int, D], D),
+            "ora_window_phihat": ([Int, I64, I64, Int, D], D),
+            "ora_nfft_D_w": ([Int, Int, P, P, Int, P, P], None),
+            "ora_nfft_DH_w": ([Int, Int, P, P, Int, P, P], None),
+            "ora_nfft_B_w": ([Int, Int, P, P, Int, I64, P, P, P], None),
+            "ora_nfft_BH_w": ([Int, Int, P, P, Int, I64, P, P, P], None),
+            "ora_nfft_dB_w": ([Int, Int, P, P, Int, I64, P, P, P], None),
+            "ora_nfft_w": ([Int, Int, P, P, Int, I64, P, P, P], Int),
+            "ora_nfft_adjoint_w": ([Int, Int, P, P, Int, I64, P, P, P], Int),
+            "ora_nfft_grad_x_w": ([Int, Int, P, P, Int, I64, P, P, P, P], Int),
         }
         for name, (argt, rest) in sigs.items():
             fn = getattr(lib, name)
@@ -87,6 +100,15 @@ def _load():
             fn.restype = rest
         _lib = lib
         return lib
+
+
+WINDOWS = {"kaiser_bessel": 0, "gaussian": 1, "bspline": 2, "sinc": 3}
+
+
+def _win(window) -> int:
+    if isinstance(window, int):
+        return window
+    return WINDOWS[window]
 
 
 def _i64(v) -> np.ndarray:
@@ -141,6 +163,27 @@ def kb_phihat(k: int, n: int, m: int, b: float) -> float:
     return float(_load().ora_kb_phihat(int(k), int(n), int(m), float(b)))
 
 
+def bspline(p: int, t: float) -> float:
+    """Centred cardinal B-spline of order p."""
+    return float(_load().ora_bspline(int(p), float(t)))
+
+
+def window_param(window, n: int, N: int, m: int) -> float:
+    return float(_load().ora_window_param(_win(window), int(n), int(N), int(m)))
+
+
+def window_psi(window, t: float, m: int, prm: float) -> float:
+    return float(_load().ora_window_psi(_win(window), float(t), int(m), float(prm)))
+
+
+def window_dpsi(window, t: float, m: int, prm: float) -> float:
+    return float(_load().ora_window_dpsi(_win(window), float(t), int(m), float(prm)))
+
+
+def window_phihat(window, k: int, n: int, m: int, prm: float) -> float:
+    return float(_load().ora_window_phihat(_win(window), int(k), int(n), int(m), float(prm)))
+
+
 # ------------------------------------------------------------------------------------ direct
 
 def ndft(x, fhat) -> np.ndarray:
@@ -187,68 +230,72 @@ def fft(a, sign: int = -1) -> np.ndarray:
 
 # ------------------------------------------------------------------------------------ NFFT steps
 
-def nfft_D(fhat, n, m: int) -> np.ndarray:
+def nfft_D(fhat, n, m: int, window="kaiser_bessel") -> np.ndarray:
     fhat = _c128(fhat)
     n = tuple(int(v) for v in n)
     g = np.zeros(n, dtype=np.complex128)
-    _load().ora_nfft_D(fhat.ndim, _p(_i64(fhat.shape)), _p(_i64(n)), int(m), _p(fhat), _p(g))
+    _load().ora_nfft_D_w(_win(window), fhat.ndim, _p(_i64(fhat.shape)), _p(_i64(n)), int(m),
+                         _p(fhat), _p(g))
     return g
 
 
-def nfft_DH(ghat, N, m: int) -> np.ndarray:
+def nfft_DH(ghat, N, m: int, window="kaiser_bessel") -> np.ndarray:
     ghat = _c128(ghat)
     N = tuple(int(v) for v in N)
     out = np.zeros(N, dtype=np.complex128)
-    _load().ora_nfft_DH(ghat.ndim, _p(_i64(N)), _p(_i64(ghat.shape)), int(m), _p(ghat), _p(out))
+    _load().ora_nfft_DH_w(_win(window), ghat.ndim, _p(_i64(N)), _p(_i64(ghat.shape)), int(m),
+                          _p(ghat), _p(out))
     return out
 
 
-def nfft_B(x, g, N, m: int) -> np.ndarray:
+def nfft_B(x, g, N, m: int, window="kaiser_bessel") -> np.ndarray:
     g = _c128(g)
     d = g.ndim
     x = _nodes(x, d)
     f = np.zeros(x.shape[0], dtype=np.complex128)
-    _load().ora_nfft_B(d, _p(_i64(N)), _p(_i64(g.shape)), int(m), x.shape[0], _p(x), _p(g), _p(f))
+    _load().ora_nfft_B_w(_win(window), d, _p(_i64(N)), _p(_i64(g.shape)), int(m), x.shape[0],
+                         _p(x), _p(g), _p(f))
     return f
 
 
-def nfft_BH(x, f, N, n, m: int) -> np.ndarray:
+def nfft_BH(x, f, N, n, m: int, window="kaiser_bessel") -> np.ndarray:
     n = tuple(int(v) for v in n)
     d = len(n)
     x = _nodes(x, d)
     f = _c128(f).reshape(-1)
     g = np.zeros(n, dtype=np.complex128)
-    _load().ora_nfft_BH(d, _p(_i64(N)), _p(_i64(n)), int(m), x.shape[0], _p(x), _p(f), _p(g))
+    _load().ora_nfft_BH_w(_win(window), d, _p(_i64(N)), _p(_i64(n)), int(m), x.shape[0], _p(x),
+                          _p(f), _p(g))
     return g
 
 
-def nfft_dB(x, g, N, m: int) -> np.ndarray:
+def nfft_dB(x, g, N, m: int, window="kaiser_bessel") -> np.ndarray:
     g = _c128(g)
     d = g.ndim
     x = _nodes(x, d)
     ds = np.zeros((x.shape[0], d), dtype=np.complex128)
-    _load().ora_nfft_dB(d, _p(_i64(N)), _p(_i64(g.shape)), int(m), x.shape[0], _p(x), _p(g),
-                        _p(ds))
+    _load().ora_nfft_dB_w(_win(window), d, _p(_i64(N)), _p(_i64(g.shape)), int(m), x.shape[0],
+                          _p(x), _p(g), _p(ds))
     return ds
 
 
 # ------------------------------------------------------------------------------------ NFFT
 
-def nfft(x, fhat, n=None, m: int = 8) -> np.ndarray:
+def nfft(x, fhat, n=None, m: int = 8, window="kaiser_bessel") -> np.ndarray:
     """Algorithm "NFFT" (Section 2): f = B F D fhat."""
     fhat = _c128(fhat)
     d = fhat.ndim
     n = default_n(fhat.shape) if n is None else tuple(int(v) for v in n)
     x = _nodes(x, d)
     f = np.zeros(x.shape[0], dtype=np.complex128)
-    rc = _load().ora_nfft(d, _p(_i64(fhat.shape)), _p(_i64(n)), int(m), x.shape[0], _p(x),
-                          _p(fhat), _p(f))
+    rc = _load().ora_nfft_w(_win(window), d, _p(_i64(fhat.shape)), _p(_i64(n)), int(m),
+                            x.shape[0], _p(x), _p(fhat), _p(f))
     if rc:
         raise MemoryError("oracle nfft: allocation failed")
     return f
 
 
-def nfft_adjoint(x, f, N, n=None, m: int = 8) -> np.ndarray:
+def nfft_adjoint(x, f, N, n=None, m: int = 8, window="kaiser_bessel") -> np.ndarray:
     """Algorithm "adjoint NFFT" (Section 2): hhat = D^H F^H B^H f."""
     N = tuple(int(v) for v in N)
     d = len(N)
@@ -256,14 +303,14 @@ def nfft_adjoint(x, f, N, n=None, m: int = 8) -> np.ndarray:
     x = _nodes(x, d)
     f = _c128(f).reshape(-1)
     out = np.zeros(N, dtype=np.complex128)
-    rc = _load().ora_nfft_adjoint(d, _p(_i64(N)), _p(_i64(n)), int(m), x.shape[0], _p(x),
-                                  _p(f), _p(out))
+    rc = _load().ora_nfft_adjoint_w(_win(window), d, _p(_i64(N)), _p(_i64(n)), int(m),
+                                    x.shape[0], _p(x), _p(f), _p(out))
     if rc:
         raise MemoryError("oracle nfft_adjoint: allocation failed")
     return out
 
 
-def nfft_grad_x(x, c, w, n=None, m: int = 8) -> np.ndarray:
+def nfft_grad_x(x, c, w, n=None, m: int = 8, window="kaiser_bessel") -> np.ndarray:
     """(M, d) real: Re(conj(w_j) d s_c/d x_t (x_j)), s_c the NFFT approximation built from c."""
     c = _c128(c)
     d = c.ndim
@@ -271,8 +318,8 @@ def nfft_grad_x(x, c, w, n=None, m: int = 8) -> np.ndarray:
     x = _nodes(x, d)
     w = _c128(w).reshape(-1)
     gx = np.zeros((x.shape[0], d), dtype=np.float64)
-    rc = _load().ora_nfft_grad_x(d, _p(_i64(c.shape)), _p(_i64(n)), int(m), x.shape[0], _p(x),
-                                 _p(c), _p(w), _p(gx))
+    rc = _load().ora_nfft_grad_x_w(_win(window), d, _p(_i64(c.shape)), _p(_i64(n)), int(m),
+                                   x.shape[0], _p(x), _p(c), _p(w), _p(gx))
     if rc:
         raise MemoryError("oracle nfft_grad_x: allocation failed")
     return gx

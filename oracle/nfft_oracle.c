@@ -221,6 +221,85 @@ double ora_kb_phihat(int64_t k, int64_t n, int m, double b)
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* The other windows the paper names (Section 4.1: Gaussian, B-spline, sinc); their formulas are */
+/* the standard Fourier pairs (the paper defers them to Plonka-Potts-Steidl-Tasche, Ch. 7.2).    */
+/* All in grid units t = n x; each pair satisfies phihat(k) = (1/n) * FT[psi](k / n), where     */
+/* FT[psi](nu) = int psi(t) e^{-2 pi i nu t} dt.                                                */
+/* ------------------------------------------------------------------------------------------ */
+
+enum { ORA_KB = 0, ORA_GAUSS = 1, ORA_BSPLINE = 2, ORA_SINC = 3 };
+
+/* Centred cardinal B-spline of order p (support [-p/2, p/2]) by the recursion
+ * M_p(t) = ((p/2 + t) M_{p-1}(t + 1/2) + (p/2 - t) M_{p-1}(t - 1/2)) / (p - 1), M_1 = 1 on
+ * [-1/2, 1/2) (all terms non-negative). */
+double ora_bspline(int p, double t)
+{
+    if (p == 1) return (t >= -0.5 && t < 0.5) ? 1.0 : 0.0;
+    if (t <= -0.5 * p || t >= 0.5 * p) return 0.0;
+    return ((0.5 * p + t) * ora_bspline(p - 1, t + 0.5) + (0.5 * p - t) * ora_bspline(p - 1, t - 0.5)) /
+           (double)(p - 1);
+}
+
+static double ora_sinc(double u) { return u == 0.0 ? 1.0 : sin(u) / u; }
+
+/* Shape parameter of window w on an axis with FFT length n and bandwidth N:
+ * KB: b = pi (2 - 1/sigma); Gaussian: b = 2 sigma m / ((2 sigma - 1) pi);
+ * sinc: a = (2 sigma - 1) / (2 m sigma); B-spline: unused. */
+double ora_window_param(int w, int64_t n, int64_t N, int m)
+{
+    const double sigma = (double)n / (double)N;
+    switch (w) {
+    case ORA_GAUSS: return 2.0 * sigma * m / ((2.0 * sigma - 1.0) * ORA_PI);
+    case ORA_SINC: return (2.0 * sigma - 1.0) / (2.0 * m * sigma);
+    case ORA_BSPLINE: return 0.0;
+    default: return ora_kb_b(n, N);
+    }
+}
+
+/* Truncated window psi(t) (0 for |t| > m). Gaussian: e^{-t^2/b}; B-spline: M_{2m}(t);
+ * sinc: sinc^{2m}(pi a t); KB: see ora_kb_psi. */
+double ora_window_psi(int w, double t, int m, double prm)
+{
+    if (fabs(t) > (double)m) return 0.0;
+    switch (w) {
+    case ORA_GAUSS: return exp(-t * t / prm);
+    case ORA_BSPLINE: return ora_bspline(2 * m, t);
+    case ORA_SINC: return pow(ora_sinc(ORA_PI * prm * t), 2 * m);
+    default: return ora_kb_psi(t, m, prm);
+    }
+}
+
+/* d psi / d t inside the support. */
+double ora_window_dpsi(int w, double t, int m, double prm)
+{
+    if (fabs(t) > (double)m) return 0.0;
+    switch (w) {
+    case ORA_GAUSS: return -2.0 * t / prm * exp(-t * t / prm);
+    case ORA_BSPLINE: return ora_bspline(2 * m - 1, t + 0.5) - ora_bspline(2 * m - 1, t - 0.5);
+    case ORA_SINC: {
+        const double u = ORA_PI * prm * t;
+        if (u == 0.0) return 0.0;
+        const double ds = (u * cos(u) - sin(u)) / (u * u);  /* d sinc / du */
+        return 2.0 * m * pow(ora_sinc(u), 2 * m - 1) * ds * ORA_PI * prm;
+    }
+    default: return ora_kb_dpsi(t, m, prm);
+    }
+}
+
+/* phihat(k) = (1/n) FT[psi_untruncated](k/n). Gaussian: sqrt(pi b) e^{-b (pi k/n)^2} / n;
+ * B-spline: sinc^{2m}(pi k / n) / n; sinc: M_{2m}(k / (n a)) / (n a); KB: ora_kb_phihat. */
+double ora_window_phihat(int w, int64_t k, int64_t n, int m, double prm)
+{
+    const double nu = (double)k / (double)n;
+    switch (w) {
+    case ORA_GAUSS: return sqrt(ORA_PI * prm) * exp(-prm * ORA_PI * ORA_PI * nu * nu) / (double)n;
+    case ORA_BSPLINE: return pow(ora_sinc(ORA_PI * nu), 2 * m) / (double)n;
+    case ORA_SINC: return ora_bspline(2 * m, nu / prm) / (prm * (double)n);
+    default: return ora_kb_phihat(k, n, m, prm);
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* FFT (Algorithm "NFFT", d-variate FFT step)                                                  */
 /* ------------------------------------------------------------------------------------------ */
 
@@ -290,17 +369,19 @@ void ora_fft(int d, const int64_t *n, cplx *a, int sign)
 /* The three steps of Algorithm "NFFT" and of Algorithm "adjoint NFFT"                         */
 /* ------------------------------------------------------------------------------------------ */
 
-/* Product over the axes of the Fourier coefficients c_k = phihat_t(k_t) of the window. */
-static double phihat_prod(int d, const int64_t *k, const int64_t *N, const int64_t *n, int m)
+/* Product over the axes of the Fourier coefficients c_k = phihat_t(k_t) of window w. */
+static double phihat_prod(int w, int d, const int64_t *k, const int64_t *N, const int64_t *n, int m)
 {
     double c = 1.0;
-    for (int t = 0; t < d; t++) c *= ora_kb_phihat(k[t], n[t], m, ora_kb_b(n[t], N[t]));
+    for (int t = 0; t < d; t++)
+        c *= ora_window_phihat(w, k[t], n[t], m, ora_window_param(w, n[t], N[t], m));
     return c;
 }
 
 /* Step D (Algorithm "NFFT", first loop; Section 2, choice of ghat):
  * ghat_{k mod n} = fhat_k / (|I_n| c_k) for k in I_N, and 0 on I_n \ I_N. */
-void ora_nfft_D(int d, const int64_t *N, const int64_t *n, int m, const cplx *fhat, cplx *ghat)
+void ora_nfft_D_w(int w, int d, const int64_t *N, const int64_t *n, int m, const cplx *fhat,
+                  cplx *ghat)
 {
     const int64_t nk = prod64(d, N), ng = prod64(d, n);
     memset(ghat, 0, (size_t)ng * sizeof(cplx));
@@ -313,13 +394,19 @@ void ora_nfft_D(int d, const int64_t *N, const int64_t *n, int m, const cplx *fh
         }
         int64_t g = 0;
         for (int t = 0; t < d; t++) g = g * n[t] + mod64(k[t], n[t]);
-        ghat[g] = fhat[idx] / ((double)ng * phihat_prod(d, k, N, n, m));
+        ghat[g] = fhat[idx] / ((double)ng * phihat_prod(w, d, k, N, n, m));
     }
+}
+
+void ora_nfft_D(int d, const int64_t *N, const int64_t *n, int m, const cplx *fhat, cplx *ghat)
+{
+    ora_nfft_D_w(ORA_KB, d, N, n, m, fhat, ghat);
 }
 
 /* Step D^H (Algorithm "adjoint NFFT", last loop):
  * hhat_k = ghat_{k mod n} / (|I_n| c_k) for k in I_N. */
-void ora_nfft_DH(int d, const int64_t *N, const int64_t *n, int m, const cplx *ghat, cplx *fhat)
+void ora_nfft_DH_w(int w, int d, const int64_t *N, const int64_t *n, int m, const cplx *ghat,
+                   cplx *fhat)
 {
     const int64_t nk = prod64(d, N), ng = prod64(d, n);
     for (int64_t idx = 0; idx < nk; idx++) {
@@ -331,8 +418,13 @@ void ora_nfft_DH(int d, const int64_t *N, const int64_t *n, int m, const cplx *g
         }
         int64_t g = 0;
         for (int t = 0; t < d; t++) g = g * n[t] + mod64(k[t], n[t]);
-        fhat[idx] = ghat[g] / ((double)ng * phihat_prod(d, k, N, n, m));
+        fhat[idx] = ghat[g] / ((double)ng * phihat_prod(w, d, k, N, n, m));
     }
+}
+
+void ora_nfft_DH(int d, const int64_t *N, const int64_t *n, int m, const cplx *ghat, cplx *fhat)
+{
+    ora_nfft_DH_w(ORA_KB, d, N, n, m, ghat, fhat);
 }
 
 /* The box of grid indices I_{n,m}(x_j) of eq. Inm: for each axis, the integers l with
@@ -350,11 +442,12 @@ static void support_box(int d, const int64_t *n, int m, const double *xj, double
 /* Step B (Algorithm "NFFT", last loop; eq. s_approx):
  * f_j = sum_{l in I_{n,m}(x_j)} g_{l mod n} psi~(x_j - l/n), with the tensor-product window
  * psi~(y) = prod_t psi_t(n_t y_t). */
-void ora_nfft_B(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
+void ora_nfft_B_w(int w, int d, const int64_t *N, const int64_t *n, int m, int64_t M,
+                  const double *x,
                 const cplx *g, cplx *f)
 {
     double b[3] = {0, 0, 0};
-    for (int t = 0; t < d; t++) b[t] = ora_kb_b(n[t], N[t]);
+    for (int t = 0; t < d; t++) b[t] = ora_window_param(w, n[t], N[t], m);
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < M; j++) {
         double nx[3];
@@ -363,13 +456,13 @@ void ora_nfft_B(int d, const int64_t *N, const int64_t *n, int m, int64_t M, con
         for (int t = 0; t < d; t++) l[t] = lo[t];
         cplx acc = 0;
         for (;;) {
-            double w = 1.0;
+            double wt = 1.0;
             int64_t gi = 0;
             for (int t = 0; t < d; t++) {
-                w *= ora_kb_psi(nx[t] - (double)l[t], m, b[t]);
+                wt *= ora_window_psi(w, nx[t] - (double)l[t], m, b[t]);
                 gi = gi * n[t] + mod64(l[t], n[t]);
             }
-            acc += g[gi] * w;
+            acc += g[gi] * wt;
             int t = d - 1;
             while (t >= 0 && l[t] == hi[t]) {
                 l[t] = lo[t];
@@ -384,11 +477,12 @@ void ora_nfft_B(int d, const int64_t *N, const int64_t *n, int m, int64_t M, con
 
 /* Step B^H (Algorithm "adjoint NFFT", first loop):
  * g_l = sum_{j in I^T_{n,m}(l)} f_j psi~(x_j - l/n); evaluated node by node. */
-void ora_nfft_BH(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
+void ora_nfft_BH_w(int w, int d, const int64_t *N, const int64_t *n, int m, int64_t M,
+                  const double *x,
                  const cplx *f, cplx *g)
 {
     double b[3] = {0, 0, 0};
-    for (int t = 0; t < d; t++) b[t] = ora_kb_b(n[t], N[t]);
+    for (int t = 0; t < d; t++) b[t] = ora_window_param(w, n[t], N[t], m);
     memset(g, 0, (size_t)prod64(d, n) * sizeof(cplx));
     for (int64_t j = 0; j < M; j++) {
         double nx[3];
@@ -396,13 +490,13 @@ void ora_nfft_BH(int d, const int64_t *N, const int64_t *n, int m, int64_t M, co
         support_box(d, n, m, x + j * d, nx, lo, hi);
         for (int t = 0; t < d; t++) l[t] = lo[t];
         for (;;) {
-            double w = 1.0;
+            double wt = 1.0;
             int64_t gi = 0;
             for (int t = 0; t < d; t++) {
-                w *= ora_kb_psi(nx[t] - (double)l[t], m, b[t]);
+                wt *= ora_window_psi(w, nx[t] - (double)l[t], m, b[t]);
                 gi = gi * n[t] + mod64(l[t], n[t]);
             }
-            g[gi] += f[j] * w;
+            g[gi] += f[j] * wt;
             int t = d - 1;
             while (t >= 0 && l[t] == hi[t]) {
                 l[t] = lo[t];
@@ -417,11 +511,12 @@ void ora_nfft_BH(int d, const int64_t *N, const int64_t *n, int m, int64_t M, co
 /* Derivative of the approximation s of eq. s_approx with respect to the node coordinates:
  * ds[j*d + t] = d s / d x_t (x_j) = sum_{l} g_{l mod n} n_t psi_t'(n_t x_t - l_t)
  *               prod_{u != t} psi_u(n_u x_u - l_u), over the same support box. */
-void ora_nfft_dB(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
+void ora_nfft_dB_w(int w, int d, const int64_t *N, const int64_t *n, int m, int64_t M,
+                  const double *x,
                  const cplx *g, cplx *ds)
 {
     double b[3] = {0, 0, 0};
-    for (int t = 0; t < d; t++) b[t] = ora_kb_b(n[t], N[t]);
+    for (int t = 0; t < d; t++) b[t] = ora_window_param(w, n[t], N[t], m);
 #pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < M; j++) {
         double nx[3];
@@ -430,17 +525,17 @@ void ora_nfft_dB(int d, const int64_t *N, const int64_t *n, int m, int64_t M, co
         for (int t = 0; t < d; t++) l[t] = lo[t];
         cplx acc[3] = {0, 0, 0};
         for (;;) {
-            double w[3], dw[3];
+            double wv[3], dw[3];
             int64_t gi = 0;
             for (int t = 0; t < d; t++) {
-                w[t] = ora_kb_psi(nx[t] - (double)l[t], m, b[t]);
-                dw[t] = (double)n[t] * ora_kb_dpsi(nx[t] - (double)l[t], m, b[t]);
+                wv[t] = ora_window_psi(w, nx[t] - (double)l[t], m, b[t]);
+                dw[t] = (double)n[t] * ora_window_dpsi(w, nx[t] - (double)l[t], m, b[t]);
                 gi = gi * n[t] + mod64(l[t], n[t]);
             }
             for (int t = 0; t < d; t++) {
                 double p = dw[t];
                 for (int u = 0; u < d; u++)
-                    if (u != t) p *= w[u];
+                    if (u != t) p *= wv[u];
                 acc[t] += g[gi] * p;
             }
             int t = d - 1;
@@ -455,42 +550,73 @@ void ora_nfft_dB(int d, const int64_t *N, const int64_t *n, int m, int64_t M, co
     }
 }
 
+
+void ora_nfft_B(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
+                const cplx *g, cplx *f)
+{
+    ora_nfft_B_w(ORA_KB, d, N, n, m, M, x, g, f);
+}
+
+void ora_nfft_BH(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
+                 const cplx *f, cplx *g)
+{
+    ora_nfft_BH_w(ORA_KB, d, N, n, m, M, x, f, g);
+}
+
+void ora_nfft_dB(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
+                 const cplx *g, cplx *ds)
+{
+    ora_nfft_dB_w(ORA_KB, d, N, n, m, M, x, g, ds);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Whole transforms                                                                           */
 /* ------------------------------------------------------------------------------------------ */
 
-/* Algorithm "NFFT": D, then the forward d-variate FFT, then B. */
-int ora_nfft(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
-             const cplx *fhat, cplx *f)
+/* Algorithm "NFFT": D, then the forward d-variate FFT, then B (window w). */
+int ora_nfft_w(int w, int d, const int64_t *N, const int64_t *n, int m, int64_t M,
+               const double *x, const cplx *fhat, cplx *f)
 {
     cplx *g = (cplx *)malloc((size_t)prod64(d, n) * sizeof(cplx));
     if (!g) return 1;
-    ora_nfft_D(d, N, n, m, fhat, g);
+    ora_nfft_D_w(w, d, N, n, m, fhat, g);
     ora_fft(d, n, g, -1);
-    ora_nfft_B(d, N, n, m, M, x, g, f);
+    ora_nfft_B_w(w, d, N, n, m, M, x, g, f);
     free(g);
     return 0;
 }
 
+int ora_nfft(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
+             const cplx *fhat, cplx *f)
+{
+    return ora_nfft_w(ORA_KB, d, N, n, m, M, x, fhat, f);
+}
+
 /* Algorithm "adjoint NFFT": B^H, then the inverse (sign +1) d-variate FFT, then D^H. */
-int ora_nfft_adjoint(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
-                     const cplx *f, cplx *fhat)
+int ora_nfft_adjoint_w(int w, int d, const int64_t *N, const int64_t *n, int m, int64_t M,
+                       const double *x, const cplx *f, cplx *fhat)
 {
     cplx *g = (cplx *)malloc((size_t)prod64(d, n) * sizeof(cplx));
     if (!g) return 1;
-    ora_nfft_BH(d, N, n, m, M, x, f, g);
+    ora_nfft_BH_w(w, d, N, n, m, M, x, f, g);
     ora_fft(d, n, g, +1);
-    ora_nfft_DH(d, N, n, m, g, fhat);
+    ora_nfft_DH_w(w, d, N, n, m, g, fhat);
     free(g);
     return 0;
+}
+
+int ora_nfft_adjoint(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
+                     const cplx *f, cplx *fhat)
+{
+    return ora_nfft_adjoint_w(ORA_KB, d, N, n, m, M, x, f, fhat);
 }
 
 /* Node gradient of a real loss through the NFFT (PyTorch's conjugate-Wirtinger convention):
  * gx[j*d + t] = Re( conj(w_j) * d s_c / d x_t (x_j) ), where s_c is the NFFT approximation
  * built from the coefficients c (steps D and F), and w is the upstream weight per node.
  * For the forward transform c = fhat and w = grad f; for the adjoint c = grad hhat and w = f. */
-int ora_nfft_grad_x(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
-                    const cplx *c, const cplx *w, double *gx)
+int ora_nfft_grad_x_w(int win, int d, const int64_t *N, const int64_t *n, int m, int64_t M,
+                      const double *x, const cplx *c, const cplx *w, double *gx)
 {
     cplx *g = (cplx *)malloc((size_t)prod64(d, n) * sizeof(cplx));
     cplx *ds = (cplx *)malloc((size_t)(M > 0 ? M : 1) * d * sizeof(cplx));
@@ -499,12 +625,18 @@ int ora_nfft_grad_x(int d, const int64_t *N, const int64_t *n, int m, int64_t M,
         free(ds);
         return 1;
     }
-    ora_nfft_D(d, N, n, m, c, g);
+    ora_nfft_D_w(win, d, N, n, m, c, g);
     ora_fft(d, n, g, -1);
-    ora_nfft_dB(d, N, n, m, M, x, g, ds);
+    ora_nfft_dB_w(win, d, N, n, m, M, x, g, ds);
     for (int64_t j = 0; j < M; j++)
         for (int t = 0; t < d; t++) gx[j * d + t] = creal(conj(w[j]) * ds[j * d + t]);
     free(g);
     free(ds);
     return 0;
+}
+
+int ora_nfft_grad_x(int d, const int64_t *N, const int64_t *n, int m, int64_t M, const double *x,
+                    const cplx *c, const cplx *w, double *gx)
+{
+    return ora_nfft_grad_x_w(ORA_KB, d, N, n, m, M, x, c, w, gx);
 }
