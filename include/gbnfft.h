@@ -127,8 +127,9 @@ int nfft_adjoint_host(nfft_plan plan, const void *f_host, void *fhat_host);
  * call (NFFT_OK if none), then clear it. A CUDA error seen while waiting gives NFFT_ECUDA. */
 int nfft_status(nfft_plan plan);
 
-/* Plan parameters after defaults: d, N[3], n[3], M, m, dtype, and the tile (bin) size used to
- * sort the nodes. Unused trailing entries are 0. */
+/* Plan parameters after defaults: d, N[3], n[3], M, m, dtype, the tile (bin) size used to
+ * sort the nodes, the workspace size and the window (NFFT_OPT_WINDOW). Unused trailing entries
+ * are 0. */
 typedef struct nfft_info {
     int d;
     int m;
@@ -138,6 +139,7 @@ typedef struct nfft_info {
     int64_t n[3];
     int64_t bin[3];
     size_t workspace_bytes;
+    int window;
 } nfft_info;
 int nfft_get_info(nfft_plan plan, nfft_info *info);
 
@@ -159,8 +161,20 @@ enum nfft_stage {
 int nfft_profile(nfft_plan plan, int enable);
 int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
 
-/* Tuning options (defaults are chosen per plan; the values below change only speed, never the
- * result beyond rounding).
+/* Plan options. NFFT_OPT_WINDOW selects the window function (Section 4.1 names the choices;
+ * the default is Kaiser-Bessel); it changes the result (the approximation error, not the
+ * exact transform the plan approximates). The others only tune speed and never change the
+ * result beyond rounding.
+ *   NFFT_OPT_WINDOW         0 Kaiser-Bessel psi(t) = sinh(b sqrt(m^2 - t^2)) / (pi sqrt(...)),
+ *                           b = pi (2 - 1/sigma); 1 Gaussian psi(t) = exp(-t^2 / b),
+ *                           b = 2 sigma m / ((2 sigma - 1) pi); 2 B-spline psi(t) = M_2m(t),
+ *                           the centred cardinal B-spline of order 2m; 3 sinc
+ *                           psi(t) = sinc^2m(pi a t), a = (2 sigma - 1) / (2 m sigma). t is in
+ *                           grid units (t = n_t x_t), sigma = n_t / N_t per axis, and psi is cut
+ *                           off to |t| <= m. The node precomputation stays valid. Waits for the
+ *                           device to go idle, then rewrites the plan's tables in place; a CUDA graph
+ *                           captured before the change keeps the old edge constants in its
+ *                           kernel arguments and must be captured again.
  *   NFFT_OPT_SPREAD_METHOD  0 automatic, 1 one thread per node with shared-memory atomics,
  *                           2 one warp per node with shared-memory atomics,
  *                           3 one warp per node with a private tile per warp (no atomics),
@@ -178,7 +192,8 @@ enum nfft_option {
     NFFT_OPT_BIN_0 = 2,
     NFFT_OPT_BIN_1 = 3,
     NFFT_OPT_BIN_2 = 4,
-    NFFT_OPT_INTERP_METHOD = 5
+    NFFT_OPT_INTERP_METHOD = 5,
+    NFFT_OPT_WINDOW = 6
 };
 int nfft_set_option(nfft_plan plan, int key, int64_t value);
 

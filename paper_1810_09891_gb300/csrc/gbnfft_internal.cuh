@@ -18,14 +18,15 @@ constexpr int kMaxDim = 3;
 constexpr int kMaxM = 8;           // window cutoffs 1..8 are instantiated
 constexpr int kMaxSub = 1024;      // nodes per spreading subproblem (one CTA tile)
 
-// Per-axis constants of the normalised window psibar(t) = psi(t) / psi(0), in grid units:
-//   psibar(t) = kscale * sinh(b u) / u,  u = sqrt(m^2 - t^2),  kscale = m / sinh(b m).
-// psi(0) is folded into the deconvolution factors, which keeps FP32 values in range at any m.
+// Per-axis constants of the normalised window psibar(t) = psi(t) / psi(0), in grid units
+// (Kaiser-Bessel, Gaussian, B-spline or sinc; the pairs are written out on the host at plan
+// creation). psi(0) is folded into the deconvolution factors, which keeps FP32 values in range
+// at any m. The kernels see the window only through the per-tap polynomials below and these
+// two edge constants.
 struct AxisWin {
-    double b;       // shape parameter b = pi (2 - 1/sigma)
-    double kscale;  // m / sinh(b m)
-    double edge_w;  // psibar(+-m) = kscale * b (the tap of a node on a grid point)
-    double edge_dw; // d psibar / dt at t = m, = -kscale * m * b^3 / 3
+    double prm;     // shape parameter: KB b, Gaussian b, sinc a (B-spline: unused)
+    double edge_w;  // psibar(+-m) (the extra tap of a node on a grid point)
+    double edge_dw; // d psibar / dt at t = m (from inside the support)
 };
 
 // Window values are evaluated from per-tap polynomials: for a node with offset frac in [0, 1]

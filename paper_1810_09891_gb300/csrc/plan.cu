@@ -68,26 +68,103 @@ void twiddle(int64_t j, int64_t L, double *re, double *im)
     *im = -s;
 }
 
-// Normalised window psibar(t) = m sinh(b u) / (u sinh(b m)), u = sqrt(m^2 - t^2), |t| <= m.
-double psibar_host(double t, int m, double b)
+// ------------------------------------------------------------------------------ windows
+// The window pairs (psi in grid units t = n x, and n * phihat(k), the Fourier transform of the
+// untruncated window at frequency k / n). Kaiser-Bessel is the paper's default (Section 4.1);
+// Gaussian, B-spline and sinc are the alternatives it names there, with their standard pairs.
+enum WindowKind { kWinKB = 0, kWinGauss = 1, kWinBspline = 2, kWinSinc = 3 };
+
+// Shape parameter: KB b = pi (2 - 1/sigma); Gaussian b = 2 sigma m / ((2 sigma - 1) pi);
+// sinc a = (2 sigma - 1) / (2 m sigma); B-spline none.
+double window_param(int kind, double sigma, int m)
 {
-    const double s = (double(m) - t) * (double(m) + t);
-    if (s < 0.0) return 0.0;
-    const double kscale = double(m) / std::sinh(b * double(m));
-    if (s == 0.0) return kscale * b;
-    const double u = std::sqrt(s);
-    return kscale * std::sinh(b * u) / u;
+    switch (kind) {
+    case kWinGauss: return 2.0 * sigma * m / ((2.0 * sigma - 1.0) * kPi);
+    case kWinSinc: return (2.0 * sigma - 1.0) / (2.0 * m * sigma);
+    case kWinBspline: return 0.0;
+    default: return kPi * (2.0 - 1.0 / sigma);
+    }
+}
+
+// Centred cardinal B-spline M_p(t) by the order recursion, evaluated bottom-up over the
+// p (p+1)/2 shifted points it needs (values non-negative, no cancellation).
+double cardinal_bspline(int p, double t)
+{
+    if (!(t > -0.5 * p && t < 0.5 * p)) return 0.0;
+    double v[40];
+    for (int j = 0; j < p; j++) {  // level 1 at u_j = t + (p - 1)/2 - j
+        const double u = t + 0.5 * (p - 1) - j;
+        v[j] = (u >= -0.5 && u < 0.5) ? 1.0 : 0.0;
+    }
+    for (int k = 2; k <= p; k++) {  // level k at u_j = t + (p - k)/2 - j, j = 0..p-k
+        for (int j = 0; j <= p - k; j++) {
+            const double u = t + 0.5 * (p - k) - j;
+            v[j] = ((0.5 * k + u) * v[j] + (0.5 * k - u) * v[j + 1]) / (k - 1);
+        }
+    }
+    return v[0];
+}
+
+double sinc_host(double u) { return u == 0.0 ? 1.0 : std::sin(u) / u; }
+
+// Truncated window psi(t), |t| <= m.
+double psi_host(int kind, double t, int m, double prm)
+{
+    if (std::fabs(t) > double(m)) return 0.0;
+    switch (kind) {
+    case kWinGauss: return std::exp(-t * t / prm);
+    case kWinBspline: return cardinal_bspline(2 * m, t);
+    case kWinSinc: return std::pow(sinc_host(kPi * prm * t), 2 * m);
+    default: {
+        const double s = (double(m) - t) * (double(m) + t);
+        if (s <= 0.0) return prm / kPi;
+        const double u = std::sqrt(s);
+        return std::sinh(prm * u) / (kPi * u);
+    }
+    }
+}
+
+// n * phihat(k): the Fourier transform of the untruncated psi at frequency k / n.
+double nphihat_host(int kind, double k, double n, int m, double prm)
+{
+    const double nu = k / n;
+    switch (kind) {
+    case kWinGauss: return std::sqrt(kPi * prm) * std::exp(-prm * kPi * kPi * nu * nu);
+    case kWinBspline: return std::pow(sinc_host(kPi * nu), 2 * m);
+    case kWinSinc: return cardinal_bspline(2 * m, nu / prm) / prm;
+    default: {
+        const double w = 2.0 * kPi * nu;
+        return bessel_i0(double(m) * std::sqrt(prm * prm - w * w));
+    }
+    }
+}
+
+// d psi / d t at t = m (from inside the support).
+double dpsi_edge_host(int kind, int m, double prm)
+{
+    switch (kind) {
+    case kWinGauss: return -2.0 * m / prm * std::exp(-double(m) * m / prm);
+    case kWinBspline: return 0.0;  // M_{2m} is flat (C^{2m-2}) at its support edge
+    case kWinSinc: {
+        const double u = kPi * prm * m;
+        const double ds = (u * std::cos(u) - std::sin(u)) / (u * u);
+        return 2.0 * m * std::pow(sinc_host(u), 2 * m - 1) * ds * kPi * prm;
+    }
+    default: return -double(m) * prm * prm * prm / (3.0 * kPi);
+    }
 }
 
 // Monomial coefficients (in z = 2 frac - 1) of the degree-deg Chebyshev interpolant of
-// frac -> psibar(frac + m - i) on [0, 1] (interpolation at the deg + 1 Chebyshev points).
-void fit_tap_poly(int m, double b, int i, int deg, double *mono)
+// frac -> psibar(frac + m - i) = psi(frac + m - i) / psi(0) on [0, 1] (interpolation at the
+// deg + 1 Chebyshev points).
+void fit_tap_poly(int kind, int m, double prm, int i, int deg, double *mono)
 {
     const int n = deg + 1;
+    const double psi0 = psi_host(kind, 0.0, m, prm);
     double f[32], c[32], Tprev[32], Tcur[32], Tnext[32];
     for (int k = 0; k < n; k++) {
         const double z = std::cos(kPi * (k + 0.5) / n);
-        f[k] = psibar_host(0.5 * (z + 1.0) + double(m) - double(i), m, b);
+        f[k] = psi_host(kind, 0.5 * (z + 1.0) + double(m) - double(i), m, prm) / psi0;
     }
     for (int j = 0; j < n; j++) {
         double acc = 0.0;
@@ -130,8 +207,11 @@ struct gbnfft_plan {
     int nbins = 0;
     int max_subs = 0;
     int64_t bin_req[3] = {0, 0, 0};  // requested bin sizes (0 = default)
-    // plan-owned device tables
+    int window = 0;  // WindowKind
+    // plan-owned device tables: [deconv_t, twiddles_t]_t, window polynomials, status word
     void *tables = nullptr;
+    size_t off_dc[3] = {0, 0, 0}, off_tw[3] = {0, 0, 0}, off_poly = 0, off_status = 0;
+    size_t tbytes = 0;
     void *deconv[3] = {nullptr, nullptr, nullptr};  // plan precision
     void *tw[3] = {nullptr, nullptr, nullptr};
     int *d_status = nullptr;
@@ -194,8 +274,8 @@ void layout_workspace(gbnfft_plan *p)
     p->ws_need = align_up(off, 256);
 }
 
-// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 16 x 16,
-// 3-D 8 x 8 x 8), clipped to n_t. Recomputes the bin counts and the workspace layout.
+// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 16 x 16
+// (8 x 16 in FP64), 3-D 8 x 8 x 8), clipped to n_t. Recomputes the bin counts and the workspace layout.
 void setup_bins(gbnfft_plan *p)
 {
     Geom &g = p->geom;
@@ -209,6 +289,8 @@ void setup_bins(gbnfft_plan *p)
             continue;
         }
         int64_t bs = p->bin_req[t] > 0 ? p->bin_req[t] : bin_default[p->d - 1][t];
+        // 2-D FP64 runs fastest with the eight-lane spreading form on 8 x 16 bins (measured)
+        if (p->bin_req[t] <= 0 && p->d == 2 && p->dtype == NFFT_FP64 && t == 0) bs = 8;
         if (bs > p->n[t]) bs = p->n[t];
         g.bs[t] = (int)bs;
         g.bslog[t] = ilog2(bs);
@@ -438,6 +520,91 @@ int nfft_use_device(int device)
     return cudaSetDevice(device) == cudaSuccess ? NFFT_OK : NFFT_ECUDA;
 }
 
+// Per-axis window shape parameter and the edge constants the kernels take by value:
+// psibar(m) (the extra tap of a node on a grid point) and d psibar / dt at t = m.
+static void set_window_constants(gbnfft_plan *p)
+{
+    Geom &g = p->geom;
+    for (int t = 0; t < p->d; t++) {
+        const double sigma = double(p->n[t]) / double(p->N[t]);
+        const double prm = window_param(p->window, sigma, p->m);
+        const double psi0 = psi_host(p->window, 0.0, p->m, prm);
+        g.win[t].prm = prm;
+        g.win[t].edge_w = psi_host(p->window, double(p->m), p->m, prm) / psi0;
+        g.win[t].edge_dw = dpsi_edge_host(p->window, p->m, prm) / psi0;
+    }
+}
+
+// Host image of the tables below off_status (the layout is fixed by d, N, n, m and precision).
+static void fill_tables(const gbnfft_plan *p, char *host)
+{
+    const bool fp64 = p->dtype == NFFT_FP64;
+    const int m = p->m;
+    const int deg = poly_degree(fp64, m);
+    const size_t poly_axis = size_t(poly_axis_stride(fp64, m));
+    for (int t = 0; t < p->d; t++) {
+        const double prm = p->geom.win[t].prm;
+        const double psi0 = psi_host(p->window, 0.0, m, prm);
+        // psi_t(0) / (n_t phihat_t(k)): the per-axis factor of 1 / (|I_n| c_k) (Algorithm
+        // "NFFT", deconvolution step) for the window normalised to psibar(0) = 1
+        for (int64_t i = 0; i < p->N[t]; i++) {
+            const double k = double(i - p->N[t] / 2);
+            const double dc = psi0 / nphihat_host(p->window, k, double(p->n[t]), m, prm);
+            if (fp64)
+                reinterpret_cast<double *>(host + p->off_dc[t])[i] = dc;
+            else
+                reinterpret_cast<float *>(host + p->off_dc[t])[i] = (float)dc;
+        }
+        // window polynomials of this axis: coefficient k of tap i at [k * kPolyTaps + i - 1]
+        for (int i = 1; i <= 2 * m; i++) {
+            double mono[32];
+            fit_tap_poly(p->window, m, prm, i, deg, mono);
+            for (int k = 0; k <= deg; k++) {
+                const size_t e = size_t(t) * poly_axis + size_t(k) * kPolyTaps + size_t(i - 1);
+                if (fp64)
+                    reinterpret_cast<double *>(host + p->off_poly)[e] = mono[k];
+                else
+                    reinterpret_cast<float *>(host + p->off_poly)[e] = (float)mono[k];
+            }
+        }
+        for (int64_t j = 0; j < p->n[t]; j++) {
+            double re, im;
+            twiddle(j, p->n[t], &re, &im);
+            if (fp64)
+                reinterpret_cast<double2 *>(host + p->off_tw[t])[j] = make_double2(re, im);
+            else
+                reinterpret_cast<float2 *>(host + p->off_tw[t])[j] =
+                    make_float2((float)re, (float)im);
+        }
+    }
+}
+
+// Switch the window: new edge constants and tables, written over the old ones in place (the
+// device pointers, the status word and the node preprocessing stay valid).
+static int set_window(gbnfft_plan *p, int kind)
+{
+    if (kind == p->window) return NFFT_OK;
+    const int old = p->window;
+    p->window = kind;
+    set_window_constants(p);
+    char *host = static_cast<char *>(std::calloc(1, p->tbytes));
+    if (!host) {
+        p->window = old;
+        set_window_constants(p);
+        return NFFT_ENOMEM;
+    }
+    fill_tables(p, host);
+    // the old tables may be read by work queued on any stream of the device
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(p->tables, host, p->off_status, cudaMemcpyHostToDevice);
+    std::free(host);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return NFFT_ECUDA;
+    }
+    return NFFT_OK;
+}
+
 int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const int64_t *n, int m,
                      int dtype)
 {
@@ -499,81 +666,35 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
             g.n[t] = 1;
             g.nlog[t] = 0;
             g.N[t] = 1;
-            g.win[t] = AxisWin{0.0, 0.0};
+            g.win[t] = AxisWin{0.0, 0.0, 0.0};
             continue;
         }
         g.n[t] = (int)nn[t];
         g.nlog[t] = ilog2(nn[t]);
         g.N[t] = (int)NNv[t];
-        const double sigma = double(nn[t]) / double(NNv[t]);
-        const double b = kPi * (2.0 - 1.0 / sigma);
-        g.win[t].b = b;
-        g.win[t].kscale = double(m) / std::sinh(b * double(m));
-        g.win[t].edge_w = g.win[t].kscale * b;
-        g.win[t].edge_dw = -g.win[t].kscale * double(m) * b * b * b / 3.0;
     }
+    set_window_constants(p);
     setup_bins(p);
 
-    // tables: deconvolution factors (FP64, per axis) and twiddles (plan precision, per axis)
+    // tables: deconvolution factors and twiddles per axis, window polynomials, status word
     size_t tbytes = 0;
-    size_t off_dc[3] = {0, 0, 0}, off_tw[3] = {0, 0, 0};
     for (int t = 0; t < d; t++) {
-        off_dc[t] = tbytes;
+        p->off_dc[t] = tbytes;
         tbytes = align_up(tbytes + size_t(NNv[t]) * p->rsize, 256);
-        off_tw[t] = tbytes;
+        p->off_tw[t] = tbytes;
         tbytes = align_up(tbytes + size_t(nn[t]) * p->csize, 256);
     }
-    const bool fp64 = dtype == NFFT_FP64;
-    const int deg = poly_degree(fp64, m);
-    const size_t poly_axis = size_t(poly_axis_stride(fp64, m));
-    const size_t off_poly = tbytes;
-    tbytes = align_up(tbytes + size_t(d) * poly_axis * p->rsize, 256);
-    const size_t off_status = tbytes;
+    p->off_poly = tbytes;
+    tbytes = align_up(tbytes + size_t(d) * poly_axis_stride(dtype == NFFT_FP64, m) * p->rsize, 256);
+    p->off_status = tbytes;
     tbytes += 256;
+    p->tbytes = tbytes;
     char *host = static_cast<char *>(std::calloc(1, tbytes));
     if (!host) {
         delete p;
         return NFFT_ENOMEM;
     }
-    for (int t = 0; t < d; t++) {
-        // psi_t(0) / (n_t phihat_t(k)) with phihat_t(k) = I0(m sqrt(b^2 - (2 pi k/n)^2)) / n_t:
-        // the per-axis factor of 1/(|I_n| c_k) (Algorithm "NFFT" line 2) for the window
-        // normalised to psibar(0) = 1.
-        const double b = g.win[t].b;
-        const double psi0 = std::sinh(b * m) / (kPi * m);
-        for (int64_t i = 0; i < NNv[t]; i++) {
-            const double k = double(i - NNv[t] / 2);
-            const double w = 2.0 * kPi * k / double(nn[t]);
-            const double dc = psi0 / bessel_i0(double(m) * std::sqrt(b * b - w * w));
-            if (dtype == NFFT_FP64)
-                reinterpret_cast<double *>(host + off_dc[t])[i] = dc;
-            else
-                reinterpret_cast<float *>(host + off_dc[t])[i] = (float)dc;
-        }
-        // window polynomials of this axis: coefficient k of tap i at [k * kPolyTaps + i - 1]
-        for (int i = 1; i <= 2 * m; i++) {
-            double mono[32];
-            fit_tap_poly(m, b, i, deg, mono);
-            for (int k = 0; k <= deg; k++) {
-                const size_t e = size_t(t) * poly_axis + size_t(k) * kPolyTaps + size_t(i - 1);
-                if (fp64)
-                    reinterpret_cast<double *>(host + off_poly)[e] = mono[k];
-                else
-                    reinterpret_cast<float *>(host + off_poly)[e] = (float)mono[k];
-            }
-        }
-        for (int64_t j = 0; j < nn[t]; j++) {
-            double re, im;
-            twiddle(j, nn[t], &re, &im);
-            if (dtype == NFFT_FP32) {
-                float2 *tw = reinterpret_cast<float2 *>(host + off_tw[t]);
-                tw[j] = make_float2((float)re, (float)im);
-            } else {
-                double2 *tw = reinterpret_cast<double2 *>(host + off_tw[t]);
-                tw[j] = make_double2(re, im);
-            }
-        }
-    }
+    fill_tables(p, host);
     cudaError_t e = cudaMalloc(&p->tables, tbytes);
     if (e == cudaSuccess) e = cudaMemcpy(p->tables, host, tbytes, cudaMemcpyHostToDevice);
     std::free(host);
@@ -585,11 +706,11 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
     }
     char *tb = static_cast<char *>(p->tables);
     for (int t = 0; t < d; t++) {
-        p->deconv[t] = tb + off_dc[t];
-        p->tw[t] = tb + off_tw[t];
+        p->deconv[t] = tb + p->off_dc[t];
+        p->tw[t] = tb + p->off_tw[t];
     }
-    p->d_status = reinterpret_cast<int *>(tb + off_status);
-    g.poly = tb + off_poly;
+    p->d_status = reinterpret_cast<int *>(tb + p->off_status);
+    g.poly = tb + p->off_poly;
     *out = p;
     return NFFT_OK;
 }
@@ -656,6 +777,7 @@ int nfft_get_info(nfft_plan p, nfft_info *info)
         info->bin[t] = p->geom.bs[t];
     }
     info->workspace_bytes = p->ws_need;
+    info->window = p->window;
     return NFFT_OK;
 }
 
@@ -742,6 +864,10 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
         if (value < kInterpAuto || value > kInterpTile) return NFFT_EINVAL;
         p->geom.interp_method = (int)value;
         return NFFT_OK;
+    case NFFT_OPT_WINDOW:
+        if (value < kWinKB || value > kWinSinc) return NFFT_EINVAL;
+        set_device(p);
+        return set_window(p, (int)value);
     case NFFT_OPT_BIN_0:
     case NFFT_OPT_BIN_1:
     case NFFT_OPT_BIN_2: {

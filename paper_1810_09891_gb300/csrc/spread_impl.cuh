@@ -651,8 +651,10 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
     for (int t = 0; t < D; t++) cells *= (size_t)(g.bs[t] + 2 * MM);
     const size_t tile = cells * 2 * sizeof(T);
     int method = g.spread_method;
-    if (method == kSpreadAuto)
+    if (method == kSpreadAuto) {
         method = tile * kSpreadWarps <= 64 * 1024 ? kSpreadWarpPrivate : kSpreadWarpAtomic;
+        if (D == 2 && sizeof(T) == 8) method = kSpreadOctet;  // measured fastest for 2-D FP64
+    }
     // a form whose shared memory does not fit falls back to the one-tile form
     constexpr size_t limit = spread_dyn_limit<T, MM>();
     const size_t octet_tiles =

@@ -1,14 +1,15 @@
-// Kaiser-Bessel window in grid units, normalised to psibar(0) = 1 (Section 2, eq. window and
-// eq. window_cutoff; the pair itself is the one of Plonka-Potts-Steidl-Tasche Ch. 7.2):
+// Window evaluation in grid units, normalised to psibar(0) = 1 (Section 2, eq. window and
+// eq. window_cutoff). The default window is Kaiser-Bessel,
 //
-//   psi(t)    = sinh(b u) / (pi u),  u = sqrt(m^2 - t^2),  |t| <= m;  psi(t) = 0 for |t| > m,
-//   psibar(t) = psi(t) / psi(0) = kscale * sinh(b u) / u,  kscale = m / sinh(b m).
+//   psi(t) = sinh(b u) / (pi u),  u = sqrt(m^2 - t^2),  |t| <= m;  psi(t) = 0 for |t| > m,
 //
-// The factor psi(0) moves into the deconvolution table, so sums of products of d weights stay
-// in range in FP32 for every m. A node with offset frac has taps t = frac + m - i, i = 0..2m;
-// i = 0 lies inside the closed support only when frac == 0 (value psibar(m) = kscale b). For
-// i = 1..2m the kernels evaluate psibar(frac + m - i) from a per-tap polynomial in frac (the
-// window is an entire function of m^2 - t^2 inside the support, so low degrees suffice); the
+// (the pair of Plonka-Potts-Steidl-Tasche Ch. 7.2); Gaussian, B-spline and sinc windows
+// (Section 4.1) go through the same code. The factor psi(0) moves into the deconvolution
+// table, so sums of products of d weights stay in range in FP32 for every m. A node with
+// offset frac has taps t = frac + m - i, i = 0..2m; i = 0 lies inside the closed support only
+// when frac == 0 (value psibar(m), a per-axis constant). For i = 1..2m the kernels evaluate
+// psibar(frac + m - i) from a per-tap polynomial in frac: each window is smooth on every tap
+// interval (the B-spline is a polynomial of degree 2m - 1 there), so low degrees suffice; the
 // polynomials are fitted on the host at plan creation (see gbnfft_internal.cuh).
 #pragma once
 

@@ -38,9 +38,13 @@ class Plan:
     m : window cutoff (default 8, the paper's standard choice)
     dtype : torch.float32 or torch.float64 (precision of x, fhat, f and the grid)
     device : CUDA device (default: the current one)
+    window : "kaiser_bessel" (default), "gaussian", "bspline" or "sinc" (Section 4.1)
     """
 
-    def __init__(self, N, M: int, n=None, m: int = 8, dtype=torch.float32, device=None):
+    def __init__(self, N, M: int, n=None, m: int = 8, dtype=torch.float32, device=None,
+                 window: str = "kaiser_bessel"):
+        if window not in _lib.WINDOWS:
+            raise ValueError(f"window must be one of {sorted(_lib.WINDOWS)}")
         if dtype not in _REAL:
             raise TypeError("dtype must be torch.float32 or torch.float64")
         if not torch.cuda.is_available():
@@ -75,6 +79,9 @@ class Plan:
                                device=self.device)
         check(L.nfft_set_workspace(h, _ptr(self._ws), self._ws.numel()), "nfft_set_workspace")
         self._nodes_key = None
+        self.window = "kaiser_bessel"
+        if window != self.window:
+            self.set_option("window", window)
 
     # ------------------------------------------------------------------ plumbing
     def _bind(self):
@@ -107,11 +114,19 @@ class Plan:
 
     # ------------------------------------------------------------------ API
     def set_option(self, key: str, value) -> None:
-        """Tuning: ``spread_method`` in {auto, thread, warp_atomic, warp_private},
-        ``interp_method`` in {auto, thread, warp}, or
+        """``window`` in {kaiser_bessel, gaussian, bspline, sinc} (changes the approximation;
+        waits for the device to go idle), or tuning: ``spread_method`` in {auto, thread,
+        warp_atomic, warp_private, octet}, ``interp_method`` in {auto, thread, warp, tile}, or
         ``bin0`` / ``bin1`` / ``bin2`` (power-of-two bin sizes). Changing a bin size discards the
         node precomputation; set the nodes again afterwards."""
         L = _lib.lib()
+        if key == "window":
+            if value not in _lib.WINDOWS:
+                raise ValueError(f"window must be one of {sorted(_lib.WINDOWS)}")
+            check(L.nfft_set_option(self._h, _lib.OPT_WINDOW, _lib.WINDOWS[value]),
+                  "nfft_set_option")
+            self.window = value
+            return
         if key == "spread_method":
             check(L.nfft_set_option(self._h, _lib.OPT_SPREAD_METHOD,
                                     _lib.SPREAD_METHODS[value]), "nfft_set_option")
@@ -178,6 +193,17 @@ class Plan:
         self._bind()
         check(_lib.lib().nfft_grad_x(self._h, _ptr(coef), _ptr(w), _ptr(gx)), "nfft_grad_x")
         return gx
+
+    def info(self) -> dict:
+        """Plan parameters after defaults (nfft_get_info)."""
+        i = _lib.NfftInfo()
+        check(_lib.lib().nfft_get_info(self._h, ctypes.byref(i)), "nfft_get_info")
+        inv = {v: k for k, v in _lib.WINDOWS.items()}
+        return dict(d=i.d, m=i.m, dtype=i.dtype, M=int(i.M),
+                    N=tuple(int(i.N[t]) for t in range(i.d)),
+                    n=tuple(int(i.n[t]) for t in range(i.d)),
+                    bin=tuple(int(i.bin[t]) for t in range(i.d)),
+                    workspace_bytes=int(i.workspace_bytes), window=inv[int(i.window)])
 
     def status(self) -> int:
         """Wait for the stream; return (and clear) the device-side error code."""
