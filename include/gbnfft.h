@@ -178,7 +178,8 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *   NFFT_OPT_SPREAD_METHOD  0 automatic, 1 one thread per node with shared-memory atomics,
  *                           2 one warp per node with shared-memory atomics,
  *                           3 one warp per node with a private tile per warp (no atomics),
- *                           4 (d = 2) eight lanes per node, a private tile per eight lanes.
+ *                           4 (d = 2) eight lanes per node, a private tile per eight lanes,
+ *                           5 (d = 2) sixteen lanes per node, a private tile per half-warp.
  *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node (gathers from the grid),
  *                           2 one warp per node, 3 one thread per node gathering from a
  *                           shared-memory tile of the node's bin.
@@ -186,14 +187,20 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           Changing a bin size discards the node precomputation (call
  *                           nfft_set_nodes again) and may change nfft_workspace_size: a
  *                           caller-owned workspace that became too small makes nfft_set_nodes
- *                           return NFFT_ENOMEM. */
+ *                           return NFFT_ENOMEM.
+ *   NFFT_OPT_SUBPROBLEM     nodes per spreading work item (a power of two in 32..1024, 0 = the
+ *                           default: 128 for 2-D FP32, else 1024): the sorted nodes of a bin are
+ *                           cut into items of at
+ *                           most this many nodes. Like a bin size, it discards the node
+ *                           precomputation and may change nfft_workspace_size. */
 enum nfft_option {
     NFFT_OPT_SPREAD_METHOD = 1,
     NFFT_OPT_BIN_0 = 2,
     NFFT_OPT_BIN_1 = 3,
     NFFT_OPT_BIN_2 = 4,
     NFFT_OPT_INTERP_METHOD = 5,
-    NFFT_OPT_WINDOW = 6
+    NFFT_OPT_WINDOW = 6,
+    NFFT_OPT_SUBPROBLEM = 7
 };
 int nfft_set_option(nfft_plan plan, int key, int64_t value);
 

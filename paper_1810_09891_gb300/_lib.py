@@ -77,9 +77,11 @@ OPT_SPREAD_METHOD = 1
 OPT_BIN = (2, 3, 4)
 OPT_INTERP_METHOD = 5
 OPT_WINDOW = 6
+OPT_SUBPROBLEM = 7
 WINDOWS = {"kaiser_bessel": 0, "gaussian": 1, "bspline": 2, "sinc": 3}
 INTERP_METHODS = {"auto": 0, "thread": 1, "warp": 2, "tile": 3}
-SPREAD_METHODS = {"auto": 0, "thread": 1, "warp_atomic": 2, "warp_private": 3, "octet": 4}
+SPREAD_METHODS = {"auto": 0, "thread": 1, "warp_atomic": 2, "warp_private": 3, "octet": 4,
+                  "half": 5}
 
 STAGES = ["set_nodes", "fft_forward", "interp", "zero_grid", "spread", "fft_adjoint", "grad"]
 

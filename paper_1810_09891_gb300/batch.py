@@ -20,20 +20,24 @@ import torch
 
 from .nfft import Plan
 
-# Candidate options per dimension: (spread_method, bins)
+# Candidate options per dimension: (spread_method, bins, nodes per spreading work item)
 CANDIDATES = {
-    1: [(s, (b,)) for s in ("warp_private", "warp_atomic") for b in (256, 1024, 4096)],
-    2: [(s, b) for s in ("warp_private", "warp_atomic", "octet")
-        for b in ((8, 8), (8, 16), (16, 16), (32, 32))],
-    3: [(s, b) for s in ("warp_atomic", "warp_private", "thread")
-        for b in ((8, 8, 8), (4, 8, 8), (8, 8, 16))],
+    1: [(s, (b,), w) for s in ("warp_private", "warp_atomic") for b in (256, 1024, 4096)
+        for w in (256, 1024)],
+    2: [("half", (8, 16), 128), ("half", (8, 16), 256), ("half", (16, 16), 128),
+        ("half", (16, 16), 256), ("octet", (8, 16), 1024), ("octet", (8, 16), 256),
+        ("warp_private", (16, 16), 256), ("warp_private", (8, 16), 256),
+        ("warp_private", (16, 16), 1024), ("warp_atomic", (16, 16), 256)],
+    3: [(s, b, w) for s in ("warp_atomic", "thread") for b in ((8, 8, 8), (4, 8, 8), (8, 8, 16))
+        for w in (256, 1024)] + [("warp_private", (8, 8, 8), w) for w in (256, 1024)],
 }
 
 
-def _apply(plan: Plan, spread: str, bins) -> None:
+def _apply(plan: Plan, spread: str, bins, sub: int = 0) -> None:
     plan.set_option("spread_method", spread)
     for t, b in enumerate(bins):
         plan.set_option(f"bin{t}", int(b))
+    plan.set_option("subproblem", int(sub))
 
 
 def time_step(plan: Plan, x: torch.Tensor, fhat: torch.Tensor, f: torch.Tensor,
@@ -56,25 +60,27 @@ def time_step(plan: Plan, x: torch.Tensor, fhat: torch.Tensor, f: torch.Tensor,
 
 def autotune(plan: Plan, x: torch.Tensor, fhat: torch.Tensor, f: torch.Tensor,
              candidates=None, steps: int = 5) -> dict:
-    """Try every candidate (spread_method, bins) on this plan and these inputs; keep the fastest
-    (the plan ends configured with it, nodes set). Returns {"spread_method", "bins", "ms",
-    "tried": [(spread, bins, ms), ...]}. Candidates that do not fit the hardware are skipped."""
+    """Try every candidate (spread_method, bins, subproblem) on this plan and these inputs; keep
+    the fastest (the plan ends configured with it, nodes set). Returns {"spread_method", "bins",
+    "subproblem", "ms", "tried": [(spread, bins, subproblem, ms), ...]}. Candidates that do not
+    fit the hardware are skipped."""
     cands = candidates if candidates is not None else CANDIDATES[plan.d]
     tried = []
-    for spread, bins in cands:
+    for spread, bins, sub in cands:
         bins = tuple(min(int(b), nn) for b, nn in zip(bins, plan.n))
         try:
-            _apply(plan, spread, bins)
+            _apply(plan, spread, bins, sub)
             ms = time_step(plan, x, fhat, f, steps)
         except RuntimeError:
             continue
-        tried.append((spread, bins, ms))
+        tried.append((spread, bins, sub, ms))
     if not tried:
         raise RuntimeError("autotune: no candidate ran")
-    spread, bins, ms = min(tried, key=lambda t: t[2])
-    _apply(plan, spread, bins)
+    spread, bins, sub, ms = min(tried, key=lambda t: t[3])
+    _apply(plan, spread, bins, sub)
     plan.set_nodes(x)
-    return {"spread_method": spread, "bins": list(bins), "ms": ms, "tried": tried}
+    return {"spread_method": spread, "bins": list(bins), "subproblem": sub, "ms": ms,
+            "tried": tried}
 
 
 class TuningCache:
@@ -96,7 +102,9 @@ class TuningCache:
 
     def put(self, plan: Plan, choice: dict) -> None:
         self.table[self.key(plan)] = {"spread_method": choice["spread_method"],
-                                      "bins": list(choice["bins"]), "ms": choice["ms"]}
+                                      "bins": list(choice["bins"]),
+                                      "subproblem": int(choice.get("subproblem", 0)),
+                                      "ms": choice["ms"]}
         if self.path:
             with open(self.path, "w") as fh:
                 json.dump(self.table, fh, indent=1)
@@ -131,7 +139,7 @@ class PlanBatch:
                 if cache is not None:
                     cache.put(p, choice)
             else:
-                _apply(p, choice["spread_method"], choice["bins"])
+                _apply(p, choice["spread_method"], choice["bins"], choice.get("subproblem", 0))
                 p.set_nodes(x)
             out.append(choice)
         return out

@@ -35,7 +35,7 @@ cudaError_t launch_grad(const Geom &g, const typename Cplx<T>::type *grid,
 template <typename T>
 cudaError_t launch_spread(const Geom &g, const typename Cplx<T>::type *f,
                           const typename RecOf<T>::type *rec, const int *perm,
-                          const SubProb *subs, const int *nsub_total, int max_subs,
+                          const SubProb *subs, int *nsub_total, int max_subs,
                           typename Cplx<T>::type *grid, cudaStream_t stream)
 {
     switch (g.d) {
@@ -57,10 +57,10 @@ template cudaError_t launch_grad<float>(const Geom &, const float2 *, const RecF
 template cudaError_t launch_grad<double>(const Geom &, const double2 *, const RecD *, const int *,
                                          int64_t, const double2 *, double *, cudaStream_t);
 template cudaError_t launch_spread<float>(const Geom &, const float2 *, const RecF *, const int *,
-                                          const SubProb *, const int *, int, float2 *,
+                                          const SubProb *, int *, int, float2 *,
                                           cudaStream_t);
 template cudaError_t launch_spread<double>(const Geom &, const double2 *, const RecD *,
-                                           const int *, const SubProb *, const int *, int,
+                                           const int *, const SubProb *, int *, int,
                                            double2 *, cudaStream_t);
 
 }  // namespace gbnfft

@@ -16,7 +16,7 @@ namespace gbnfft {
 
 constexpr int kMaxDim = 3;
 constexpr int kMaxM = 8;           // window cutoffs 1..8 are instantiated
-constexpr int kMaxSub = 1024;      // nodes per spreading subproblem (one CTA tile)
+constexpr int kMaxSub = 1024;      // largest spreading subproblem (nodes of one bin per work item)
 
 // Per-axis constants of the normalised window psibar(t) = psi(t) / psi(0), in grid units
 // (Kaiser-Bessel, Gaussian, B-spline or sinc; the pairs are written out on the host at plan
@@ -52,6 +52,7 @@ constexpr int kSpreadThread = 1;
 constexpr int kSpreadWarpAtomic = 2;
 constexpr int kSpreadWarpPrivate = 3;
 constexpr int kSpreadOctet = 4;
+constexpr int kSpreadHalf = 5;
 
 // Interpolation methods (see interp_impl.cuh).
 constexpr int kInterpAuto = 0;
@@ -114,13 +115,13 @@ template <typename T>
 cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *bin_count, int2 *bin_rank,
                             int *status, cudaStream_t stream);
 cudaError_t launch_bin_scan(const int *bin_count, int *bin_start, int *sub_start, int *nsub_total,
-                            int nbins, cudaStream_t stream);
+                            int nbins, int sub_max, cudaStream_t stream);
 template <typename T>
 cudaError_t launch_node_scatter(const Geom &g, const T *x, int64_t M, const int2 *bin_rank,
                                 const int *bin_start, typename RecOf<T>::type *rec, int *perm,
                                 cudaStream_t stream);
 cudaError_t launch_fill_subprobs(const int *bin_count, const int *bin_start, const int *sub_start,
-                                 SubProb *subs, int nbins, cudaStream_t stream);
+                                 SubProb *subs, int nbins, int sub_max, cudaStream_t stream);
 
 // One axis pass of the pruned d-variate FFT.
 //   in  : [outer][Lin][inner]   out : [outer][Lout][inner]
@@ -148,7 +149,7 @@ cudaError_t launch_interp(const Geom &g, const typename Cplx<T>::type *grid,
 template <typename T>
 cudaError_t launch_spread(const Geom &g, const typename Cplx<T>::type *f,
                           const typename RecOf<T>::type *rec, const int *perm,
-                          const SubProb *subs, const int *nsub_total, int max_subs,
+                          const SubProb *subs, int *nsub_total, int max_subs,
                           typename Cplx<T>::type *grid, cudaStream_t stream);
 
 // Node gradient: gx[perm[s]*d + t] = Re(conj(w[perm[s]]) * n_t * sum grid * dpsibar_t * ...).
@@ -195,7 +196,7 @@ cudaError_t grad_d(const Geom &g, const typename Cplx<T>::type *grid,
 template <typename T, int D>
 cudaError_t spread_d(const Geom &g, const typename Cplx<T>::type *f,
                      const typename RecOf<T>::type *rec, const int *perm, const SubProb *subs,
-                     const int *nsub_total, int max_subs, typename Cplx<T>::type *grid,
+                     int *nsub_total, int max_subs, typename Cplx<T>::type *grid,
                      cudaStream_t stream);
 }  // namespace detail
 

@@ -3,6 +3,6 @@
 
 namespace gbnfft {
 namespace detail {
-template cudaError_t spread_d<float, 3>(const Geom &, const float2 *, const RecF *, const int *, const SubProb *, const int *, int, float2 *, cudaStream_t);
+template cudaError_t spread_d<float, 3>(const Geom &, const float2 *, const RecF *, const int *, const SubProb *, int *, int, float2 *, cudaStream_t);
 }  // namespace detail
 }  // namespace gbnfft

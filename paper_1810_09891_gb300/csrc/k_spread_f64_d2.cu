@@ -3,6 +3,6 @@
 
 namespace gbnfft {
 namespace detail {
-template cudaError_t spread_d<double, 2>(const Geom &, const double2 *, const RecD *, const int *, const SubProb *, const int *, int, double2 *, cudaStream_t);
+template cudaError_t spread_d<double, 2>(const Geom &, const double2 *, const RecD *, const int *, const SubProb *, int *, int, double2 *, cudaStream_t);
 }  // namespace detail
 }  // namespace gbnfft

@@ -79,11 +79,12 @@ cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *bin_count
     return cudaGetLastError();
 }
 
-// Exclusive scans of the bin counts and of the subproblem counts ceil(count / kMaxSub), in one
+// Exclusive scans of the bin counts and of the subproblem counts ceil(count / sub_max), in one
 // CTA of 1024 threads (each thread owns a contiguous chunk of bins).
 __global__ void __launch_bounds__(1024)
     bin_scan_kernel(const int *__restrict__ count, int *__restrict__ start,
-                    int *__restrict__ sub_start, int *__restrict__ nsub_total, int nbins)
+                    int *__restrict__ sub_start, int *__restrict__ nsub_total, int nbins,
+                    int sub_max)
 {
     __shared__ int s_a[1024];
     __shared__ int s_b[1024];
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(1024)
     for (int i = lo; i < hi; i++) {
         const int c = count[i];
         a += c;
-        b += (c + kMaxSub - 1) / kMaxSub;
+        b += (c + sub_max - 1) / sub_max;
     }
     s_a[tid] = a;
     s_b[tid] = b;
@@ -114,15 +115,20 @@ __global__ void __launch_bounds__(1024)
         start[i] = ra;
         sub_start[i] = rb;
         ra += c;
-        rb += (c + kMaxSub - 1) / kMaxSub;
+        rb += (c + sub_max - 1) / sub_max;
     }
-    if (tid == 1023) nsub_total[0] = s_b[1023];
+    if (tid == 1023) {
+        nsub_total[0] = s_b[1023];
+        nsub_total[1] = 0;  // work counters of the spreading kernels (next entry, CTAs done)
+        nsub_total[2] = 0;
+    }
 }
 
 cudaError_t launch_bin_scan(const int *bin_count, int *bin_start, int *sub_start, int *nsub_total,
-                            int nbins, cudaStream_t stream)
+                            int nbins, int sub_max, cudaStream_t stream)
 {
-    bin_scan_kernel<<<1, 1024, 0, stream>>>(bin_count, bin_start, sub_start, nsub_total, nbins);
+    bin_scan_kernel<<<1, 1024, 0, stream>>>(bin_count, bin_start, sub_start, nsub_total, nbins,
+                                            sub_max);
     return cudaGetLastError();
 }
 
@@ -166,28 +172,28 @@ cudaError_t launch_node_scatter(const Geom &g, const T *x, int64_t M, const int2
 
 __global__ void fill_subprobs_kernel(const int *__restrict__ count, const int *__restrict__ start,
                                      const int *__restrict__ sub_start, SubProb *__restrict__ subs,
-                                     int nbins)
+                                     int nbins, int sub_max)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nbins) return;
     const int c = count[b];
     const int s0 = sub_start[b];
-    for (int k = 0; k * kMaxSub < c; k++) {
+    for (int k = 0; k * sub_max < c; k++) {
         SubProb p;
         p.bin = b;
-        p.start = start[b] + k * kMaxSub;
-        p.count = min(kMaxSub, c - k * kMaxSub);
+        p.start = start[b] + k * sub_max;
+        p.count = min(sub_max, c - k * sub_max);
         p.pad = 0;
         subs[s0 + k] = p;
     }
 }
 
 cudaError_t launch_fill_subprobs(const int *bin_count, const int *bin_start, const int *sub_start,
-                                 SubProb *subs, int nbins, cudaStream_t stream)
+                                 SubProb *subs, int nbins, int sub_max, cudaStream_t stream)
 {
     const int threads = 256;
     fill_subprobs_kernel<<<(nbins + threads - 1) / threads, threads, 0, stream>>>(
-        bin_count, bin_start, sub_start, subs, nbins);
+        bin_count, bin_start, sub_start, subs, nbins, sub_max);
     return cudaGetLastError();
 }
 

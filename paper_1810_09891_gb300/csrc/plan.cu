@@ -207,6 +207,8 @@ struct gbnfft_plan {
     int nbins = 0;
     int max_subs = 0;
     int64_t bin_req[3] = {0, 0, 0};  // requested bin sizes (0 = default)
+    int64_t sub_req = 0;             // requested nodes per spreading subproblem (0 = default)
+    int sub_max = kMaxSub;
     int window = 0;  // WindowKind
     // plan-owned device tables: [deconv_t, twiddles_t]_t, window polynomials, status word
     void *tables = nullptr;
@@ -274,12 +276,15 @@ void layout_workspace(gbnfft_plan *p)
     p->ws_need = align_up(off, 256);
 }
 
-// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 16 x 16
-// (8 x 16 in FP64), 3-D 8 x 8 x 8), clipped to n_t. Recomputes the bin counts and the workspace layout.
+// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 8 x 16,
+// 3-D 8 x 8 x 8), clipped to n_t; nodes per spreading work item: the requested number, else 128
+// for 2-D FP32 and 1024 otherwise (the fastest choices measured with the default spreading forms
+// on a radial trajectory, whose bins hold very different node counts). Recomputes the bin
+// counts and the workspace layout.
 void setup_bins(gbnfft_plan *p)
 {
     Geom &g = p->geom;
-    const int64_t bin_default[3][3] = {{1024, 0, 0}, {16, 16, 0}, {8, 8, 8}};
+    const int64_t bin_default[3][3] = {{1024, 0, 0}, {8, 16, 0}, {8, 8, 8}};
     int64_t nbins = 1;
     for (int t = 0; t < kMaxDim; t++) {
         if (t >= p->d) {
@@ -289,8 +294,6 @@ void setup_bins(gbnfft_plan *p)
             continue;
         }
         int64_t bs = p->bin_req[t] > 0 ? p->bin_req[t] : bin_default[p->d - 1][t];
-        // 2-D FP64 runs fastest with the eight-lane spreading form on 8 x 16 bins (measured)
-        if (p->bin_req[t] <= 0 && p->d == 2 && p->dtype == NFFT_FP64 && t == 0) bs = 8;
         if (bs > p->n[t]) bs = p->n[t];
         g.bs[t] = (int)bs;
         g.bslog[t] = ilog2(bs);
@@ -298,7 +301,9 @@ void setup_bins(gbnfft_plan *p)
         nbins *= g.nb[t];
     }
     p->nbins = (int)nbins;
-    p->max_subs = (int)(nbins + (p->M + kMaxSub - 1) / kMaxSub + 1);
+    p->sub_max = p->sub_req > 0 ? (int)p->sub_req
+                                : (p->d == 2 && p->dtype == NFFT_FP32 ? 128 : kMaxSub);
+    p->max_subs = (int)(nbins + (p->M + p->sub_max - 1) / p->sub_max + 1);
     layout_workspace(p);
 }
 
@@ -419,12 +424,12 @@ template <typename T> int do_set_nodes(gbnfft_plan *p, const void *x)
     GB_CHECK(launch_node_bin<T>(p->geom, static_cast<const T *>(x), p->M, count,
                                 at<int2>(p, p->binrank), p->d_status, s));
     GB_CHECK(launch_bin_scan(count, at<int>(p, p->binstart), at<int>(p, p->substart),
-                             at<int>(p, p->nsub), p->nbins, s));
+                             at<int>(p, p->nsub), p->nbins, p->sub_max, s));
     GB_CHECK(launch_node_scatter<T>(p->geom, static_cast<const T *>(x), p->M,
                                     at<int2>(p, p->binrank), at<int>(p, p->binstart),
                                     at<Rec>(p, p->rec), at<int>(p, p->perm), s));
     GB_CHECK(launch_fill_subprobs(count, at<int>(p, p->binstart), at<int>(p, p->substart),
-                                  at<SubProb>(p, p->subs), p->nbins, s));
+                                  at<SubProb>(p, p->subs), p->nbins, p->sub_max, s));
     return NFFT_OK;
 }
 
@@ -857,7 +862,7 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
     if (!p) return NFFT_EINVAL;
     switch (key) {
     case NFFT_OPT_SPREAD_METHOD:
-        if (value < kSpreadAuto || value > kSpreadOctet) return NFFT_EINVAL;
+        if (value < kSpreadAuto || value > kSpreadHalf) return NFFT_EINVAL;
         p->geom.spread_method = (int)value;
         return NFFT_OK;
     case NFFT_OPT_INTERP_METHOD:
@@ -868,6 +873,23 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
         if (value < kWinKB || value > kWinSinc) return NFFT_EINVAL;
         set_device(p);
         return set_window(p, (int)value);
+    case NFFT_OPT_SUBPROBLEM: {
+        if (value < 0 || value > kMaxSub || (value > 0 && (value < 32 || !is_pow2(value))))
+            return NFFT_EINVAL;
+        p->sub_req = value;
+        const size_t old_need = p->ws_need;
+        setup_bins(p);
+        p->nodes_ready = false;  // the subproblem list is built by set_nodes
+        if (p->ws_owned && p->ws && p->ws_need > old_need) {
+            set_device(p);
+            if (p->stream) cudaStreamSynchronize(p->stream);
+            cudaFree(p->ws);
+            p->ws = nullptr;
+            p->ws_bytes = 0;
+            p->ws_owned = false;
+        }
+        return NFFT_OK;
+    }
     case NFFT_OPT_BIN_0:
     case NFFT_OPT_BIN_1:
     case NFFT_OPT_BIN_2: {

@@ -13,7 +13,9 @@
 //   kSpreadWarpAtomic  one warp per node, the lanes cover the node's taps (so a warp never
 //                  writes one cell twice), shared-memory atomics into one tile (re and im planes);
 //   kSpreadWarpPrivate one warp per node as above, but every warp owns a private tile and adds
-//                  with plain loads and stores (no atomics); the tiles are summed at the flush.
+//                  with plain loads and stores (no atomics); the tiles are summed at the flush;
+//   kSpreadOctet / kSpreadHalf (d = 2) eight or sixteen lanes per node, a private tile per
+//                  group of lanes (see below).
 // Coincident and clustered nodes (a radial trajectory puts every spoke through the origin) make
 // the atomics of the first form collide; the warp forms do not.
 #pragma once
@@ -23,6 +25,30 @@
 
 namespace gbnfft {
 namespace detail {
+
+// Dynamic scheduling of the subproblem list: work[0] holds the list length, work[1] the next
+// unclaimed entry and work[2] the number of CTAs that have finished. A CTA claims one entry at a
+// time with an atomic fetch (heavy and light bins of a nonuniform node set then even out across
+// the SMs); the last CTA to finish puts both counters back to zero for the next launch. Nothing
+// waits on another CTA.
+__device__ __forceinline__ int next_subproblem(int *work, int *s_slot)
+{
+    __syncthreads();  // every thread has read the previous entry
+    if (threadIdx.x == 0) *s_slot = atomicAdd(work + 1, 1);
+    __syncthreads();
+    return *s_slot;
+}
+
+__device__ __forceinline__ void finish_subproblems(int *work)
+{
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(work + 2, 1) == (int)gridDim.x - 1) {
+            work[1] = 0;
+            work[2] = 0;
+        }
+    }
+}
 
 
 
@@ -91,7 +117,7 @@ template <typename T, int D, int MM>
 __global__ void __launch_bounds__(256)
     spread_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
                   const typename RecOf<T>::type *__restrict__ rec, const int *__restrict__ perm,
-                  const SubProb *__restrict__ subs, const int *__restrict__ nsub_total,
+                  const SubProb *__restrict__ subs, int *__restrict__ nsub_total,
                   typename Cplx<T>::type *__restrict__ grid)
 {
     using C = typename Cplx<T>::type;
@@ -106,8 +132,10 @@ __global__ void __launch_bounds__(256)
         tdim[t] = g.bs[t] + 2 * MM;
         cells *= tdim[t];
     }
-    const int nsub = *nsub_total;
-    for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+    const int nsub = nsub_total[0];
+    __shared__ int s_sp;
+    for (int sp = next_subproblem(nsub_total, &s_sp); sp < nsub;
+         sp = next_subproblem(nsub_total, &s_sp)) {
         const SubProb P = subs[sp];
         int origin[D];
         {
@@ -162,6 +190,7 @@ __global__ void __launch_bounds__(256)
         }
         __syncthreads();
     }
+    finish_subproblems(nsub_total);
 }
 
 // ----------------------------------------------------------------------------- warp forms
@@ -276,7 +305,7 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
     spread_warp_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
                        const typename RecOf<T>::type *__restrict__ rec,
                        const int *__restrict__ perm, const SubProb *__restrict__ subs,
-                       const int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
+                       int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
 {
     using C = typename Cplx<T>::type;
     using Rec = typename RecOf<T>::type;
@@ -327,8 +356,10 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
     st[D - 1] = 1;
 #pragma unroll
     for (int t = D - 2; t >= 0; t--) st[t] = st[t + 1] * tdim[t + 1];
-    const int nsub = *nsub_total;
-    for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+    const int nsub = nsub_total[0];
+    __shared__ int s_sp;
+    for (int sp = next_subproblem(nsub_total, &s_sp); sp < nsub;
+         sp = next_subproblem(nsub_total, &s_sp)) {
         const SubProb P = subs[sp];
         int origin[D];
         {
@@ -464,6 +495,7 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
         }
         __syncthreads();
     }
+    finish_subproblems(nsub_total);
 }
 
 // ----------------------------------------------------------------------------- octet form (d = 2)
@@ -533,7 +565,7 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
     spread_octet_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
                         const typename RecOf<T>::type *__restrict__ rec,
                         const int *__restrict__ perm, const SubProb *__restrict__ subs,
-                        const int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
+                        int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
 {
     using C = typename Cplx<T>::type;
     using Rec = typename RecOf<T>::type;
@@ -553,8 +585,10 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
     C *st_val = reinterpret_cast<C *>(st_rec + kSpreadChunk);
     const T *ca = tab, *cb = tab + AS;
     const T ea = (T)g.win[0].edge_w, eb = (T)g.win[1].edge_w;
-    const int nsub = *nsub_total;
-    for (int sp = blockIdx.x; sp < nsub; sp += gridDim.x) {
+    const int nsub = nsub_total[0];
+    __shared__ int s_sp;
+    for (int sp = next_subproblem(nsub_total, &s_sp); sp < nsub;
+         sp = next_subproblem(nsub_total, &s_sp)) {
         const SubProb P = subs[sp];
         const int org1 = (P.bin % g.nb[1]) * g.bs[1];
         const int org0 = (P.bin / g.nb[1]) * g.bs[0];
@@ -618,6 +652,187 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
         }
         __syncthreads();
     }
+    finish_subproblems(nsub_total);
+}
+
+// ------------------------------------------------------------------------ half-warp form (d = 2)
+// Sixteen lanes per node, two nodes per warp, one private complex tile per half-warp. The lanes
+// of a half form RG row groups x CW columns (CW = the 2m taps per axis rounded up to a power of
+// two); lane (rg, c) owns tap column c and tap rows rg, rg + RG, ... of its node. A lane
+// evaluates the column weight of its column and the row weight of row h (its index in the half)
+// from coefficients held in registers; row weights reach the other lanes by shuffles, and the
+// column weight times the node value is formed once per node. A node on a grid point (2m + 1
+// taps on some axis) takes a plain loop over its taps with weights from the global tables.
+// The tile row pitch is padded so that the row groups of one half fall on distinct banks.
+//
+// The CTAs are small (kHalfWarps warps): the flush reads every private tile of the CTA at every
+// cell, so its shared-memory traffic per subproblem grows with the number of tiles per CTA,
+// while small CTAs keep the same number of warps per SM. The flush zeroes the tiles as it reads
+// them, so a tile is cleared once at kernel start and then stays clean between subproblems.
+#ifndef GBNFFT_HALF_WARPS
+#define GBNFFT_HALF_WARPS 2
+#endif
+constexpr int kHalfWarps = GBNFFT_HALF_WARPS;
+constexpr int kHalfTiles = 2 * kHalfWarps;     // half-warps (and private tiles) per CTA
+constexpr int kHalfChunk = 32 * kHalfWarps;    // nodes staged per round
+
+template <int MM> struct HalfShape {
+    static constexpr int PER = 2 * MM;
+    static constexpr int CW = PER <= 2 ? 2 : PER <= 4 ? 4 : PER <= 8 ? 8 : 16;
+    static constexpr int RG = 16 / CW;
+    static constexpr int ROWS = (PER + RG - 1) / RG;
+};
+
+// Row pitch (in cells) of a half-warp tile whose rows hold td1 cells: one half touches RG rows
+// of CW contiguous cells per access; a pitch of CW cells modulo one 128-byte bank cycle puts
+// those RG runs side by side in the banks. Runs that fill a bank cycle need no padding.
+template <typename T, int MM> __host__ __device__ inline int half_pitch(int td1)
+{
+    constexpr int cw = HalfShape<MM>::CW;
+    constexpr int cplx = 2 * (int)sizeof(T);
+    constexpr int mod = 128 / cplx;  // cells per bank cycle
+    if (HalfShape<MM>::RG == 1 || cw * cplx >= 128) return td1;
+    return td1 + ((cw - td1 % mod) + mod) % mod;
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t half_stage_bytes()
+{
+    return kHalfChunk * (sizeof(typename RecOf<T>::type) + sizeof(typename Cplx<T>::type));
+}
+
+template <typename T, int MM>
+__global__ void __launch_bounds__(32 * kHalfWarps)
+    spread_half_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
+                       const typename RecOf<T>::type *__restrict__ rec,
+                       const int *__restrict__ perm, const SubProb *__restrict__ subs,
+                       int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    using Sh = HalfShape<MM>;
+    constexpr int PER = Sh::PER, CW = Sh::CW, RG = Sh::RG, ROWS = Sh::ROWS;
+    constexpr int NT = 2 * MM + 1;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const T *tab = static_cast<const T *>(g.poly);  // read once into registers (and on edges)
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int h = lane & 15, half = tid >> 4;
+    const unsigned mask = 0xffffu << (lane & 16);
+    const int c = h & (CW - 1), rg = h / CW;
+    const int td0 = g.bs[0] + 2 * MM, td1 = g.bs[1] + 2 * MM;
+    const int pitch = half_pitch<T, MM>(td1);
+    const int tcells = td0 * pitch;
+    C *tiles = reinterpret_cast<C *>(smem_raw);
+    C *mine = tiles + (size_t)half * tcells;
+    Rec *st_rec = reinterpret_cast<Rec *>(smem_raw + (size_t)kHalfTiles * tcells * sizeof(C));
+    C *st_val = reinterpret_cast<C *>(st_rec + kHalfChunk);
+    // column tap c + 1 of axis 1 and row tap h + 1 of axis 0 (coefficient k of tap i at
+    // [k * kPolyTaps + i - 1]); lanes past the 2m taps hold zeros
+    T cc[DEG + 1], cr[DEG + 1];
+#pragma unroll
+    for (int k = 0; k <= DEG; k++) {
+        cc[k] = c < PER ? tab[AS + k * kPolyTaps + c] : (T)0;
+        cr[k] = h < PER ? tab[k * kPolyTaps + h] : (T)0;
+    }
+    const T e0 = (T)g.win[0].edge_w, e1 = (T)g.win[1].edge_w;
+    {
+        C z;
+        z.x = (T)0;
+        z.y = (T)0;
+        for (int e = tid; e < kHalfTiles * tcells; e += 32 * kHalfWarps) tiles[e] = z;
+    }
+    const int nsub = nsub_total[0];
+    __shared__ int s_sp;
+    for (int sp = next_subproblem(nsub_total, &s_sp); sp < nsub;
+         sp = next_subproblem(nsub_total, &s_sp)) {
+        const SubProb P = subs[sp];
+        const int org1 = (P.bin % g.nb[1]) * g.bs[1];
+        const int org0 = (P.bin / g.nb[1]) * g.bs[0];
+        Rec r_next;
+        C v_next;
+        if (tid < P.count) {
+            r_next = rec[P.start + tid];
+            v_next = f[perm[P.start + tid]];
+        }
+        for (int c0 = 0; c0 < P.count; c0 += kHalfChunk) {
+            const int cnt = min(kHalfChunk, P.count - c0);
+            if (tid < cnt) {
+                st_rec[tid] = r_next;
+                st_val[tid] = v_next;
+            }
+            __syncthreads();  // (also orders the previous flush's zeroing before these adds)
+            {
+                const int nx = c0 + kHalfChunk + tid;
+                if (nx < P.count) {
+                    r_next = rec[P.start + nx];
+                    v_next = f[perm[P.start + nx]];
+                }
+            }
+            for (int k = half; k < cnt; k += kHalfTiles) {
+                const Rec r = st_rec[k];
+                const C v = st_val[k];
+                const int loc1 = (r.cell & (g.n[1] - 1)) - org1;
+                const int loc0 = ((r.cell >> g.nlog[1]) & (g.n[0] - 1)) - org0;
+                const T fr0 = r.fr[0], fr1 = r.fr[1];
+                if (fr0 != (T)0 && fr1 != (T)0) {  // uniform inside the half (one node)
+                    const T w1 = poly_horner<T, DEG>(cc, (T)2 * fr1 - (T)1);
+                    const T w0h = poly_horner<T, DEG>(cr, (T)2 * fr0 - (T)1);
+                    const T ar = w1 * v.x, ai = w1 * v.y;
+                    C *col = mine + (loc0 + 1) * pitch + loc1 + 1 + c;
+#pragma unroll
+                    for (int j = 0; j < ROWS; j++) {
+                        const int rr = rg + j * RG;
+                        const T w0 = __shfl_sync(mask, w0h, rr, 16);
+                        if (c < PER && rr < PER) {
+                            C a = col[rr * pitch];
+                            a.x += w0 * ar;
+                            a.y += w0 * ai;
+                            col[rr * pitch] = a;
+                        }
+                    }
+                } else {
+                    for (int q = h; q < NT * NT; q += 16) {
+                        const int a0 = q / NT, a1 = q - a0 * NT;
+                        const T w = window_tap<T, MM>(tab, a0, fr0, e0) *
+                                    window_tap<T, MM>(tab + AS, a1, fr1, e1);
+                        C *p = mine + (loc0 + a0) * pitch + loc1 + a1;
+                        C a = *p;
+                        a.x += w * v.x;
+                        a.y += w * v.y;
+                        *p = a;
+                    }
+                }
+                __syncwarp(mask);
+            }
+            __syncthreads();
+        }
+
+        // flush: cell (a0, a1) of the tile is grid point ((org0 - m + a0) mod n0,
+        // (org1 - m + a1) mod n1); consecutive threads take consecutive cells; each cell is read
+        // from every tile and zeroed there
+        C z;
+        z.x = (T)0;
+        z.y = (T)0;
+        for (int idx = tid; idx < td0 * td1; idx += 32 * kHalfWarps) {
+            const int a0 = idx / td1, a1 = idx - a0 * td1;
+            const int e = a0 * pitch + a1;
+            T vr = (T)0, vi = (T)0;
+#pragma unroll
+            for (int o = 0; o < kHalfTiles; o++) {
+                const C cv = tiles[(size_t)o * tcells + e];
+                tiles[(size_t)o * tcells + e] = z;
+                vr += cv.x;
+                vi += cv.y;
+            }
+            if (vr == (T)0 && vi == (T)0) continue;
+            const size_t gi = ((size_t)((org0 - MM + a0) & (g.n[0] - 1)) << g.nlog[1]) |
+                              (size_t)((org1 - MM + a1) & (g.n[1] - 1));
+            global_add(grid + gi, vr, vi);
+        }
+    }
+    finish_subproblems(nsub_total);
 }
 
 // Shared memory left for the dynamic part once the static window tables are placed.
@@ -644,7 +859,7 @@ static cudaError_t launch_persistent(K kernel, size_t smem, int threads, int max
 template <typename T, int D, int MM>
 cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
                             const typename RecOf<T>::type *rec, const int *perm,
-                            const SubProb *subs, const int *nsub_total, int max_subs,
+                            const SubProb *subs, int *nsub_total, int max_subs,
                             typename Cplx<T>::type *grid, cudaStream_t stream)
 {
     size_t cells = 1;
@@ -653,14 +868,20 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
     int method = g.spread_method;
     if (method == kSpreadAuto) {
         method = tile * kSpreadWarps <= 64 * 1024 ? kSpreadWarpPrivate : kSpreadWarpAtomic;
-        if (D == 2 && sizeof(T) == 8) method = kSpreadOctet;  // measured fastest for 2-D FP64
+        // measured fastest for 2-D: sixteen lanes per node in FP32, eight in FP64
+        if (D == 2) method = sizeof(T) == 8 ? kSpreadOctet : kSpreadHalf;
     }
     // a form whose shared memory does not fit falls back to the one-tile form
     constexpr size_t limit = spread_dyn_limit<T, MM>();
     const size_t octet_tiles =
         (size_t)octet_tile_stride<T>((int)cells) * sizeof(typename Cplx<T>::type) * kOctets;
+    const size_t half_tiles = (size_t)(g.bs[0] + 2 * MM) *
+                              (size_t)half_pitch<T, MM>(g.bs[D - 1] + 2 * MM) *
+                              sizeof(typename Cplx<T>::type) * kHalfTiles;
     if (method == kSpreadOctet &&
         (D != 2 || 2 * MM + 1 > 16 || octet_tiles + spread_stage_bytes<T>() > limit))
+        method = kSpreadWarpPrivate;
+    if (method == kSpreadHalf && (D != 2 || half_tiles + half_stage_bytes<T>() > 227 * 1024))
         method = kSpreadWarpPrivate;
     if (method == kSpreadWarpPrivate && tile * kSpreadWarps + 16 + spread_stage_bytes<T>() > limit)
         method = kSpreadWarpAtomic;
@@ -690,6 +911,15 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
             spread_octet_kernel<T, MM><<<blocks, 32 * kSpreadWarps, smem, stream>>>(
                 g, f, rec, perm, subs, nsub_total, grid);
         }
+    } else if (method == kSpreadHalf) {
+        if constexpr (D == 2) {
+            const size_t smem = half_tiles + half_stage_bytes<T>();
+            e = launch_persistent(spread_half_kernel<T, MM>, smem, 32 * kHalfWarps, max_subs,
+                                  blocks);
+            if (e != cudaSuccess) return e;
+            spread_half_kernel<T, MM><<<blocks, 32 * kHalfWarps, smem, stream>>>(
+                g, f, rec, perm, subs, nsub_total, grid);
+        }
     } else if (method == kSpreadWarpPrivate) {
         const size_t smem = (tile * kSpreadWarps + 15) / 16 * 16 + spread_stage_bytes<T>();
         e = launch_persistent(spread_warp_kernel<T, D, MM, true>, smem, 32 * kSpreadWarps,
@@ -708,7 +938,7 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
 template <typename T, int D>
 cudaError_t spread_d(const Geom &g, const typename Cplx<T>::type *f,
                      const typename RecOf<T>::type *rec, const int *perm, const SubProb *subs,
-                     const int *nsub_total, int max_subs, typename Cplx<T>::type *grid,
+                     int *nsub_total, int max_subs, typename Cplx<T>::type *grid,
                      cudaStream_t stream)
 {
     GBNFFT_DISPATCH_M(launch_spread_m, T, D, g, f, rec, perm, subs, nsub_total, max_subs, grid,

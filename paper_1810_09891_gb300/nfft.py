@@ -116,9 +116,10 @@ class Plan:
     def set_option(self, key: str, value) -> None:
         """``window`` in {kaiser_bessel, gaussian, bspline, sinc} (changes the approximation;
         waits for the device to go idle), or tuning: ``spread_method`` in {auto, thread,
-        warp_atomic, warp_private, octet}, ``interp_method`` in {auto, thread, warp, tile}, or
-        ``bin0`` / ``bin1`` / ``bin2`` (power-of-two bin sizes). Changing a bin size discards the
-        node precomputation; set the nodes again afterwards."""
+        warp_atomic, warp_private, octet, half}, ``interp_method`` in {auto, thread, warp, tile}, or
+        ``bin0`` / ``bin1`` / ``bin2`` (power-of-two bin sizes), ``subproblem`` (nodes per
+        spreading work item, a power of two in 32..1024). Changing a bin or subproblem size
+        discards the node precomputation; set the nodes again afterwards."""
         L = _lib.lib()
         if key == "window":
             if value not in _lib.WINDOWS:
@@ -135,9 +136,9 @@ class Plan:
             check(L.nfft_set_option(self._h, _lib.OPT_INTERP_METHOD,
                                     _lib.INTERP_METHODS[value]), "nfft_set_option")
             return
-        if key in ("bin0", "bin1", "bin2"):
-            t = int(key[-1])
-            check(L.nfft_set_option(self._h, _lib.OPT_BIN[t], int(value)), "nfft_set_option")
+        if key in ("bin0", "bin1", "bin2", "subproblem"):
+            opt = _lib.OPT_SUBPROBLEM if key == "subproblem" else _lib.OPT_BIN[int(key[-1])]
+            check(L.nfft_set_option(self._h, opt, int(value)), "nfft_set_option")
             info = _lib.NfftInfo()
             check(L.nfft_get_info(self._h, ctypes.byref(info)), "nfft_get_info")
             self.bin = tuple(int(info.bin[u]) for u in range(self.d))

@@ -14,6 +14,7 @@ from gpu_helpers import DEV, TOL, rel_l2, rounded, to_dev
 pytestmark = pytest.mark.gpu
 
 METHODS = ["thread", "warp_atomic", "warp_private"]
+METHODS_2D = METHODS + ["octet", "half"]  # the group forms exist for d = 2 only
 INTERP = ["thread", "warp", "tile"]
 
 
@@ -29,7 +30,7 @@ def _plan(N, n, m, M, dtype, method=None, bins=None, interp=None):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("method", METHODS_2D)
 @pytest.mark.parametrize("interp", INTERP)
 @pytest.mark.parametrize("m", [4, 6])
 def test_radial_reduced(dtype, method, interp, m):
@@ -89,7 +90,7 @@ def test_bin_sizes(bins):
     M = x.shape[0]
     fh = W.gaussian_fhat(N, 605)
     f = W.gaussian_values(M, 606)
-    for method in METHODS:
+    for method in METHODS_2D:
         plan = _plan(N, n, m, M, torch.float64, method, bins)
         assert plan.bin == tuple(min(b, v) for b, v in zip(bins, n))
         plan.set_nodes(to_dev(x, torch.float64))
@@ -139,3 +140,33 @@ def test_clusters_full_size_fp32():
     assert rel_l2(yf[s], oracle.nfft(xr[s], fhr, n=c["n"], m=4)) <= TOL[torch.float32]
     assert rel_l2(yh, oracle.nfft_adjoint(xr[idx], fr[idx], c["N"], n=c["n"], m=4)) <= \
         TOL[torch.float32]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_subproblem_sizes(dtype):
+    """Cutting the bins' sorted nodes into work items of 32 ... 1024 nodes changes only the work
+    split; sizes that are not powers of two in that range are rejected."""
+    from paper_1810_09891_gb300._lib import NfftError
+    N, n, m = (64, 64), (128, 128), 4
+    npdt = np.float32 if dtype == torch.float32 else np.float64
+    x = W.round_nodes(W.radial_nodes(48, 512), npdt)
+    M = x.shape[0]
+    fh = W.gaussian_fhat(N, 607)
+    f = W.gaussian_values(M, 608)
+    xr, fhr, fr = rounded(x, dtype), rounded(fh, dtype), rounded(f, dtype)
+    ref_f = oracle.nfft(xr, fhr, n=n, m=m)
+    ref_h = oracle.nfft_adjoint(xr, fr, N, n=n, m=m)
+    for method in METHODS_2D:
+        for sub in (32, 128, 1024, 0):
+            plan = _plan(N, n, m, M, dtype, method)
+            plan.set_option("subproblem", sub)
+            plan.set_nodes(to_dev(x, dtype))
+            yf = plan.trafo(to_dev(fh, dtype)).cpu().numpy()
+            yh = plan.adjoint(to_dev(f, dtype)).cpu().numpy()
+            assert plan.status() == 0
+            assert rel_l2(yf, ref_f) <= TOL[dtype]
+            assert rel_l2(yh, ref_h) <= TOL[dtype]
+    plan = _plan(N, n, m, M, dtype)
+    for bad in (16, 33, 2048, -1):
+        with pytest.raises(NfftError, match="NFFT_EINVAL"):
+            plan.set_option("subproblem", bad)
