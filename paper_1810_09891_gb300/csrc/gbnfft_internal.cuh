@@ -74,7 +74,25 @@ struct Geom {
     int nb[kMaxDim];       // bins per axis
     AxisWin win[kMaxDim];
     const void *poly;      // device table of window polynomials (plan precision), d axes
+    const void *poly_host; // host copy of the same table (source of WinCoef kernel arguments)
 };
+
+// The window polynomial table as a kernel argument (same layout as the device table). Kernels
+// that evaluate the window for every node take it by value with __grid_constant__: the
+// coefficients are then read through the constant cache (as FMA operands where the tap index is
+// known at compile time) rather than from shared memory, which the grid gathers need.
+template <typename T, int MM> struct WinCoef {
+    T c[kMaxDim * poly_axis_stride(sizeof(T) == 8, MM)];
+};
+
+template <typename T, int MM> inline WinCoef<T, MM> make_wincoef(const Geom &g)
+{
+    WinCoef<T, MM> w;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    const T *h = static_cast<const T *>(g.poly_host);
+    for (int e = 0; e < kMaxDim * AS; e++) w.c[e] = (h && e < g.d * AS) ? h[e] : (T)0;
+    return w;
+}
 
 // A spreading subproblem: up to kMaxSub consecutive sorted nodes of one bin.
 struct SubProb {

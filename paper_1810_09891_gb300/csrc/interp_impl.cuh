@@ -36,6 +36,47 @@ __device__ __forceinline__ void decode_node(const Geom &g, const typename RecOf<
     }
 }
 
+// FP32 rows in pairs of cells: the NC = 2m + 1 - START cells of a node's row segment, first
+// cell s, are read as aligned 16-byte pairs starting at the even cell e0 = s - (s & 1) (the grid
+// rows hold an even number of cells and start 16-byte aligned, and wrapping keeps pairs whole).
+// That takes NC / 2 + 1 loads (the last one only when it holds a cell of the segment) instead of
+// NC. wv[j] is the weight of cell e0 + j: the tap weight w[START + j - (s & 1)] inside the
+// segment, 0 outside.
+template <int MM, int START> struct PairRow {
+    static constexpr int NC = 2 * MM + 1 - START;  // cells of the segment
+    static constexpr int NP = NC / 2 + 1;          // pairs that cover it at either parity
+};
+
+template <int MM, int START>
+__device__ __forceinline__ void pair_weights(const float *w, int odd, float *wv)
+{
+    constexpr int NC = PairRow<MM, START>::NC, NP = PairRow<MM, START>::NP;
+#pragma unroll
+    for (int j = 0; j < 2 * NP; j++) {
+        const float we = j < NC ? w[START + j] : 0.0f;
+        const float wo = (j >= 1 && j - 1 < NC) ? w[START + j - 1] : 0.0f;
+        wv[j] = odd ? wo : we;
+    }
+}
+
+template <int MM, int START>
+__device__ __forceinline__ float2 row_dot_pairs(const float2 *__restrict__ row, int e0, int mask,
+                                                int odd, const float *wv)
+{
+    constexpr int NC = PairRow<MM, START>::NC, NP = PairRow<MM, START>::NP;
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+    float2 in = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+        if (p < NP - 1 || (NC & 1) || odd) {
+            const float4 v = __ldg(r4 + (((e0 + 2 * p) & mask) >> 1));
+            in.x += v.x * wv[2 * p] + v.z * wv[2 * p + 1];
+            in.y += v.y * wv[2 * p] + v.w * wv[2 * p + 1];
+        }
+    }
+    return in;
+}
+
 template <typename T, int D, int MM, int START>
 __device__ __forceinline__ typename Cplx<T>::type
 interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::type *__restrict__ grid,
@@ -44,6 +85,8 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
     using C = typename Cplx<T>::type;
     constexpr int NT = 2 * MM + 1;
     constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    constexpr bool PAIRS = sizeof(T) == 4;
+    constexpr int NW = 2 * PairRow<MM, START>::NP;
     C acc;
     acc.x = (T)0;
     acc.y = (T)0;
@@ -51,27 +94,44 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
         T w0[NT];
         window_taps<T, MM, START>(tab, frac[0], (T)g.win[0].edge_w, w0);
         const int mask0 = g.n[0] - 1;
+        if constexpr (PAIRS) {
+            const int s0 = base[0] - MM + START, odd = s0 & 1;
+            float wv[NW];
+            pair_weights<MM, START>(w0, odd, wv);
+            const float2 in = row_dot_pairs<MM, START>(grid, s0 - odd, mask0, odd, wv);
+            acc.x = in.x;
+            acc.y = in.y;
+        } else {
 #pragma unroll
-        for (int i = START; i < NT; i++) {
-            const C v = grid[(base[0] - MM + i) & mask0];
-            acc.x += v.x * w0[i];
-            acc.y += v.y * w0[i];
+            for (int i = START; i < NT; i++) {
+                const C v = grid[(base[0] - MM + i) & mask0];
+                acc.x += v.x * w0[i];
+                acc.y += v.y * w0[i];
+            }
         }
     } else if (D == 2) {
         T w1[NT];
         window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
         const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, sh0 = g.nlog[1];
+        const int s1 = base[1] - MM + START, odd = s1 & 1;
+        float wv[NW];
+        if constexpr (PAIRS) pair_weights<MM, START>(w1, odd, wv);
+#pragma unroll
         for (int i0 = START; i0 < NT; i0++) {
             const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
             const C *row = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
             C in;
-            in.x = (T)0;
-            in.y = (T)0;
+            if constexpr (PAIRS) {
+                in = row_dot_pairs<MM, START>(row, s1 - odd, mask1, odd, wv);
+            } else {
+                in.x = (T)0;
+                in.y = (T)0;
 #pragma unroll
-            for (int i1 = START; i1 < NT; i1++) {
-                const C v = row[(base[1] - MM + i1) & mask1];
-                in.x += v.x * w1[i1];
-                in.y += v.y * w1[i1];
+                for (int i1 = START; i1 < NT; i1++) {
+                    const C v = row[(base[1] - MM + i1) & mask1];
+                    in.x += v.x * w1[i1];
+                    in.y += v.y * w1[i1];
+                }
             }
             acc.x += in.x * w0;
             acc.y += in.y * w0;
@@ -82,6 +142,9 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
         window_taps<T, MM, START>(tab + 2 * AS, frac[2], (T)g.win[2].edge_w, w2);
         const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, mask2 = g.n[2] - 1;
         const int sh1 = g.nlog[2], sh0 = g.nlog[1] + g.nlog[2];
+        const int s2 = base[2] - MM + START, odd = s2 & 1;
+        float wv[NW];
+        if constexpr (PAIRS) pair_weights<MM, START>(w2, odd, wv);
         for (int i0 = START; i0 < NT; i0++) {
             const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
             const C *plane = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
@@ -92,13 +155,17 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
             for (int i1 = START; i1 < NT; i1++) {
                 const C *row = plane + ((size_t)((base[1] - MM + i1) & mask1) << sh1);
                 C in;
-                in.x = (T)0;
-                in.y = (T)0;
+                if constexpr (PAIRS) {
+                    in = row_dot_pairs<MM, START>(row, s2 - odd, mask2, odd, wv);
+                } else {
+                    in.x = (T)0;
+                    in.y = (T)0;
 #pragma unroll
-                for (int i2 = START; i2 < NT; i2++) {
-                    const C v = row[(base[2] - MM + i2) & mask2];
-                    in.x += v.x * w2[i2];
-                    in.y += v.y * w2[i2];
+                    for (int i2 = START; i2 < NT; i2++) {
+                        const C v = row[(base[2] - MM + i2) & mask2];
+                        in.x += v.x * w2[i2];
+                        in.y += v.y * w2[i2];
+                    }
                 }
                 pl.x += in.x * w1[i1];
                 pl.y += in.y * w1[i1];
@@ -112,12 +179,12 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
 
 template <typename T, int D, int MM>
 __global__ void __launch_bounds__(kInterpThreads)
-    interp_kernel(Geom g, const typename Cplx<T>::type *__restrict__ grid,
+    interp_kernel(Geom g, const __grid_constant__ WinCoef<T, MM> wc,
+                  const typename Cplx<T>::type *__restrict__ grid,
                   const typename RecOf<T>::type *__restrict__ rec, const int *__restrict__ perm,
                   int M, typename Cplx<T>::type *__restrict__ f)
 {
-    __shared__ __align__(16) T tab[kMaxDim * poly_axis_stride(sizeof(T) == 8, MM)];
-    load_window_tables<T, MM>(tab, g.poly, D);
+    const T *tab = wc.c;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= M) return;
     const typename RecOf<T>::type r = rec[s];
@@ -485,12 +552,12 @@ __device__ __forceinline__ void grad_node(const Geom &g, const T *__restrict__ t
 
 template <typename T, int D, int MM>
 __global__ void __launch_bounds__(kInterpThreads)
-    grad_kernel(Geom g, const typename Cplx<T>::type *__restrict__ grid,
+    grad_kernel(Geom g, const __grid_constant__ WinCoef<T, MM> wc,
+                const typename Cplx<T>::type *__restrict__ grid,
                 const typename RecOf<T>::type *__restrict__ rec, const int *__restrict__ perm,
                 int M, const typename Cplx<T>::type *__restrict__ w, T *__restrict__ gx)
 {
-    __shared__ __align__(16) T tab[kMaxDim * poly_axis_stride(sizeof(T) == 8, MM)];
-    load_window_tables<T, MM>(tab, g.poly, D);
+    const T *tab = wc.c;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= M) return;
     const typename RecOf<T>::type r = rec[s];
@@ -544,8 +611,8 @@ cudaError_t launch_interp_m(const Geom &g, const typename Cplx<T>::type *grid,
             g, grid, rec, perm, (int)M, f);
     } else {
         const int64_t blocks = (M + kInterpThreads - 1) / kInterpThreads;
-        interp_kernel<T, D, MM><<<(unsigned)blocks, kInterpThreads, 0, stream>>>(g, grid, rec,
-                                                                                 perm, (int)M, f);
+        interp_kernel<T, D, MM><<<(unsigned)blocks, kInterpThreads, 0, stream>>>(
+            g, make_wincoef<T, MM>(g), grid, rec, perm, (int)M, f);
     }
     return cudaGetLastError();
 }
@@ -556,8 +623,8 @@ cudaError_t launch_grad_m(const Geom &g, const typename Cplx<T>::type *grid,
                           const typename Cplx<T>::type *w, T *gx, cudaStream_t stream)
 {
     const int64_t blocks = (M + kInterpThreads - 1) / kInterpThreads;
-    grad_kernel<T, D, MM><<<(unsigned)blocks, kInterpThreads, 0, stream>>>(g, grid, rec, perm,
-                                                                           (int)M, w, gx);
+    grad_kernel<T, D, MM><<<(unsigned)blocks, kInterpThreads, 0, stream>>>(
+        g, make_wincoef<T, MM>(g), grid, rec, perm, (int)M, w, gx);
     return cudaGetLastError();
 }
 

@@ -214,6 +214,7 @@ struct gbnfft_plan {
     void *tables = nullptr;
     size_t off_dc[3] = {0, 0, 0}, off_tw[3] = {0, 0, 0}, off_poly = 0, off_status = 0;
     size_t tbytes = 0;
+    std::vector<unsigned char> poly_host;  // host copy of the window polynomials
     void *deconv[3] = {nullptr, nullptr, nullptr};  // plan precision
     void *tw[3] = {nullptr, nullptr, nullptr};
     int *d_status = nullptr;
@@ -584,6 +585,15 @@ static void fill_tables(const gbnfft_plan *p, char *host)
     }
 }
 
+// Host copy of the window polynomials (the kernels that take them as an argument copy it at
+// every launch).
+static void keep_poly_host(gbnfft_plan *p, const char *host)
+{
+    const size_t bytes = size_t(p->d) * poly_axis_stride(p->dtype == NFFT_FP64, p->m) * p->rsize;
+    p->poly_host.assign(host + p->off_poly, host + p->off_poly + bytes);
+    p->geom.poly_host = p->poly_host.data();
+}
+
 // Switch the window: new edge constants and tables, written over the old ones in place (the
 // device pointers, the status word and the node preprocessing stay valid).
 static int set_window(gbnfft_plan *p, int kind)
@@ -599,6 +609,7 @@ static int set_window(gbnfft_plan *p, int kind)
         return NFFT_ENOMEM;
     }
     fill_tables(p, host);
+    keep_poly_host(p, host);
     // the old tables may be read by work queued on any stream of the device
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaMemcpy(p->tables, host, p->off_status, cudaMemcpyHostToDevice);
@@ -700,6 +711,7 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
         return NFFT_ENOMEM;
     }
     fill_tables(p, host);
+    keep_poly_host(p, host);
     cudaError_t e = cudaMalloc(&p->tables, tbytes);
     if (e == cudaSuccess) e = cudaMemcpy(p->tables, host, tbytes, cudaMemcpyHostToDevice);
     std::free(host);
