@@ -3,16 +3,19 @@
 // pruned: a forward transform only ever transforms lines that hold nonzero data, and an adjoint
 // transform only writes the |I_N| outputs it needs.
 //
-// A CTA loads P lines of length L = 2^LOGL of one axis into shared memory, runs a Stockham
-// autosort FFT (radix 4, one radix-2 pass when LOGL is odd) entirely in shared memory, and
-// writes the lines back. Lines along the contiguous axis are rows; lines along a strided axis
-// are taken P columns at a time so that global loads and stores are coalesced. The kernel is
-// instantiated per LOGL, so every index of the passes is a compile-time shift or mask; one
-// thread owns one radix-4 butterfly per pass (several only for the longest lines).
+// Two line kernels, both instantiated per LOGL (L = 2^LOGL) so that every index is a
+// compile-time shift or mask:
+//  * fftr_axis_kernel (lines of 16 ... 8192 points in FP32, 16 ... 4096 in FP64): radix-8
+//    Stockham stages with the butterflies in registers; the first stage reads global memory and
+//    the last one writes it, the stages in between exchange through shared memory.
+//  * fft_axis_kernel (all other lengths): a CTA loads P lines into shared memory, runs a
+//    radix-4 Stockham FFT (one radix-2 pass when LOGL is odd) there and writes the lines back.
+// Lines along the contiguous axis are rows; lines along a strided axis are taken P columns at a
+// time so that global loads and stores are coalesced.
 //
-// The deconvolution factor of axis t is applied in the pass of axis t (the factor of
-// Algorithm "NFFT" line 2, 1/(|I_n| c_k), is a product over axes). The factors are computed in
-// FP64 at plan creation and stored in the plan's precision.
+// The deconvolution factor of axis t is applied in the pass of axis t (the factor
+// 1/(|I_n| c_k) of the deconvolution step of Algorithm "NFFT" is a product over axes). The
+// factors are computed in FP64 at plan creation and stored in the plan's precision.
 #pragma once
 
 #include "gbnfft_internal.cuh"
@@ -292,6 +295,270 @@ cudaError_t launch_kb(const typename Cplx<T>::type *in, typename Cplx<T>::type *
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ DFTs in registers
+// cos and sin of 2 pi k / 32 for k = 0..15 (DFTs of length <= 32 need no others)
+__device__ constexpr double kRootCos[16] = {
+    1.0, 0.98078528040323043, 0.92387953251128674, 0.83146961230254524,
+    0.70710678118654757, 0.55557023301960229, 0.38268343236508984, 0.19509032201612833,
+    0.0, -0.19509032201612833, -0.38268343236508984, -0.55557023301960229,
+    -0.70710678118654757, -0.83146961230254524, -0.92387953251128674, -0.98078528040323043};
+__device__ constexpr double kRootSin[16] = {
+    0.0, 0.19509032201612833, 0.38268343236508984, 0.55557023301960229,
+    0.70710678118654757, 0.83146961230254524, 0.92387953251128674, 0.98078528040323043,
+    1.0, 0.98078528040323043, 0.92387953251128674, 0.83146961230254524,
+    0.70710678118654757, 0.55557023301960229, 0.38268343236508984, 0.19509032201612833};
+
+__host__ __device__ constexpr int bit_reverse(int x, int bits)
+{
+    int r = 0;
+    for (int i = 0; i < bits; i++) r = (r << 1) | ((x >> i) & 1);
+    return r;
+}
+
+// In-register DFT of length R = 2^LOGR <= 32 (natural order in and out), radix-2 decimation in
+// time; every index and twiddle is a compile-time constant once unrolled.
+template <typename C, int LOGR, bool INV> __device__ __forceinline__ void dft_reg(C *v)
+{
+    using T = decltype(v[0].x);
+    constexpr int R = 1 << LOGR;
+    C a[R];
+#pragma unroll
+    for (int i = 0; i < R; i++) a[bit_reverse(i, LOGR)] = v[i];
+#pragma unroll
+    for (int s = 1; s <= LOGR; s++) {
+        const int m = 1 << s, h = m >> 1;
+#pragma unroll
+        for (int k = 0; k < R; k += m) {
+#pragma unroll
+            for (int j = 0; j < h; j++) {
+                const int e = j * (32 / m);  // root index: e^(-+2 pi i j / m) = root32^e
+                C b = a[k + j + h];
+                if (e == 8) {
+                    b = cmul_i<INV>(b);
+                } else if (e != 0) {
+                    C w;
+                    w.x = (T)kRootCos[e];
+                    w.y = INV ? (T)kRootSin[e] : -(T)kRootSin[e];
+                    b = cmul(b, w);
+                }
+                const C u = a[k + j];
+                a[k + j] = cadd(u, b);
+                a[k + j + h] = csub(u, b);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < R; i++) v[i] = a[i];
+}
+
+// ---------------------------------------------------------------- radix-8 register Stockham
+// The same line transform as the shared-memory Stockham kernel above, with the butterflies in
+// registers: stages of radix 8 (the last one of radix 4 or 2 when log2 L is not a multiple of
+// 3), L / 8 threads per line, each owning one radix-8 butterfly (or several smaller ones) per
+// stage. The first stage reads the line straight from global memory (zero padding and the
+// deconvolution factor on the way in), the last one writes it straight back (cropping and the
+// factor on the way out); the stages in between exchange through two shared-memory buffers used
+// in turn, so one barrier separates consecutive stages. Shared indices are padded by one cell
+// per 16, which keeps the stride-8 writes of the first stages free of bank conflicts.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
+struct LineIO {
+    int Nt, half, pad_mode;
+    long long es;
+};
+
+template <typename T, int LOGL>
+__device__ __forceinline__ typename Cplx<T>::type line_load(const typename Cplx<T>::type *src,
+                                                            const LineIO &io, const T *deconv,
+                                                            int pos, bool live)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int L = 1 << LOGL;
+    C x;
+    x.x = (T)0;
+    x.y = (T)0;
+    if (!live) return x;
+    if (io.pad_mode) {
+        const int p = (pos + io.half) & (L - 1);
+        if (p < io.Nt) {
+            x = src[(long long)p * io.es];
+            const T w = deconv[p];
+            x.x *= w;
+            x.y *= w;
+        }
+    } else {
+        x = src[(long long)pos * io.es];
+    }
+    return x;
+}
+
+template <typename T, int LOGL>
+__device__ __forceinline__ void line_store(typename Cplx<T>::type *dst, const LineIO &io,
+                                           const T *deconv, int pos,
+                                           typename Cplx<T>::type y, bool live)
+{
+    constexpr int L = 1 << LOGL;
+    if (!live) return;
+    if (io.pad_mode) {
+        dst[(long long)pos * io.es] = y;
+    } else {
+        const int p = (pos + io.half) & (L - 1);
+        if (p < io.Nt) {
+            const T w = deconv[p];
+            y.x *= w;
+            y.y *= w;
+            dst[(long long)p * io.es] = y;
+        }
+    }
+}
+
+template <typename T, int LOGL, int LOGNS, bool INV>
+__device__ __forceinline__ void r8_stage(const typename Cplx<T>::type *src,
+                                         typename Cplx<T>::type *dst, const LineIO &io,
+                                         const T *deconv, bool live, int j,
+                                         typename Cplx<T>::type *bin,
+                                         typename Cplx<T>::type *bout,
+                                         const typename Cplx<T>::type *__restrict__ tw)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int L = 1 << LOGL;
+    constexpr int TL = L / 8;
+    constexpr int LOGRS = (LOGL - LOGNS) >= 3 ? 3 : (LOGL - LOGNS);
+    constexpr int RS = 1 << LOGRS;
+    constexpr int K = 8 / RS;
+    constexpr int NS = 1 << LOGNS;
+    constexpr bool FIRST = LOGNS == 0;
+    constexpr bool LAST = LOGNS + LOGRS == LOGL;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int b = j + k * TL;
+        C a[RS];
+#pragma unroll
+        for (int r = 0; r < RS; r++) {
+            const int i = b + r * (L / RS);
+            a[r] = FIRST ? line_load<T, LOGL>(src, io, deconv, i, live) : bin[pad16(i)];
+        }
+        const int kk = b & (NS - 1);
+        if (LOGNS > 0) {
+#pragma unroll
+            for (int r = 1; r < RS; r++) {
+                C w = tw[(r * kk) << (LOGL - LOGNS - LOGRS)];
+                if (INV) w.y = -w.y;
+                a[r] = cmul(a[r], w);
+            }
+        }
+        dft_reg<C, LOGRS, INV>(a);
+        const int idx = ((b >> LOGNS) << (LOGNS + LOGRS)) + kk;
+#pragma unroll
+        for (int r = 0; r < RS; r++) {
+            if (LAST)
+                line_store<T, LOGL>(dst, io, deconv, idx + r * NS, a[r], live);
+            else
+                bout[pad16(idx + r * NS)] = a[r];
+        }
+    }
+    if constexpr (!LAST) {
+        __syncthreads();
+        r8_stage<T, LOGL, LOGNS + LOGRS, INV>(src, dst, io, deconv, live, j, bout, bin, tw);
+    }
+}
+
+template <typename T, int LOGL, bool INV>
+__global__ void __launch_bounds__(FftMaxThreads<T>::value)
+    fftr_axis_kernel(const typename Cplx<T>::type *__restrict__ in,
+                     typename Cplx<T>::type *__restrict__ out, long long outer, long long inner,
+                     int Nt, int P, int LS, int pad_mode,
+                     const typename Cplx<T>::type *__restrict__ tw, const T *__restrict__ deconv)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int L = 1 << LOGL;
+    constexpr int TL = L / 8;
+    constexpr int BUF = L + L / 16;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *S = reinterpret_cast<C *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int Lin = pad_mode ? Nt : L;
+    const int Lout = pad_mode ? L : Nt;
+    int c, j;
+    long long o0, i0;
+    int lines;
+    if (inner == 1) {
+        c = tid / TL;
+        j = tid - c * TL;
+        o0 = (long long)blockIdx.x * P;
+        i0 = 0;
+        lines = (int)min((long long)P, outer - o0);
+    } else {
+        c = tid % P;
+        j = tid / P;
+        const long long tiles = (inner + P - 1) / P;
+        o0 = blockIdx.x / tiles;
+        i0 = (blockIdx.x - o0 * tiles) * P;
+        lines = (int)min((long long)P, inner - i0);
+    }
+    const bool live = c < lines;
+    LineIO io;
+    io.Nt = Nt;
+    io.half = Nt / 2;
+    io.pad_mode = pad_mode;
+    const C *src;
+    C *dst;
+    if (inner == 1) {
+        src = in + (o0 + c) * Lin;
+        dst = out + (o0 + c) * Lout;
+        io.es = 1;
+    } else {
+        src = in + o0 * Lin * inner + i0 + c;
+        dst = out + o0 * Lout * inner + i0 + c;
+        io.es = inner;
+    }
+    C *b0 = S + (size_t)c * LS;
+    C *b1 = b0 + BUF;
+    r8_stage<T, LOGL, 0, INV>(src, dst, io, deconv, live, j, b1, b0, tw);
+}
+
+template <typename T, int LOGL>
+cudaError_t launch_fftr(const typename Cplx<T>::type *in, typename Cplx<T>::type *out,
+                        int64_t outer, int64_t inner, int Nt, bool pad_mode, int sign,
+                        const typename Cplx<T>::type *twiddle, const T *deconv,
+                        cudaStream_t stream)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int L = 1 << LOGL;
+    constexpr int TL = L / 8;
+    const int64_t lines = outer * inner;
+    const int64_t min_ctas = 2 * (int64_t)num_sms();
+    int P = inner > 1 ? (int)(32 / sizeof(C)) : 1;
+    while (P * TL < 256 && lines / (2 * P) >= min_ctas) P *= 2;
+    while (P > 1 && P * TL > FftMaxThreads<T>::value) P /= 2;
+    const int64_t cap = inner > 1 ? inner : outer;
+    while (P > 1 && P > cap) P /= 2;
+    if (TL > FftMaxThreads<T>::value) return cudaErrorInvalidValue;
+    int LS = 2 * (L + L / 16);
+    if (inner > 1 && P > 1) {
+        const int cells = 128 / (int)sizeof(C);
+        const int want = (cells / P) % cells;
+        LS += ((want - LS % cells) + cells) % cells;
+    }
+    const size_t smem = (size_t)P * LS * sizeof(C);
+    long long blocks = inner == 1 ? (outer + P - 1) / P : outer * ((inner + P - 1) / P);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const int threads = P * TL;
+    cudaError_t e;
+    if (sign > 0) {
+        e = ensure_dynamic_smem(fftr_axis_kernel<T, LOGL, true>, smem);
+        if (e != cudaSuccess) return e;
+        fftr_axis_kernel<T, LOGL, true><<<(unsigned)blocks, threads, smem, stream>>>(
+            in, out, outer, inner, Nt, P, LS, pad_mode ? 1 : 0, twiddle, deconv);
+    } else {
+        e = ensure_dynamic_smem(fftr_axis_kernel<T, LOGL, false>, smem);
+        if (e != cudaSuccess) return e;
+        fftr_axis_kernel<T, LOGL, false><<<(unsigned)blocks, threads, smem, stream>>>(
+            in, out, outer, inner, Nt, P, LS, pad_mode ? 1 : 0, twiddle, deconv);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T, int LOGL>
 cudaError_t launch_fixed(const typename Cplx<T>::type *in, typename Cplx<T>::type *out,
                          int64_t outer, int64_t inner, int Nt, bool pad_mode, int sign,
@@ -305,6 +572,11 @@ cudaError_t launch_fixed(const typename Cplx<T>::type *in, typename Cplx<T>::typ
     // stores use whole sectors. Short lines widen the tile (up to 1024 points) while the grid
     // keeps at least four CTAs per SM. Threads: one radix-4 butterfly each (KB = 1) for tiles of
     // up to 2048 points, else four (KB = 4), which keeps CTAs small enough for several per SM.
+    // lines of 16 ... 8192 points (FP32) or 16 ... 4096 points (FP64): radix-8 in registers
+    if constexpr (LOGL >= 4 && LOGL <= (sizeof(T) == 4 ? 13 : 12)) {
+        return launch_fftr<T, LOGL>(in, out, outer, inner, Nt, pad_mode, sign, twiddle, deconv,
+                                    stream);
+    }
     const int64_t lines = outer * inner;
     const int64_t min_ctas = 4 * (int64_t)num_sms();
     int P = 1;
