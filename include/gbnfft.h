@@ -70,9 +70,12 @@ enum nfft_status_code {
  *   N      d even bandwidths, N_t >= 2 (Section 2, eq. index_set: N in 2 N^d).
  *   M      number of nodes, M >= 0 and M < 2^31.
  *   n      d FFT lengths, or NULL for the paper's default n_t = 2^(ceil(log2 N_t) + 1)
- *          (Section 2, after eq. gl). Each n_t must be even and > N_t (Section 3.1); this
- *          library builds power-of-two n_t only (NFFT_EUNSUPPORTED otherwise), with
- *          n_t <= 16384 (FP32) / 8192 (FP64) and |I_n| < 2^31.
+ *          (Section 2, after eq. gl). Each n_t must be even and > N_t (Section 3.1). Powers of
+ *          two up to 16384 (FP32) / 8192 (FP64) use the radix-8/4/2 FFT; other even lengths up
+ *          to 4096 (FP32) / 2048 (FP64) use Bluestein's chirp transform (the workspace grows by
+ *          two buffers of |I_n| / n_t x M values, M the power of two >= 2 n_t - 1). Larger
+ *          lengths, |I_n| >= 2^31 or more than 31 bits of packed cell index (sum over the
+ *          axes of ceil(log2 n_t)) give NFFT_EUNSUPPORTED.
  *   m      window cutoff, 1 <= m <= 8, with 2m + 2 <= n_t; m <= 0 selects the paper's default 8
  *          (Section 3.1).
  *   dtype  NFFT_FP32 or NFFT_FP64.
@@ -183,7 +186,9 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node (gathers from the grid),
  *                           2 one warp per node, 3 one thread per node gathering from a
  *                           shared-memory tile of the node's bin.
- *   NFFT_OPT_BIN_0..2       bin (tile) size on axis 0..d-1: a power of two, 0 = default.
+ *   NFFT_OPT_BIN_0..2       bin (tile) size on axis 0..d-1: a power of two, 0 = default;
+ *                           clipped to n_t (power-of-two n_t) or to the largest power of two
+ *                           <= n_t / 2 (other n_t, whose last bin is then partial).
  *                           Changing a bin size discards the node precomputation (call
  *                           nfft_set_nodes again) and may change nfft_workspace_size: a
  *                           caller-owned workspace that became too small makes nfft_set_nodes

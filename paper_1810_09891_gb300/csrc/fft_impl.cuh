@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(FftMaxThreads<T>::value)
 
 template <typename T, int LOGL, int KB>
 cudaError_t launch_kb(const typename Cplx<T>::type *in, typename Cplx<T>::type *out,
-                      int64_t outer, int64_t inner, int Nt, int P, bool pad_mode, int sign,
+                      int64_t outer, int64_t inner, int Nt, int P, int pad_mode, int sign,
                       const typename Cplx<T>::type *twiddle, const T *deconv,
                       cudaStream_t stream)
 {
@@ -291,7 +291,7 @@ cudaError_t launch_kb(const typename Cplx<T>::type *in, typename Cplx<T>::type *
         if (e != cudaSuccess) return e;
     }
     fft_axis_kernel<T, LOGL, KB><<<(unsigned)blocks, threads, smem, stream>>>(
-        in, out, outer, inner, Nt, P, pad_mode ? 1 : 0, sign > 0 ? 1 : 0, twiddle, deconv);
+        in, out, outer, inner, Nt, P, pad_mode, sign > 0 ? 1 : 0, twiddle, deconv);
     return cudaGetLastError();
 }
 
@@ -378,7 +378,7 @@ __device__ __forceinline__ typename Cplx<T>::type line_load(const typename Cplx<
     x.x = (T)0;
     x.y = (T)0;
     if (!live) return x;
-    if (io.pad_mode) {
+    if (io.pad_mode == 1) {
         const int p = (pos + io.half) & (L - 1);
         if (p < io.Nt) {
             x = src[(long long)p * io.es];
@@ -399,7 +399,7 @@ __device__ __forceinline__ void line_store(typename Cplx<T>::type *dst, const Li
 {
     constexpr int L = 1 << LOGL;
     if (!live) return;
-    if (io.pad_mode) {
+    if (io.pad_mode != 0) {  // zero padding or plain: every output
         dst[(long long)pos * io.es] = y;
     } else {
         const int p = (pos + io.half) & (L - 1);
@@ -477,8 +477,8 @@ __global__ void __launch_bounds__(FftMaxThreads<T>::value)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *S = reinterpret_cast<C *>(smem_raw);
     const int tid = threadIdx.x;
-    const int Lin = pad_mode ? Nt : L;
-    const int Lout = pad_mode ? L : Nt;
+    const int Lin = pad_mode == 1 ? Nt : L;
+    const int Lout = pad_mode == 0 ? Nt : L;
     int c, j;
     long long o0, i0;
     int lines;
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(FftMaxThreads<T>::value)
 
 template <typename T, int LOGL>
 cudaError_t launch_fftr(const typename Cplx<T>::type *in, typename Cplx<T>::type *out,
-                        int64_t outer, int64_t inner, int Nt, bool pad_mode, int sign,
+                        int64_t outer, int64_t inner, int Nt, int pad_mode, int sign,
                         const typename Cplx<T>::type *twiddle, const T *deconv,
                         cudaStream_t stream)
 {
@@ -549,19 +549,19 @@ cudaError_t launch_fftr(const typename Cplx<T>::type *in, typename Cplx<T>::type
         e = ensure_dynamic_smem(fftr_axis_kernel<T, LOGL, true>, smem);
         if (e != cudaSuccess) return e;
         fftr_axis_kernel<T, LOGL, true><<<(unsigned)blocks, threads, smem, stream>>>(
-            in, out, outer, inner, Nt, P, LS, pad_mode ? 1 : 0, twiddle, deconv);
+            in, out, outer, inner, Nt, P, LS, pad_mode, twiddle, deconv);
     } else {
         e = ensure_dynamic_smem(fftr_axis_kernel<T, LOGL, false>, smem);
         if (e != cudaSuccess) return e;
         fftr_axis_kernel<T, LOGL, false><<<(unsigned)blocks, threads, smem, stream>>>(
-            in, out, outer, inner, Nt, P, LS, pad_mode ? 1 : 0, twiddle, deconv);
+            in, out, outer, inner, Nt, P, LS, pad_mode, twiddle, deconv);
     }
     return cudaGetLastError();
 }
 
 template <typename T, int LOGL>
 cudaError_t launch_fixed(const typename Cplx<T>::type *in, typename Cplx<T>::type *out,
-                         int64_t outer, int64_t inner, int Nt, bool pad_mode, int sign,
+                         int64_t outer, int64_t inner, int Nt, int pad_mode, int sign,
                          const typename Cplx<T>::type *twiddle, const T *deconv,
                          cudaStream_t stream)
 {
@@ -577,6 +577,7 @@ cudaError_t launch_fixed(const typename Cplx<T>::type *in, typename Cplx<T>::typ
         return launch_fftr<T, LOGL>(in, out, outer, inner, Nt, pad_mode, sign, twiddle, deconv,
                                     stream);
     }
+    if (pad_mode == 2) return cudaErrorInvalidValue;  // plain lines only through the kernel above
     const int64_t lines = outer * inner;
     const int64_t min_ctas = 4 * (int64_t)num_sms();
     int P = 1;
@@ -596,7 +597,7 @@ cudaError_t launch_fixed(const typename Cplx<T>::type *in, typename Cplx<T>::typ
 
 template <typename T>
 cudaError_t launch_fft_axis(const typename Cplx<T>::type *in, typename Cplx<T>::type *out,
-                            int64_t outer, int64_t inner, int L, int Nt, bool pad_mode, int sign,
+                            int64_t outer, int64_t inner, int L, int Nt, int pad_mode, int sign,
                             const typename Cplx<T>::type *twiddle, const T *deconv,
                             cudaStream_t stream)
 {
@@ -624,6 +625,141 @@ cudaError_t launch_fft_axis(const typename Cplx<T>::type *in, typename Cplx<T>::
     default: return cudaErrorInvalidValue;
     }
 #undef GB_FFT_CASE
+}
+
+// ------------------------------------------------------------------ any even length: Bluestein
+// A line of length L that is not a power of two is transformed through the chirp identity
+// jk = (j^2 + k^2 - (k - j)^2) / 2:
+//   X_k = sum_j x_j e^(-+2 pi i jk/L) = w_k sum_j (x_j w_j) v_(k-j),
+// w_j = e^(-+pi i j^2/L), v = conj(w), a linear convolution computed as a circular one of length
+// M >= 2L - 1 (a power of two) with the line FFT above: the chirped line is zero-padded to M,
+// transformed, multiplied by the transform of the wrapped v (divided by M, precomputed per axis
+// and direction), transformed back and chirped again. Zero padding (or cropping) and the
+// deconvolution factor are applied in the first (or last) step as in the power-of-two passes.
+namespace {
+
+template <typename T>
+__global__ void blu_pre_kernel(const typename Cplx<T>::type *__restrict__ in,
+                               typename Cplx<T>::type *__restrict__ buf, long long lines,
+                               long long inner, int L, int Nt, int M, int pad_mode, int sign,
+                               const T *__restrict__ deconv,
+                               const typename Cplx<T>::type *__restrict__ chirp)
+{
+    using C = typename Cplx<T>::type;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= lines * M) return;
+    const long long l = e / M;
+    const int j = (int)(e - l * M);
+    C y;
+    y.x = (T)0;
+    y.y = (T)0;
+    if (j < L) {
+        const long long o = l / inner, i = l - o * inner;
+        const int Lin = pad_mode == 1 ? Nt : L;
+        bool take = true;
+        int q = j;
+        if (pad_mode == 1) {
+            q = j + Nt / 2;
+            if (q >= L) q -= L;
+            take = q < Nt;
+        }
+        if (take) {
+            C x = in[(o * Lin + q) * inner + i];
+            if (pad_mode == 1) {
+                const T d = deconv[q];
+                x.x *= d;
+                x.y *= d;
+            }
+            C w = chirp[j];
+            if (sign > 0) w.y = -w.y;
+            y.x = x.x * w.x - x.y * w.y;
+            y.y = x.x * w.y + x.y * w.x;
+        }
+    }
+    buf[e] = y;
+}
+
+template <typename T>
+__global__ void blu_mul_kernel(typename Cplx<T>::type *__restrict__ buf, long long total, int M,
+                               const typename Cplx<T>::type *__restrict__ filt)
+{
+    using C = typename Cplx<T>::type;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const C a = buf[e], b = filt[e % M];
+    C y;
+    y.x = a.x * b.x - a.y * b.y;
+    y.y = a.x * b.y + a.y * b.x;
+    buf[e] = y;
+}
+
+template <typename T>
+__global__ void blu_post_kernel(const typename Cplx<T>::type *__restrict__ buf,
+                                typename Cplx<T>::type *__restrict__ out, long long lines,
+                                long long inner, int L, int Nt, int M, int pad_mode, int sign,
+                                const T *__restrict__ deconv,
+                                const typename Cplx<T>::type *__restrict__ chirp)
+{
+    using C = typename Cplx<T>::type;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= lines * L) return;
+    const long long l = e / L;
+    const int k = (int)(e - l * L);
+    const long long o = l / inner, i = l - o * inner;
+    const C a = buf[l * M + k];
+    C w = chirp[k];
+    if (sign > 0) w.y = -w.y;
+    C y;
+    y.x = a.x * w.x - a.y * w.y;
+    y.y = a.x * w.y + a.y * w.x;
+    if (pad_mode == 0) {  // crop to the centred I_N and deconvolve
+        int q = k + Nt / 2;
+        if (q >= L) q -= L;
+        if (q >= Nt) return;
+        const T d = deconv[q];
+        y.x *= d;
+        y.y *= d;
+        out[(o * Nt + q) * inner + i] = y;
+    } else {
+        out[(o * L + k) * inner + i] = y;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fft_axis_bluestein(const typename Cplx<T>::type *in,
+                                      typename Cplx<T>::type *out, int64_t outer, int64_t inner,
+                                      int L, int Nt, int pad_mode, int sign, const T *deconv,
+                                      const BluesteinAxis<T> &ax, cudaStream_t stream)
+{
+    using C = typename Cplx<T>::type;
+    if (outer <= 0 || inner <= 0) return cudaSuccess;
+    const int M = ax.M;
+    const long long lines = (long long)outer * inner;
+    C *b0 = static_cast<C *>(ax.buf0);
+    C *b1 = static_cast<C *>(ax.buf1);
+    const C *chirp = static_cast<const C *>(ax.chirp);
+    const C *twM = static_cast<const C *>(ax.twM);
+    const C *filt = static_cast<const C *>(sign < 0 ? ax.filt_fwd : ax.filt_inv);
+    const int threads = 256;
+    long long total = lines * M;
+    blu_pre_kernel<T><<<(unsigned)((total + threads - 1) / threads), threads, 0, stream>>>(
+        in, b0, lines, inner, L, Nt, M, pad_mode, sign, deconv, chirp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_fft_axis<T>(b0, b1, lines, 1, M, M, 2, -1, twM, nullptr, stream);
+    if (e != cudaSuccess) return e;
+    blu_mul_kernel<T><<<(unsigned)((total + threads - 1) / threads), threads, 0, stream>>>(
+        b1, total, M, filt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_fft_axis<T>(b1, b0, lines, 1, M, M, 2, +1, twM, nullptr, stream);
+    if (e != cudaSuccess) return e;
+    total = lines * L;
+    blu_post_kernel<T><<<(unsigned)((total + threads - 1) / threads), threads, 0, stream>>>(
+        b0, out, lines, inner, L, Nt, M, pad_mode, sign, deconv, chirp);
+    return cudaGetLastError();
 }
 
 }  // namespace gbnfft

@@ -66,8 +66,9 @@ struct Geom {
     int m;
     int spread_method;
     int interp_method;
-    int n[kMaxDim];        // grid size per axis (power of two)
-    int nlog[kMaxDim];     // log2 n
+    int n[kMaxDim];        // grid size per axis (even)
+    int cbits[kMaxDim];    // bits of the axis' cell index in a packed cell, ceil(log2 n)
+    int cmask[kMaxDim];    // (1 << cbits) - 1
     int N[kMaxDim];        // bandwidth per axis
     int bs[kMaxDim];       // bin (tile) size per axis, power of two
     int bslog[kMaxDim];
@@ -92,6 +93,22 @@ template <typename T, int MM> inline WinCoef<T, MM> make_wincoef(const Geom &g)
     const T *h = static_cast<const T *>(g.poly_host);
     for (int e = 0; e < kMaxDim * AS; e++) w.c[e] = (h && e < g.d * AS) ? h[e] : (T)0;
     return w;
+}
+
+// x mod n for x in [-n, 2n). Grid indices of taps and of tile cells never leave that range:
+// taps lie within m < n/2 cells of a grid point, and bins are at most n/2 wide unless a single
+// bin covers the axis (see setup_bins), so a tile ends before origin + n/2 + m <= 2n.
+__host__ __device__ __forceinline__ int wrapn(int x, int n)
+{
+    x = x < 0 ? x + n : x;
+    return x >= n ? x - n : x;
+}
+
+// x mod n for any x (tile cells of a partial last bin can lie beyond 2n).
+__host__ __device__ __forceinline__ int modn(int x, int n)
+{
+    x %= n;
+    return x < 0 ? x + n : x;
 }
 
 // A spreading subproblem: up to kMaxSub consecutive sorted nodes of one bin.
@@ -151,9 +168,24 @@ cudaError_t launch_fill_subprobs(const int *bin_count, const int *bin_start, con
 //   sign: -1 forward e^{-2 pi i kl/L}, +1 inverse.
 template <typename T>
 cudaError_t launch_fft_axis(const typename Cplx<T>::type *in, typename Cplx<T>::type *out,
-                            int64_t outer, int64_t inner, int L, int Nt, bool pad_mode, int sign,
+                            int64_t outer, int64_t inner, int L, int Nt, int pad_mode, int sign,
                             const typename Cplx<T>::type *twiddle, const T *deconv,
                             cudaStream_t stream);
+
+// Tables and scratch of one axis whose FFT length is not a power of two (Bluestein, see
+// fft_impl.cuh): M = the power-of-two convolution length (>= 2L - 1), chirp[j] = e^(-pi i j^2/L)
+// (L values), filt_fwd / filt_inv the length-M transforms of the wrapped conj(chirp) / chirp
+// divided by M, twM the length-M twiddles, and two scratch buffers of lines x M values.
+template <typename T> struct BluesteinAxis {
+    int M;
+    const void *chirp, *filt_fwd, *filt_inv, *twM;
+    void *buf0, *buf1;
+};
+template <typename T>
+cudaError_t launch_fft_axis_bluestein(const typename Cplx<T>::type *in,
+                                      typename Cplx<T>::type *out, int64_t outer, int64_t inner,
+                                      int L, int Nt, int pad_mode, int sign, const T *deconv,
+                                      const BluesteinAxis<T> &ax, cudaStream_t stream);
 
 // B: f[perm[s]] = sum over taps of grid * prod psibar. The tiled form walks the subproblem list
 // built by set_nodes (subs, nsub_total, at most max_subs entries).

@@ -29,8 +29,8 @@ __device__ __forceinline__ void decode_node(const Geom &g, const typename RecOf<
     edge = false;
 #pragma unroll
     for (int t = D - 1; t >= 0; t--) {
-        base[t] = cell & (g.n[t] - 1);
-        cell >>= g.nlog[t];
+        base[t] = cell & g.cmask[t];
+        cell >>= g.cbits[t];
         frac[t] = r.fr[t];
         edge |= (frac[t] == (T)0);
     }
@@ -60,7 +60,7 @@ __device__ __forceinline__ void pair_weights(const float *w, int odd, float *wv)
 }
 
 template <int MM, int START>
-__device__ __forceinline__ float2 row_dot_pairs(const float2 *__restrict__ row, int e0, int mask,
+__device__ __forceinline__ float2 row_dot_pairs(const float2 *__restrict__ row, int e0, int n,
                                                 int odd, const float *wv)
 {
     constexpr int NC = PairRow<MM, START>::NC, NP = PairRow<MM, START>::NP;
@@ -69,7 +69,7 @@ __device__ __forceinline__ float2 row_dot_pairs(const float2 *__restrict__ row, 
 #pragma unroll
     for (int p = 0; p < NP; p++) {
         if (p < NP - 1 || (NC & 1) || odd) {
-            const float4 v = __ldg(r4 + (((e0 + 2 * p) & mask) >> 1));
+            const float4 v = __ldg(r4 + (wrapn(e0 + 2 * p, n) >> 1));
             in.x += v.x * wv[2 * p] + v.z * wv[2 * p + 1];
             in.y += v.y * wv[2 * p] + v.w * wv[2 * p + 1];
         }
@@ -93,18 +93,18 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
     if (D == 1) {
         T w0[NT];
         window_taps<T, MM, START>(tab, frac[0], (T)g.win[0].edge_w, w0);
-        const int mask0 = g.n[0] - 1;
+        const int n0 = g.n[0];
         if constexpr (PAIRS) {
             const int s0 = base[0] - MM + START, odd = s0 & 1;
             float wv[NW];
             pair_weights<MM, START>(w0, odd, wv);
-            const float2 in = row_dot_pairs<MM, START>(grid, s0 - odd, mask0, odd, wv);
+            const float2 in = row_dot_pairs<MM, START>(grid, s0 - odd, n0, odd, wv);
             acc.x = in.x;
             acc.y = in.y;
         } else {
 #pragma unroll
             for (int i = START; i < NT; i++) {
-                const C v = grid[(base[0] - MM + i) & mask0];
+                const C v = grid[wrapn(base[0] - MM + i, n0)];
                 acc.x += v.x * w0[i];
                 acc.y += v.y * w0[i];
             }
@@ -112,23 +112,23 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
     } else if (D == 2) {
         T w1[NT];
         window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
-        const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, sh0 = g.nlog[1];
+        const int n0 = g.n[0], n1 = g.n[1];
         const int s1 = base[1] - MM + START, odd = s1 & 1;
         float wv[NW];
         if constexpr (PAIRS) pair_weights<MM, START>(w1, odd, wv);
 #pragma unroll
         for (int i0 = START; i0 < NT; i0++) {
             const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
-            const C *row = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
+            const C *row = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1;
             C in;
             if constexpr (PAIRS) {
-                in = row_dot_pairs<MM, START>(row, s1 - odd, mask1, odd, wv);
+                in = row_dot_pairs<MM, START>(row, s1 - odd, n1, odd, wv);
             } else {
                 in.x = (T)0;
                 in.y = (T)0;
 #pragma unroll
                 for (int i1 = START; i1 < NT; i1++) {
-                    const C v = row[(base[1] - MM + i1) & mask1];
+                    const C v = row[wrapn(base[1] - MM + i1, n1)];
                     in.x += v.x * w1[i1];
                     in.y += v.y * w1[i1];
                 }
@@ -140,29 +140,28 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
         T w1[NT], w2[NT];
         window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
         window_taps<T, MM, START>(tab + 2 * AS, frac[2], (T)g.win[2].edge_w, w2);
-        const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, mask2 = g.n[2] - 1;
-        const int sh1 = g.nlog[2], sh0 = g.nlog[1] + g.nlog[2];
+        const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
         const int s2 = base[2] - MM + START, odd = s2 & 1;
         float wv[NW];
         if constexpr (PAIRS) pair_weights<MM, START>(w2, odd, wv);
         for (int i0 = START; i0 < NT; i0++) {
             const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
-            const C *plane = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
+            const C *plane = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1 * n2;
             C pl;
             pl.x = (T)0;
             pl.y = (T)0;
 #pragma unroll
             for (int i1 = START; i1 < NT; i1++) {
-                const C *row = plane + ((size_t)((base[1] - MM + i1) & mask1) << sh1);
+                const C *row = plane + (size_t)wrapn(base[1] - MM + i1, n1) * n2;
                 C in;
                 if constexpr (PAIRS) {
-                    in = row_dot_pairs<MM, START>(row, s2 - odd, mask2, odd, wv);
+                    in = row_dot_pairs<MM, START>(row, s2 - odd, n2, odd, wv);
                 } else {
                     in.x = (T)0;
                     in.y = (T)0;
 #pragma unroll
                     for (int i2 = START; i2 < NT; i2++) {
-                        const C v = row[(base[2] - MM + i2) & mask2];
+                        const C v = row[wrapn(base[2] - MM + i2, n2)];
                         in.x += v.x * w2[i2];
                         in.y += v.y * w2[i2];
                     }
@@ -330,13 +329,12 @@ __global__ void __launch_bounds__(kInterpTileThreads)
                 }
 #pragma unroll
                 for (int t = 0; t < D - 1; t++)
-                    gbase = (gbase << g.nlog[t]) |
-                            (size_t)((origin[t] - MM + a[t]) & (g.n[t] - 1));
-                gbase <<= g.nlog[D - 1];
+                    gbase = gbase * g.n[t] + (size_t)modn(origin[t] - MM + a[t], g.n[t]);
+                gbase *= g.n[D - 1];
             }
             for (int a = lane; a < tdim[D - 1]; a += 32)
                 tile[row * tdim[D - 1] + a] =
-                    grid[gbase | (size_t)((origin[D - 1] - MM + a) & (g.n[D - 1] - 1))];
+                    grid[gbase + (size_t)modn(origin[D - 1] - MM + a, g.n[D - 1])];
         }
         __syncthreads();
         for (int k = tid; k < P.count; k += kInterpTileThreads) {
@@ -348,8 +346,8 @@ __global__ void __launch_bounds__(kInterpTileThreads)
             bool edge = false;
 #pragma unroll
             for (int t = D - 1; t >= 0; t--) {
-                loc[t] = (cell & (g.n[t] - 1)) - origin[t];  // in [0, bs_t)
-                cell >>= g.nlog[t];
+                loc[t] = (cell & g.cmask[t]) - origin[t];  // in [0, bs_t)
+                cell >>= g.cbits[t];
                 frac[t] = r.fr[t];
                 edge |= (frac[t] == (T)0);
             }
@@ -387,7 +385,7 @@ interp_warp_taps(const Geom &g, const typename Cplx<T>::type *__restrict__ grid,
         int rem = q < TAPS ? q : 0;
         T w = (T)1;
         size_t gi = 0;
-        int shift = 0;
+        size_t stride = 1;
 #pragma unroll
         for (int t = D - 1; t >= 0; t--) {
             const int a = rem % PER;
@@ -400,8 +398,8 @@ interp_warp_taps(const Geom &g, const typename Cplx<T>::type *__restrict__ grid,
                 wt = src < 32 ? wa_s : wb_s;
             }
             w *= wt;
-            gi |= (size_t)((base[t] - MM + a + START) & (g.n[t] - 1)) << shift;
-            shift += g.nlog[t];
+            gi += (size_t)wrapn(base[t] - MM + a + START, g.n[t]) * stride;
+            stride *= (size_t)g.n[t];
         }
         if (q < TAPS) {
             const C v = grid[gi];
@@ -468,12 +466,12 @@ __device__ __forceinline__ void grad_node(const Geom &g, const T *__restrict__ t
         acc[t].y = (T)0;
     }
     if (D == 1) {
-        const int mask0 = g.n[0] - 1;
+        const int n0 = g.n[0];
 #pragma unroll
         for (int i = START; i < NT; i++) {
             T w, dw;
             window_tap_d<T, MM>(tab, i, frac[0], (T)g.win[0].edge_w, (T)g.win[0].edge_dw, w, dw);
-            const C v = grid[(base[0] - MM + i) & mask0];
+            const C v = grid[wrapn(base[0] - MM + i, n0)];
             acc[0].x += v.x * dw;
             acc[0].y += v.y * dw;
         }
@@ -483,16 +481,16 @@ __device__ __forceinline__ void grad_node(const Geom &g, const T *__restrict__ t
         for (int i = START; i < NT; i++)
             window_tap_d<T, MM>(tab + AS, i, frac[1], (T)g.win[1].edge_w, (T)g.win[1].edge_dw,
                                 w1[i], d1[i]);
-        const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, sh0 = g.nlog[1];
+        const int n0 = g.n[0], n1 = g.n[1];
         for (int i0 = START; i0 < NT; i0++) {
             T w0, d0;
             window_tap_d<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w, (T)g.win[0].edge_dw, w0, d0);
-            const C *row = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
+            const C *row = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1;
             C s0, s1;
             s0.x = s0.y = s1.x = s1.y = (T)0;
 #pragma unroll
             for (int i1 = START; i1 < NT; i1++) {
-                const C v = row[(base[1] - MM + i1) & mask1];
+                const C v = row[wrapn(base[1] - MM + i1, n1)];
                 s0.x += v.x * w1[i1];
                 s0.y += v.y * w1[i1];
                 s1.x += v.x * d1[i1];
@@ -512,22 +510,21 @@ __device__ __forceinline__ void grad_node(const Geom &g, const T *__restrict__ t
             window_tap_d<T, MM>(tab + 2 * AS, i, frac[2], (T)g.win[2].edge_w,
                                 (T)g.win[2].edge_dw, w2[i], d2[i]);
         }
-        const int mask0 = g.n[0] - 1, mask1 = g.n[1] - 1, mask2 = g.n[2] - 1;
-        const int sh1 = g.nlog[2], sh0 = g.nlog[1] + g.nlog[2];
+        const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
         for (int i0 = START; i0 < NT; i0++) {
             T w0, d0;
             window_tap_d<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w, (T)g.win[0].edge_dw, w0, d0);
-            const C *plane = grid + ((size_t)((base[0] - MM + i0) & mask0) << sh0);
+            const C *plane = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1 * n2;
             C p0, p1, p2;  // plane sums for the three partial derivatives
             p0.x = p0.y = p1.x = p1.y = p2.x = p2.y = (T)0;
 #pragma unroll
             for (int i1 = START; i1 < NT; i1++) {
-                const C *row = plane + ((size_t)((base[1] - MM + i1) & mask1) << sh1);
+                const C *row = plane + (size_t)wrapn(base[1] - MM + i1, n1) * n2;
                 C sw, sd;
                 sw.x = sw.y = sd.x = sd.y = (T)0;
 #pragma unroll
                 for (int i2 = START; i2 < NT; i2++) {
-                    const C v = row[(base[2] - MM + i2) & mask2];
+                    const C v = row[wrapn(base[2] - MM + i2, n2)];
                     sw.x += v.x * w2[i2];
                     sw.y += v.y * w2[i2];
                     sd.x += v.x * d2[i2];

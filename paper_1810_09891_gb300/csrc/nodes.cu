@@ -60,8 +60,9 @@ __global__ void node_bin_kernel(Geom g, const T *__restrict__ x, int M, int *__r
         long long base;
         double frac;
         ok &= node_pos<T>(x[(long long)j * g.d + t], g.n[t], base, frac);
-        const int b = (int)(base & (long long)(g.n[t] - 1));  // base mod n (two's complement)
-        bin = bin * g.nb[t] + (b >> g.bslog[t]);
+        long long b = base % g.n[t];  // base mod n
+        if (b < 0) b += g.n[t];
+        bin = bin * g.nb[t] + ((int)b >> g.bslog[t]);
     }
     if (!ok) atomicCAS(status, kStatusOk, (int)NFFT_EBADNODE);
     const int rank = atomicAdd(&bin_count[bin], 1);
@@ -147,8 +148,9 @@ __global__ void node_scatter_kernel(Geom g, const T *__restrict__ x, int M,
         long long base;
         double frac;
         node_pos<T>(x[(long long)j * g.d + t], g.n[t], base, frac);
-        const int b = (int)(base & (long long)(g.n[t] - 1));
-        r.cell = (r.cell << g.nlog[t]) | b;
+        long long b = base % g.n[t];
+        if (b < 0) b += g.n[t];
+        r.cell = (r.cell << g.cbits[t]) | (int)b;
         r.fr[t] = (T)frac;
     }
     const int2 br = bin_rank[j];

@@ -2,7 +2,9 @@
 // tables (deconvolution factors and FFT twiddles, both in FP64), workspace layout, and the
 // orchestration of the kernels for set_nodes, the forward NFFT (Algorithm "NFFT": D, F, B),
 // the adjoint NFFT (Algorithm "adjoint NFFT": B^H, F^H, D^H) and the node gradient.
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -215,6 +217,11 @@ struct gbnfft_plan {
     size_t off_dc[3] = {0, 0, 0}, off_tw[3] = {0, 0, 0}, off_poly = 0, off_status = 0;
     size_t tbytes = 0;
     std::vector<unsigned char> poly_host;  // host copy of the window polynomials
+    // axes whose FFT length is not a power of two (Bluestein): convolution length and tables
+    int blu_M[3] = {0, 0, 0};
+    size_t off_chirp[3] = {0, 0, 0}, off_ff[3] = {0, 0, 0}, off_fi[3] = {0, 0, 0};
+    size_t off_twM[3] = {0, 0, 0};
+    size_t blu_elems = 0;  // values per Bluestein scratch buffer (max over axes of lines x M)
     void *deconv[3] = {nullptr, nullptr, nullptr};  // plan precision
     void *tw[3] = {nullptr, nullptr, nullptr};
     int *d_status = nullptr;
@@ -222,7 +229,7 @@ struct gbnfft_plan {
     char *ws = nullptr;
     size_t ws_bytes = 0;
     bool ws_owned = false;
-    Region gA, gB, rec, perm, binrank, bincount, binstart, substart, nsub, subs;
+    Region gA, gB, rec, perm, binrank, bincount, binstart, substart, nsub, subs, blu;
     size_t ws_need = 0;
     bool nodes_ready = false;
     // host-call staging (plan-owned)
@@ -274,6 +281,7 @@ void layout_workspace(gbnfft_plan *p)
     put(p->substart, size_t(p->nbins) * sizeof(int));
     put(p->nsub, 16);
     put(p->subs, size_t(p->max_subs) * sizeof(SubProb));
+    put(p->blu, 2 * p->blu_elems * p->csize);
     p->ws_need = align_up(off, 256);
 }
 
@@ -295,10 +303,16 @@ void setup_bins(gbnfft_plan *p)
             continue;
         }
         int64_t bs = p->bin_req[t] > 0 ? p->bin_req[t] : bin_default[p->d - 1][t];
-        if (bs > p->n[t]) bs = p->n[t];
+        if (is_pow2(p->n[t])) {
+            if (bs > p->n[t]) bs = p->n[t];  // one bin covers the axis
+        } else {
+            int64_t cap = 1;  // the largest power of two <= n/2 (the last bin may be partial)
+            while (cap * 2 <= p->n[t] / 2) cap *= 2;
+            if (bs > cap) bs = cap;
+        }
         g.bs[t] = (int)bs;
         g.bslog[t] = ilog2(bs);
-        g.nb[t] = (int)(p->n[t] / bs);
+        g.nb[t] = (int)((p->n[t] + bs - 1) / bs);
         nbins *= g.nb[t];
     }
     p->nbins = (int)nbins;
@@ -359,6 +373,30 @@ struct ProfScope {
     ~ProfScope() { prof_end(p, idx); }
 };
 
+// One axis pass of the oversampled FFT along axis t: the power-of-two kernels, or Bluestein
+// through the axis' tables and the workspace scratch.
+template <typename T>
+cudaError_t fft_pass(gbnfft_plan *p, int t, const typename Cplx<T>::type *in,
+                     typename Cplx<T>::type *out, int64_t outer, int64_t inner, bool pad, int sign)
+{
+    using C = typename Cplx<T>::type;
+    const T *dc = static_cast<const T *>(p->deconv[t]);
+    if (!p->blu_M[t])
+        return launch_fft_axis<T>(in, out, outer, inner, (int)p->n[t], (int)p->N[t], pad ? 1 : 0,
+                                  sign, static_cast<const C *>(p->tw[t]), dc, p->stream);
+    char *tb = static_cast<char *>(p->tables);
+    BluesteinAxis<T> ax;
+    ax.M = p->blu_M[t];
+    ax.chirp = tb + p->off_chirp[t];
+    ax.filt_fwd = tb + p->off_ff[t];
+    ax.filt_inv = tb + p->off_fi[t];
+    ax.twM = tb + p->off_twM[t];
+    ax.buf0 = p->ws + p->blu.off;
+    ax.buf1 = p->ws + p->blu.off + p->blu_elems * p->csize;
+    return launch_fft_axis_bluestein<T>(in, out, outer, inner, (int)p->n[t], (int)p->N[t],
+                                        pad ? 1 : 0, sign, dc, ax, p->stream);
+}
+
 // Forward FFT passes with D fused: fhat (centred, |I_N|) -> gA (|I_n|, natural order).
 template <typename T> int forward_grid(gbnfft_plan *p, const void *fhat)
 {
@@ -366,23 +404,15 @@ template <typename T> int forward_grid(gbnfft_plan *p, const void *fhat)
     const C *in = static_cast<const C *>(fhat);
     C *A = at<C>(p, p->gA), *B = at<C>(p, p->gB);
     const int64_t *N = p->N, *n = p->n;
-    auto tw = [&](int t) { return static_cast<const C *>(p->tw[t]); };
-    cudaStream_t s = p->stream;
     if (p->d == 1) {
-        GB_CHECK(launch_fft_axis<T>(in, A, 1, 1, (int)n[0], (int)N[0], true, -1, tw(0),
-                                    static_cast<const T *>(p->deconv[0]), s));
+        GB_CHECK(fft_pass<T>(p, 0, in, A, 1, 1, true, -1));
     } else if (p->d == 2) {
-        GB_CHECK(launch_fft_axis<T>(in, B, N[0], 1, (int)n[1], (int)N[1], true, -1, tw(1),
-                                    static_cast<const T *>(p->deconv[1]), s));
-        GB_CHECK(launch_fft_axis<T>(B, A, 1, n[1], (int)n[0], (int)N[0], true, -1, tw(0),
-                                    static_cast<const T *>(p->deconv[0]), s));
+        GB_CHECK(fft_pass<T>(p, 1, in, B, N[0], 1, true, -1));
+        GB_CHECK(fft_pass<T>(p, 0, B, A, 1, n[1], true, -1));
     } else {
-        GB_CHECK(launch_fft_axis<T>(in, A, N[0] * N[1], 1, (int)n[2], (int)N[2], true, -1, tw(2),
-                                    static_cast<const T *>(p->deconv[2]), s));
-        GB_CHECK(launch_fft_axis<T>(A, B, N[0], n[2], (int)n[1], (int)N[1], true, -1, tw(1),
-                                    static_cast<const T *>(p->deconv[1]), s));
-        GB_CHECK(launch_fft_axis<T>(B, A, 1, n[1] * n[2], (int)n[0], (int)N[0], true, -1, tw(0),
-                                    static_cast<const T *>(p->deconv[0]), s));
+        GB_CHECK(fft_pass<T>(p, 2, in, A, N[0] * N[1], 1, true, -1));
+        GB_CHECK(fft_pass<T>(p, 1, A, B, N[0], n[2], true, -1));
+        GB_CHECK(fft_pass<T>(p, 0, B, A, 1, n[1] * n[2], true, -1));
     }
     return NFFT_OK;
 }
@@ -394,23 +424,15 @@ template <typename T> int adjoint_grid(gbnfft_plan *p, void *fhat)
     C *out = static_cast<C *>(fhat);
     C *A = at<C>(p, p->gA), *B = at<C>(p, p->gB);
     const int64_t *N = p->N, *n = p->n;
-    auto tw = [&](int t) { return static_cast<const C *>(p->tw[t]); };
-    cudaStream_t s = p->stream;
     if (p->d == 1) {
-        GB_CHECK(launch_fft_axis<T>(A, out, 1, 1, (int)n[0], (int)N[0], false, +1, tw(0),
-                                    static_cast<const T *>(p->deconv[0]), s));
+        GB_CHECK(fft_pass<T>(p, 0, A, out, 1, 1, false, +1));
     } else if (p->d == 2) {
-        GB_CHECK(launch_fft_axis<T>(A, B, 1, n[1], (int)n[0], (int)N[0], false, +1, tw(0),
-                                    static_cast<const T *>(p->deconv[0]), s));
-        GB_CHECK(launch_fft_axis<T>(B, out, N[0], 1, (int)n[1], (int)N[1], false, +1, tw(1),
-                                    static_cast<const T *>(p->deconv[1]), s));
+        GB_CHECK(fft_pass<T>(p, 0, A, B, 1, n[1], false, +1));
+        GB_CHECK(fft_pass<T>(p, 1, B, out, N[0], 1, false, +1));
     } else {
-        GB_CHECK(launch_fft_axis<T>(A, B, 1, n[1] * n[2], (int)n[0], (int)N[0], false, +1, tw(0),
-                                    static_cast<const T *>(p->deconv[0]), s));
-        GB_CHECK(launch_fft_axis<T>(B, A, N[0], n[2], (int)n[1], (int)N[1], false, +1, tw(1),
-                                    static_cast<const T *>(p->deconv[1]), s));
-        GB_CHECK(launch_fft_axis<T>(A, out, N[0] * N[1], 1, (int)n[2], (int)N[2], false, +1,
-                                    tw(2), static_cast<const T *>(p->deconv[2]), s));
+        GB_CHECK(fft_pass<T>(p, 0, A, B, 1, n[1] * n[2], false, +1));
+        GB_CHECK(fft_pass<T>(p, 1, B, A, N[0], n[2], false, +1));
+        GB_CHECK(fft_pass<T>(p, 2, A, out, N[0] * N[1], 1, false, +1));
     }
     return NFFT_OK;
 }
@@ -503,6 +525,44 @@ int check_dev_ptr(const gbnfft_plan *p, const void *ptr, int64_t count)
 
 }  // namespace
 
+namespace {
+
+// In-place forward DFT X_k = sum_j x_j e^(-2 pi i jk/M) of length M = 2^k in FP64 (iterative
+// radix 2), for the Bluestein filter spectra built at plan creation.
+void host_fft_pow2(std::vector<std::complex<double>> &a)
+{
+    const int64_t M = (int64_t)a.size();
+    for (int64_t i = 1, j = 0; i < M; i++) {
+        int64_t bit = M >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (int64_t len = 2; len <= M; len <<= 1) {
+        for (int64_t i = 0; i < M; i += len) {
+            for (int64_t k = 0; k < len / 2; k++) {
+                double re, im;
+                twiddle(k, len, &re, &im);  // e^(-2 pi i k / len)
+                const std::complex<double> w(re, im);
+                const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+        }
+    }
+}
+
+template <typename CT, typename RT>
+void put_complex(char *dst, int64_t i, double re, double im)
+{
+    CT v;
+    v.x = (RT)re;
+    v.y = (RT)im;
+    reinterpret_cast<CT *>(dst)[i] = v;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *nfft_strerror(int code)
@@ -582,6 +642,49 @@ static void fill_tables(const gbnfft_plan *p, char *host)
                 reinterpret_cast<float2 *>(host + p->off_tw[t])[j] =
                     make_float2((float)re, (float)im);
         }
+        if (p->blu_M[t]) {
+            // chirp w_j = e^(-pi i j^2 / L) = e^(-2 pi i (j^2 mod 2L) / (2L)), exact reduction
+            const int64_t L = p->n[t], Mb = p->blu_M[t];
+            std::vector<std::complex<double>> w(L), vf(Mb, 0.0), vi(Mb, 0.0);
+            for (int64_t j = 0; j < L; j++) {
+                double re, im;
+                twiddle((j * j) % (2 * L), 2 * L, &re, &im);
+                w[j] = std::complex<double>(re, im);
+            }
+            // wrapped filters: v_m for |m| < L at index m mod M; forward uses conj(w)
+            for (int64_t j = 0; j < L; j++) {
+                vf[j] = std::conj(w[j]);
+                vi[j] = w[j];
+                if (j > 0) {
+                    vf[Mb - j] = std::conj(w[j]);
+                    vi[Mb - j] = w[j];
+                }
+            }
+            host_fft_pow2(vf);
+            host_fft_pow2(vi);
+            for (int64_t j = 0; j < Mb; j++) {
+                double re, im;
+                twiddle(j, Mb, &re, &im);
+                const std::complex<double> a = vf[j] / double(Mb), b = vi[j] / double(Mb);
+                if (fp64) {
+                    put_complex<double2, double>(host + p->off_ff[t], j, a.real(), a.imag());
+                    put_complex<double2, double>(host + p->off_fi[t], j, b.real(), b.imag());
+                    put_complex<double2, double>(host + p->off_twM[t], j, re, im);
+                } else {
+                    put_complex<float2, float>(host + p->off_ff[t], j, a.real(), a.imag());
+                    put_complex<float2, float>(host + p->off_fi[t], j, b.real(), b.imag());
+                    put_complex<float2, float>(host + p->off_twM[t], j, re, im);
+                }
+            }
+            for (int64_t j = 0; j < L; j++) {
+                if (fp64)
+                    put_complex<double2, double>(host + p->off_chirp[t], j, w[j].real(),
+                                                 w[j].imag());
+                else
+                    put_complex<float2, float>(host + p->off_chirp[t], j, w[j].real(),
+                                               w[j].imag());
+            }
+        }
     }
 }
 
@@ -641,13 +744,20 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
     }
     if (m > kMaxM) return NFFT_EUNSUPPORTED;
     int64_t G = 1, NN = 1;
+    int cbits = 0;
     for (int t = 0; t < d; t++) {
-        if (!is_pow2(nn[t])) return NFFT_EUNSUPPORTED;
-        if (nn[t] > (dtype == NFFT_FP32 ? 16384 : 8192)) return NFFT_EUNSUPPORTED;
+        // powers of two up to 16384 (FP32) / 8192 (FP64); other even lengths (Bluestein, whose
+        // power-of-two convolution length is at most 8192 / 4096) up to 4096 / 2048
+        if (is_pow2(nn[t])) {
+            if (nn[t] > (dtype == NFFT_FP32 ? 16384 : 8192)) return NFFT_EUNSUPPORTED;
+        } else {
+            if (nn[t] > (dtype == NFFT_FP32 ? 4096 : 2048)) return NFFT_EUNSUPPORTED;
+        }
         G *= nn[t];
         NN *= NNv[t];
+        cbits += ilog2(nn[t]);
     }
-    if (G > 0x7fffffffLL) return NFFT_EUNSUPPORTED;
+    if (G > 0x7fffffffLL || cbits > 31) return NFFT_EUNSUPPORTED;
 
     gbnfft_plan *p = new (std::nothrow) gbnfft_plan();
     if (!p) return NFFT_ENOMEM;
@@ -680,13 +790,19 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
     for (int t = 0; t < kMaxDim; t++) {
         if (t >= d) {
             g.n[t] = 1;
-            g.nlog[t] = 0;
+            g.cbits[t] = 0;
+            g.cmask[t] = 0;
             g.N[t] = 1;
             g.win[t] = AxisWin{0.0, 0.0, 0.0};
             continue;
         }
         g.n[t] = (int)nn[t];
-        g.nlog[t] = ilog2(nn[t]);
+        g.cbits[t] = ilog2(nn[t]);
+        g.cmask[t] = (1 << g.cbits[t]) - 1;
+        if (!is_pow2(nn[t])) {  // Bluestein: convolution length and scratch (lines x M)
+            p->blu_M[t] = 1 << ilog2(2 * nn[t] - 1);
+            p->blu_elems = std::max(p->blu_elems, size_t(G / nn[t]) * size_t(p->blu_M[t]));
+        }
         g.N[t] = (int)NNv[t];
     }
     set_window_constants(p);
@@ -699,6 +815,17 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
         tbytes = align_up(tbytes + size_t(NNv[t]) * p->rsize, 256);
         p->off_tw[t] = tbytes;
         tbytes = align_up(tbytes + size_t(nn[t]) * p->csize, 256);
+        if (p->blu_M[t]) {
+            const int Mb = p->blu_M[t];
+            p->off_chirp[t] = tbytes;
+            tbytes = align_up(tbytes + size_t(nn[t]) * p->csize, 256);
+            p->off_ff[t] = tbytes;
+            tbytes = align_up(tbytes + size_t(Mb) * p->csize, 256);
+            p->off_fi[t] = tbytes;
+            tbytes = align_up(tbytes + size_t(Mb) * p->csize, 256);
+            p->off_twM[t] = tbytes;
+            tbytes = align_up(tbytes + size_t(Mb) * p->csize, 256);
+        }
     }
     p->off_poly = tbytes;
     tbytes = align_up(tbytes + size_t(d) * poly_axis_stride(dtype == NFFT_FP64, m) * p->rsize, 256);

@@ -159,8 +159,8 @@ __global__ void __launch_bounds__(256)
             bool edge = false;
 #pragma unroll
             for (int t = D - 1; t >= 0; t--) {
-                loc[t] = (cell & (g.n[t] - 1)) - origin[t];  // in [0, bs_t)
-                cell >>= g.nlog[t];
+                loc[t] = (cell & g.cmask[t]) - origin[t];  // in [0, bs_t)
+                cell >>= g.cbits[t];
                 frac[t] = r.fr[t];
                 edge |= (frac[t] == (T)0);
             }
@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256)
             }
 #pragma unroll
             for (int t = 0; t < D; t++)
-                gi = (gi << g.nlog[t]) | (size_t)((origin[t] - MM + a[t]) & (g.n[t] - 1));
+                gi = gi * g.n[t] + (size_t)wrapn(origin[t] - MM + a[t], g.n[t]);
             global_add(grid + gi, re, im);
         }
         __syncthreads();
@@ -407,8 +407,8 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
                 bool edge = false;
 #pragma unroll
                 for (int t = D - 1; t >= 0; t--) {
-                    loc[t] = (cell & (g.n[t] - 1)) - origin[t];
-                    cell >>= g.nlog[t];
+                    loc[t] = (cell & g.cmask[t]) - origin[t];
+                    cell >>= g.cbits[t];
                     frac[t] = r.fr[t];
                     edge |= (frac[t] == (T)0);
                 }
@@ -466,9 +466,8 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
                 }
 #pragma unroll
                 for (int t = 0; t < D - 1; t++)
-                    gbase = (gbase << g.nlog[t]) |
-                            (size_t)((origin[t] - MM + a[t]) & (g.n[t] - 1));
-                gbase <<= g.nlog[D - 1];
+                    gbase = gbase * g.n[t] + (size_t)wrapn(origin[t] - MM + a[t], g.n[t]);
+                gbase *= g.n[D - 1];
             }
             for (int a = lane; a < tdim[D - 1]; a += 32) {
                 const int e = row * tdim[D - 1] + a;
@@ -489,7 +488,7 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
                 }
                 if (vr == (T)0 && vi == (T)0) continue;
                 const size_t gi =
-                    gbase | (size_t)((origin[D - 1] - MM + a) & (g.n[D - 1] - 1));
+                    gbase + (size_t)wrapn(origin[D - 1] - MM + a, g.n[D - 1]);
                 global_add(grid + gi, vr, vi);
             }
         }
@@ -619,8 +618,8 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
             for (int k = oct; k < cnt; k += kOctets) {
                 const Rec r = st_rec[k];
                 const C v = st_val[k];
-                const int loc1 = (r.cell & (g.n[1] - 1)) - org1;
-                const int loc0 = ((r.cell >> g.nlog[1]) & (g.n[0] - 1)) - org0;
+                const int loc1 = (r.cell & g.cmask[1]) - org1;
+                const int loc0 = ((r.cell >> g.cbits[1]) & g.cmask[0]) - org0;
                 const T fr0 = r.fr[0], fr1 = r.fr[1];
                 if (fr0 == (T)0 || fr1 == (T)0)  // uniform inside the group (one node)
                     spread_octet_node<T, MM, 0>(mine, td1, loc0 * td1 + loc1, fr0, fr1, ca, ea,
@@ -636,7 +635,7 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
         // flush: cell (a0, a1) of the tile is grid point ((org0 - m + a0) mod n0,
         // (org1 - m + a1) mod n1); one warp per tile row, lanes along the row
         for (int a0 = warp; a0 < td0; a0 += kSpreadWarps) {
-            const size_t gbase = (size_t)((org0 - MM + a0) & (g.n[0] - 1)) << g.nlog[1];
+            const size_t gbase = (size_t)wrapn(org0 - MM + a0, g.n[0]) * g.n[1];
             for (int a1 = lane; a1 < td1; a1 += 32) {
                 const int e = a0 * td1 + a1;
                 T vr = (T)0, vi = (T)0;
@@ -647,7 +646,7 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
                     vi += c.y;
                 }
                 if (vr == (T)0 && vi == (T)0) continue;
-                global_add(grid + (gbase | (size_t)((org1 - MM + a1) & (g.n[1] - 1))), vr, vi);
+                global_add(grid + (gbase + (size_t)wrapn(org1 - MM + a1, g.n[1])), vr, vi);
             }
         }
         __syncthreads();
@@ -773,8 +772,8 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
             for (int k = half; k < cnt; k += kHalfTiles) {
                 const Rec r = st_rec[k];
                 const C v = st_val[k];
-                const int loc1 = (r.cell & (g.n[1] - 1)) - org1;
-                const int loc0 = ((r.cell >> g.nlog[1]) & (g.n[0] - 1)) - org0;
+                const int loc1 = (r.cell & g.cmask[1]) - org1;
+                const int loc0 = ((r.cell >> g.cbits[1]) & g.cmask[0]) - org0;
                 const T fr0 = r.fr[0], fr1 = r.fr[1];
                 if (fr0 != (T)0 && fr1 != (T)0) {  // uniform inside the half (one node)
                     const T w1 = poly_horner<T, DEG>(cc, (T)2 * fr1 - (T)1);
@@ -827,8 +826,8 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
                 vi += cv.y;
             }
             if (vr == (T)0 && vi == (T)0) continue;
-            const size_t gi = ((size_t)((org0 - MM + a0) & (g.n[0] - 1)) << g.nlog[1]) |
-                              (size_t)((org1 - MM + a1) & (g.n[1] - 1));
+            const size_t gi = (size_t)wrapn(org0 - MM + a0, g.n[0]) * g.n[1] +
+                              (size_t)wrapn(org1 - MM + a1, g.n[1]);
             global_add(grid + gi, vr, vi);
         }
     }

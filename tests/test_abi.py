@@ -61,7 +61,8 @@ def _create(lib, d, N, M, n=None, m=4, dtype=0):
     (dict(d=1, N=(8,), M=1, n=(15,)), 1),    # odd n
     (dict(d=1, N=(8,), M=1, n=(16,), m=8), 1),   # 2m + 2 > n
     (dict(d=1, N=(8,), M=1, dtype=2), 1),    # bad dtype
-    (dict(d=1, N=(8,), M=1, n=(24,)), 7),    # even n, not a power of two: unsupported here
+    (dict(d=1, N=(8,), M=1, n=(4098,)), 7),  # even n, not a power of two, beyond 4096 (FP32)
+    (dict(d=1, N=(8,), M=1, n=(2050,), dtype=1), 7),  # ... beyond 2048 (FP64)
     (dict(d=1, N=(8,), M=1, n=(64,), m=9), 7),   # m > 8
     (dict(d=1, N=(8192,), M=1, n=(32768,)), 7),  # n beyond the in-shared-memory FFT
 ])
