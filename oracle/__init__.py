@@ -84,6 +84,8 @@ def _load():
             "ora_window_param": ([Int, I64, I64, Int], D),
             "ora_window_psi": ([Int, D, Int, D], D),
             "ora_window_dpsi": ([Int, D, Int, D], D),
+            "ora_window_psi_eval": ([Int, D, Int, D], D),
+            "ora_window_dpsi_eval": ([Int, D, Int, D], D),
             "ora_window_phihat": ([Int, I64, I64, Int, D], D),
             "ora_nfft_D_w": ([Int, Int, P, P, Int, P, P], None),
             "ora_nfft_DH_w": ([Int, Int, P, P, Int, P, P], None),
@@ -105,10 +107,14 @@ def _load():
 WINDOWS = {"kaiser_bessel": 0, "gaussian": 1, "bspline": 2, "sinc": 3}
 
 
-def _win(window) -> int:
-    if isinstance(window, int):
-        return window
-    return WINDOWS[window]
+def _win(window, lin_psi: int = 0) -> int:
+    """Window spec of the C oracle: the window kind in the low 8 bits, the lookup-table size K
+    (samples per unit of t, 0 = the exact window) above them."""
+    kind = window if isinstance(window, int) else WINDOWS[window]
+    K = int(lin_psi)
+    if K < 0 or K >= (1 << 22):
+        raise ValueError("lin_psi must be in [0, 2^22)")
+    return int(kind) | (K << 8)
 
 
 def _i64(v) -> np.ndarray:
@@ -180,6 +186,15 @@ def window_dpsi(window, t: float, m: int, prm: float) -> float:
     return float(_load().ora_window_dpsi(_win(window), float(t), int(m), float(prm)))
 
 
+def window_psi_eval(window, t: float, m: int, prm: float, lin_psi: int = 0) -> float:
+    """psi(t) as steps B, B^H use it: exact, or from the K-point lookup table (lin_psi = K)."""
+    return float(_load().ora_window_psi_eval(_win(window, lin_psi), float(t), int(m), float(prm)))
+
+
+def window_dpsi_eval(window, t: float, m: int, prm: float, lin_psi: int = 0) -> float:
+    return float(_load().ora_window_dpsi_eval(_win(window, lin_psi), float(t), int(m), float(prm)))
+
+
 def window_phihat(window, k: int, n: int, m: int, prm: float) -> float:
     return float(_load().ora_window_phihat(_win(window), int(k), int(n), int(m), float(prm)))
 
@@ -248,54 +263,54 @@ def nfft_DH(ghat, N, m: int, window="kaiser_bessel") -> np.ndarray:
     return out
 
 
-def nfft_B(x, g, N, m: int, window="kaiser_bessel") -> np.ndarray:
+def nfft_B(x, g, N, m: int, window="kaiser_bessel", lin_psi: int = 0) -> np.ndarray:
     g = _c128(g)
     d = g.ndim
     x = _nodes(x, d)
     f = np.zeros(x.shape[0], dtype=np.complex128)
-    _load().ora_nfft_B_w(_win(window), d, _p(_i64(N)), _p(_i64(g.shape)), int(m), x.shape[0],
+    _load().ora_nfft_B_w(_win(window, lin_psi), d, _p(_i64(N)), _p(_i64(g.shape)), int(m), x.shape[0],
                          _p(x), _p(g), _p(f))
     return f
 
 
-def nfft_BH(x, f, N, n, m: int, window="kaiser_bessel") -> np.ndarray:
+def nfft_BH(x, f, N, n, m: int, window="kaiser_bessel", lin_psi: int = 0) -> np.ndarray:
     n = tuple(int(v) for v in n)
     d = len(n)
     x = _nodes(x, d)
     f = _c128(f).reshape(-1)
     g = np.zeros(n, dtype=np.complex128)
-    _load().ora_nfft_BH_w(_win(window), d, _p(_i64(N)), _p(_i64(n)), int(m), x.shape[0], _p(x),
+    _load().ora_nfft_BH_w(_win(window, lin_psi), d, _p(_i64(N)), _p(_i64(n)), int(m), x.shape[0], _p(x),
                           _p(f), _p(g))
     return g
 
 
-def nfft_dB(x, g, N, m: int, window="kaiser_bessel") -> np.ndarray:
+def nfft_dB(x, g, N, m: int, window="kaiser_bessel", lin_psi: int = 0) -> np.ndarray:
     g = _c128(g)
     d = g.ndim
     x = _nodes(x, d)
     ds = np.zeros((x.shape[0], d), dtype=np.complex128)
-    _load().ora_nfft_dB_w(_win(window), d, _p(_i64(N)), _p(_i64(g.shape)), int(m), x.shape[0],
+    _load().ora_nfft_dB_w(_win(window, lin_psi), d, _p(_i64(N)), _p(_i64(g.shape)), int(m), x.shape[0],
                           _p(x), _p(g), _p(ds))
     return ds
 
 
 # ------------------------------------------------------------------------------------ NFFT
 
-def nfft(x, fhat, n=None, m: int = 8, window="kaiser_bessel") -> np.ndarray:
+def nfft(x, fhat, n=None, m: int = 8, window="kaiser_bessel", lin_psi: int = 0) -> np.ndarray:
     """Algorithm "NFFT" (Section 2): f = B F D fhat."""
     fhat = _c128(fhat)
     d = fhat.ndim
     n = default_n(fhat.shape) if n is None else tuple(int(v) for v in n)
     x = _nodes(x, d)
     f = np.zeros(x.shape[0], dtype=np.complex128)
-    rc = _load().ora_nfft_w(_win(window), d, _p(_i64(fhat.shape)), _p(_i64(n)), int(m),
+    rc = _load().ora_nfft_w(_win(window, lin_psi), d, _p(_i64(fhat.shape)), _p(_i64(n)), int(m),
                             x.shape[0], _p(x), _p(fhat), _p(f))
     if rc:
         raise MemoryError("oracle nfft: allocation failed")
     return f
 
 
-def nfft_adjoint(x, f, N, n=None, m: int = 8, window="kaiser_bessel") -> np.ndarray:
+def nfft_adjoint(x, f, N, n=None, m: int = 8, window="kaiser_bessel", lin_psi: int = 0) -> np.ndarray:
     """Algorithm "adjoint NFFT" (Section 2): hhat = D^H F^H B^H f."""
     N = tuple(int(v) for v in N)
     d = len(N)
@@ -303,14 +318,14 @@ def nfft_adjoint(x, f, N, n=None, m: int = 8, window="kaiser_bessel") -> np.ndar
     x = _nodes(x, d)
     f = _c128(f).reshape(-1)
     out = np.zeros(N, dtype=np.complex128)
-    rc = _load().ora_nfft_adjoint_w(_win(window), d, _p(_i64(N)), _p(_i64(n)), int(m),
+    rc = _load().ora_nfft_adjoint_w(_win(window, lin_psi), d, _p(_i64(N)), _p(_i64(n)), int(m),
                                     x.shape[0], _p(x), _p(f), _p(out))
     if rc:
         raise MemoryError("oracle nfft_adjoint: allocation failed")
     return out
 
 
-def nfft_grad_x(x, c, w, n=None, m: int = 8, window="kaiser_bessel") -> np.ndarray:
+def nfft_grad_x(x, c, w, n=None, m: int = 8, window="kaiser_bessel", lin_psi: int = 0) -> np.ndarray:
     """(M, d) real: Re(conj(w_j) d s_c/d x_t (x_j)), s_c the NFFT approximation built from c."""
     c = _c128(c)
     d = c.ndim
@@ -318,7 +333,7 @@ def nfft_grad_x(x, c, w, n=None, m: int = 8, window="kaiser_bessel") -> np.ndarr
     x = _nodes(x, d)
     w = _c128(w).reshape(-1)
     gx = np.zeros((x.shape[0], d), dtype=np.float64)
-    rc = _load().ora_nfft_grad_x_w(_win(window), d, _p(_i64(c.shape)), _p(_i64(n)), int(m),
+    rc = _load().ora_nfft_grad_x_w(_win(window, lin_psi), d, _p(_i64(c.shape)), _p(_i64(n)), int(m),
                                    x.shape[0], _p(x), _p(c), _p(w), _p(gx))
     if rc:
         raise MemoryError("oracle nfft_grad_x: allocation failed")

@@ -247,6 +247,7 @@ static double ora_sinc(double u) { return u == 0.0 ? 1.0 : sin(u) / u; }
  * sinc: a = (2 sigma - 1) / (2 m sigma); B-spline: unused. */
 double ora_window_param(int w, int64_t n, int64_t N, int m)
 {
+    w &= 0xff; /* window kind (the lookup-table setting does not change the pair) */
     const double sigma = (double)n / (double)N;
     switch (w) {
     case ORA_GAUSS: return 2.0 * sigma * m / ((2.0 * sigma - 1.0) * ORA_PI);
@@ -260,6 +261,7 @@ double ora_window_param(int w, int64_t n, int64_t N, int m)
  * sinc: sinc^{2m}(pi a t); KB: see ora_kb_psi. */
 double ora_window_psi(int w, double t, int m, double prm)
 {
+    w &= 0xff; /* window kind (the lookup-table setting does not change the pair) */
     if (fabs(t) > (double)m) return 0.0;
     switch (w) {
     case ORA_GAUSS: return exp(-t * t / prm);
@@ -272,6 +274,7 @@ double ora_window_psi(int w, double t, int m, double prm)
 /* d psi / d t inside the support. */
 double ora_window_dpsi(int w, double t, int m, double prm)
 {
+    w &= 0xff; /* window kind (the lookup-table setting does not change the pair) */
     if (fabs(t) > (double)m) return 0.0;
     switch (w) {
     case ORA_GAUSS: return -2.0 * t / prm * exp(-t * t / prm);
@@ -286,10 +289,40 @@ double ora_window_dpsi(int w, double t, int m, double prm)
     }
 }
 
+/* PRE_LIN_PSI (Section 3.1, Table tab:nfftflags): psi read from a table of its values at the
+ * K points per unit t = j / K, linearly interpolated. A window spec w carries the window kind
+ * in its low 8 bits and K in the bits above (K = 0: the exact window). The interpolant between
+ * samples j / K and (j + 1) / K of |t| is written out directly (the samples are the table). */
+double ora_window_psi_eval(int w, double t, int m, double prm)
+{
+    const int K = w >> 8;
+    if (K == 0) return ora_window_psi(w, t, m, prm);
+    const double a = fabs(t);
+    if (a > (double)m) return 0.0;
+    const double u = a * (double)K;
+    const double j = floor(u), lam = u - j;
+    return (1.0 - lam) * ora_window_psi(w, j / K, m, prm) +
+           lam * ora_window_psi(w, (j + 1.0) / K, m, prm);
+}
+
+/* d/dt of the interpolant: the slope of the segment holding |t|, times sign(t). */
+double ora_window_dpsi_eval(int w, double t, int m, double prm)
+{
+    const int K = w >> 8;
+    if (K == 0) return ora_window_dpsi(w, t, m, prm);
+    const double a = fabs(t);
+    if (a > (double)m) return 0.0;
+    const double j = floor(a * (double)K);
+    const double slope =
+        (ora_window_psi(w, (j + 1.0) / K, m, prm) - ora_window_psi(w, j / K, m, prm)) * K;
+    return t < 0 ? -slope : slope;
+}
+
 /* phihat(k) = (1/n) FT[psi_untruncated](k/n). Gaussian: sqrt(pi b) e^{-b (pi k/n)^2} / n;
  * B-spline: sinc^{2m}(pi k / n) / n; sinc: M_{2m}(k / (n a)) / (n a); KB: ora_kb_phihat. */
 double ora_window_phihat(int w, int64_t k, int64_t n, int m, double prm)
 {
+    w &= 0xff; /* window kind (the lookup-table setting does not change the pair) */
     const double nu = (double)k / (double)n;
     switch (w) {
     case ORA_GAUSS: return sqrt(ORA_PI * prm) * exp(-prm * ORA_PI * ORA_PI * nu * nu) / (double)n;
@@ -459,7 +492,7 @@ void ora_nfft_B_w(int w, int d, const int64_t *N, const int64_t *n, int m, int64
             double wt = 1.0;
             int64_t gi = 0;
             for (int t = 0; t < d; t++) {
-                wt *= ora_window_psi(w, nx[t] - (double)l[t], m, b[t]);
+                wt *= ora_window_psi_eval(w, nx[t] - (double)l[t], m, b[t]);
                 gi = gi * n[t] + mod64(l[t], n[t]);
             }
             acc += g[gi] * wt;
@@ -493,7 +526,7 @@ void ora_nfft_BH_w(int w, int d, const int64_t *N, const int64_t *n, int m, int6
             double wt = 1.0;
             int64_t gi = 0;
             for (int t = 0; t < d; t++) {
-                wt *= ora_window_psi(w, nx[t] - (double)l[t], m, b[t]);
+                wt *= ora_window_psi_eval(w, nx[t] - (double)l[t], m, b[t]);
                 gi = gi * n[t] + mod64(l[t], n[t]);
             }
             g[gi] += f[j] * wt;
@@ -528,8 +561,8 @@ void ora_nfft_dB_w(int w, int d, const int64_t *N, const int64_t *n, int m, int6
             double wv[3], dw[3];
             int64_t gi = 0;
             for (int t = 0; t < d; t++) {
-                wv[t] = ora_window_psi(w, nx[t] - (double)l[t], m, b[t]);
-                dw[t] = (double)n[t] * ora_window_dpsi(w, nx[t] - (double)l[t], m, b[t]);
+                wv[t] = ora_window_psi_eval(w, nx[t] - (double)l[t], m, b[t]);
+                dw[t] = (double)n[t] * ora_window_dpsi_eval(w, nx[t] - (double)l[t], m, b[t]);
                 gi = gi * n[t] + mod64(l[t], n[t]);
             }
             for (int t = 0; t < d; t++) {
