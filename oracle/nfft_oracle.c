@@ -305,14 +305,16 @@ double ora_window_psi_eval(int w, double t, int m, double prm)
            lam * ora_window_psi(w, (j + 1.0) / K, m, prm);
 }
 
-/* d/dt of the interpolant: the slope of the segment holding |t|, times sign(t). */
+/* d/dt of the interpolant: the slope of the segment holding |t|, times sign(t). At a sample
+ * point (a kink) this is the right derivative in t, the limit from larger t: the segment above
+ * |t| for t >= 0, the one below |t| for t < 0. */
 double ora_window_dpsi_eval(int w, double t, int m, double prm)
 {
     const int K = w >> 8;
     if (K == 0) return ora_window_dpsi(w, t, m, prm);
     const double a = fabs(t);
     if (a > (double)m) return 0.0;
-    const double j = floor(a * (double)K);
+    const double j = t >= 0 ? floor(a * (double)K) : ceil(a * (double)K) - 1.0;
     const double slope =
         (ora_window_psi(w, (j + 1.0) / K, m, prm) - ora_window_psi(w, j / K, m, prm)) * K;
     return t < 0 ? -slope : slope;

@@ -107,3 +107,18 @@ def test_adjoint_identity_with_table(window):
     lhs = np.vdot(f, oracle.nfft(x, fh, n=n, m=m, window=window, lin_psi=100))
     rhs = np.vdot(oracle.nfft_adjoint(x, f, N, n=n, m=m, window=window, lin_psi=100), fh)
     assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+@pytest.mark.parametrize("window", ["kaiser_bessel", "sinc"])
+def test_derivative_at_a_sample_is_the_right_derivative(window):
+    """At a kink of the interpolant (t = j/K, e.g. a node on a grid point) the derivative is the
+    one from larger t: the forward difference quotient, on both sides of 0 and at |t| = m."""
+    m, K = 3, 32
+    prm = _prm(window, m)
+    e = 1e-4 / K
+    for j in (-m * K, -m * K + 1, -17, -1, 0, 1, 40, m * K - 1, m * K):
+        t = j / K
+        fwd = (oracle.window_psi_eval(window, t + e, m, prm, lin_psi=K)
+               - oracle.window_psi_eval(window, t, m, prm, lin_psi=K)) / e
+        got = oracle.window_dpsi_eval(window, t, m, prm, lin_psi=K)
+        assert got == pytest.approx(fwd, rel=1e-6, abs=1e-9 * oracle.window_psi(window, 0, m, prm)), j
