@@ -307,14 +307,16 @@ double ora_window_psi_eval(int w, double t, int m, double prm)
 
 /* d/dt of the interpolant: the slope of the segment holding |t|, times sign(t). At a sample
  * point (a kink) this is the right derivative in t, the limit from larger t: the segment above
- * |t| for t >= 0, the one below |t| for t < 0. */
+ * |t| for t >= 0, the one below |t| for t < 0; at t = +m, where the cut-off window jumps to 0,
+ * it is the derivative from inside the support, as for the exact window. */
 double ora_window_dpsi_eval(int w, double t, int m, double prm)
 {
     const int K = w >> 8;
     if (K == 0) return ora_window_dpsi(w, t, m, prm);
     const double a = fabs(t);
     if (a > (double)m) return 0.0;
-    const double j = t >= 0 ? floor(a * (double)K) : ceil(a * (double)K) - 1.0;
+    double j = t >= 0 ? floor(a * (double)K) : ceil(a * (double)K) - 1.0;
+    if (j > (double)m * K - 1.0) j = (double)m * K - 1.0;
     const double slope =
         (ora_window_psi(w, (j + 1.0) / K, m, prm) - ora_window_psi(w, j / K, m, prm)) * K;
     return t < 0 ? -slope : slope;

@@ -112,13 +112,15 @@ def test_adjoint_identity_with_table(window):
 @pytest.mark.parametrize("window", ["kaiser_bessel", "sinc"])
 def test_derivative_at_a_sample_is_the_right_derivative(window):
     """At a kink of the interpolant (t = j/K, e.g. a node on a grid point) the derivative is the
-    one from larger t: the forward difference quotient, on both sides of 0 and at |t| = m."""
+    one from larger t: the forward difference quotient, on both sides of 0 and at t = -m; at
+    t = +m, where the cut-off window jumps to 0, the backward one (from inside the support)."""
     m, K = 3, 32
     prm = _prm(window, m)
     e = 1e-4 / K
     for j in (-m * K, -m * K + 1, -17, -1, 0, 1, 40, m * K - 1, m * K):
         t = j / K
-        fwd = (oracle.window_psi_eval(window, t + e, m, prm, lin_psi=K)
-               - oracle.window_psi_eval(window, t, m, prm, lin_psi=K)) / e
+        s = -1.0 if j == m * K else 1.0
+        fwd = s * (oracle.window_psi_eval(window, t + s * e, m, prm, lin_psi=K)
+                   - oracle.window_psi_eval(window, t, m, prm, lin_psi=K)) / e
         got = oracle.window_dpsi_eval(window, t, m, prm, lin_psi=K)
         assert got == pytest.approx(fwd, rel=1e-6, abs=1e-9 * oracle.window_psi(window, 0, m, prm)), j
