@@ -143,6 +143,7 @@ typedef struct nfft_info {
     int64_t bin[3];
     size_t workspace_bytes;
     int window;
+    int window_table; /* NFFT_OPT_WINDOW_TABLE (0 = polynomial window) */
 } nfft_info;
 int nfft_get_info(nfft_plan plan, nfft_info *info);
 
@@ -193,6 +194,15 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           nfft_set_nodes again) and may change nfft_workspace_size: a
  *                           caller-owned workspace that became too small makes nfft_set_nodes
  *                           return NFFT_ENOMEM.
+ *   NFFT_OPT_WINDOW_TABLE   K = 0 (default): the window is evaluated from per-tap polynomials
+ *                           fitted to FP32 / FP64 accuracy. K in 2..65536: PRE_LIN_PSI
+ *                           (Section 3.1, Table tab:nfftflags) - the window is read from a
+ *                           table of its values at K points per unit of t = n_t x and linearly
+ *                           interpolated (error ~ K^-2 max|psi''| / 8, so it changes the result).
+ *                           The node derivative at a table sample is the slope of the segment
+ *                           above it (from inside the support at t = +m). The table (d x (K+1)
+ *                           x 2m values, plan precision) is allocated here and rebuilt when the
+ *                           window changes; waits for the device to go idle.
  *   NFFT_OPT_SUBPROBLEM     nodes per spreading work item (a power of two in 32..1024, 0 = the
  *                           default: 128 for 2-D FP32, else 1024): the sorted nodes of a bin are
  *                           cut into items of at
@@ -205,7 +215,8 @@ enum nfft_option {
     NFFT_OPT_BIN_2 = 4,
     NFFT_OPT_INTERP_METHOD = 5,
     NFFT_OPT_WINDOW = 6,
-    NFFT_OPT_SUBPROBLEM = 7
+    NFFT_OPT_SUBPROBLEM = 7,
+    NFFT_OPT_WINDOW_TABLE = 8
 };
 int nfft_set_option(nfft_plan plan, int key, int64_t value);
 

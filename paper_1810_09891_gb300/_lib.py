@@ -47,6 +47,7 @@ class NfftInfo(ctypes.Structure):
         ("bin", ctypes.c_int64 * 3),
         ("workspace_bytes", ctypes.c_size_t),
         ("window", ctypes.c_int),
+        ("window_table", ctypes.c_int),
     ]
 
 
@@ -78,6 +79,7 @@ OPT_BIN = (2, 3, 4)
 OPT_INTERP_METHOD = 5
 OPT_WINDOW = 6
 OPT_SUBPROBLEM = 7
+OPT_WINDOW_TABLE = 8
 WINDOWS = {"kaiser_bessel": 0, "gaussian": 1, "bspline": 2, "sinc": 3}
 INTERP_METHODS = {"auto": 0, "thread": 1, "warp": 2, "tile": 3}
 SPREAD_METHODS = {"auto": 0, "thread": 1, "warp_atomic": 2, "warp_private": 3, "octet": 4,

@@ -76,6 +76,8 @@ struct Geom {
     AxisWin win[kMaxDim];
     const void *poly;      // device table of window polynomials (plan precision), d axes
     const void *poly_host; // host copy of the same table (source of WinCoef kernel arguments)
+    const void *lin;       // lookup tables of the window (PRE_LIN_PSI), d axes, or null
+    int lin_k;             // samples per unit of t of those tables; 0 = polynomial window
 };
 
 // The window polynomial table as a kernel argument (same layout as the device table). Kernels

@@ -92,7 +92,7 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
     acc.y = (T)0;
     if (D == 1) {
         T w0[NT];
-        window_taps<T, MM, START>(tab, frac[0], (T)g.win[0].edge_w, w0);
+        eval_taps<T, MM, START>(g, tab, 0, frac[0], w0);
         const int n0 = g.n[0];
         if constexpr (PAIRS) {
             const int s0 = base[0] - MM + START, odd = s0 & 1;
@@ -111,14 +111,14 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
         }
     } else if (D == 2) {
         T w1[NT];
-        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
+        eval_taps<T, MM, START>(g, tab + AS, 1, frac[1], w1);
         const int n0 = g.n[0], n1 = g.n[1];
         const int s1 = base[1] - MM + START, odd = s1 & 1;
         float wv[NW];
         if constexpr (PAIRS) pair_weights<MM, START>(w1, odd, wv);
 #pragma unroll
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
+            const T w0 = eval_tap<T, MM>(g, tab, 0, i0, frac[0]);
             const C *row = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1;
             C in;
             if constexpr (PAIRS) {
@@ -138,14 +138,14 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
         }
     } else {
         T w1[NT], w2[NT];
-        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
-        window_taps<T, MM, START>(tab + 2 * AS, frac[2], (T)g.win[2].edge_w, w2);
+        eval_taps<T, MM, START>(g, tab + AS, 1, frac[1], w1);
+        eval_taps<T, MM, START>(g, tab + 2 * AS, 2, frac[2], w2);
         const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
         const int s2 = base[2] - MM + START, odd = s2 & 1;
         float wv[NW];
         if constexpr (PAIRS) pair_weights<MM, START>(w2, odd, wv);
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
+            const T w0 = eval_tap<T, MM>(g, tab, 0, i0, frac[0]);
             const C *plane = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1 * n2;
             C pl;
             pl.x = (T)0;
@@ -220,7 +220,7 @@ interp_tile_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T
     acc.y = (T)0;
     if (D == 1) {
         T w0[NT];
-        window_taps<T, MM, START>(tab, frac[0], (T)g.win[0].edge_w, w0);
+        eval_taps<T, MM, START>(g, tab, 0, frac[0], w0);
         const C *row = tile + loc[0];
 #pragma unroll
         for (int i = START; i < NT; i++) {
@@ -230,9 +230,9 @@ interp_tile_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T
         }
     } else if (D == 2) {
         T w1[NT];
-        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
+        eval_taps<T, MM, START>(g, tab + AS, 1, frac[1], w1);
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
+            const T w0 = eval_tap<T, MM>(g, tab, 0, i0, frac[0]);
             const C *row = tile + (loc[0] + i0) * st[0] + loc[1];
             C in;
             in.x = (T)0;
@@ -248,10 +248,10 @@ interp_tile_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T
         }
     } else {
         T w1[NT], w2[NT];
-        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
-        window_taps<T, MM, START>(tab + 2 * AS, frac[2], (T)g.win[2].edge_w, w2);
+        eval_taps<T, MM, START>(g, tab + AS, 1, frac[1], w1);
+        eval_taps<T, MM, START>(g, tab + 2 * AS, 2, frac[2], w2);
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
+            const T w0 = eval_tap<T, MM>(g, tab, 0, i0, frac[0]);
             const C *plane = tile + (loc[0] + i0) * st[0];
             C pl;
             pl.x = (T)0;
@@ -433,11 +433,11 @@ __global__ void __launch_bounds__(32 * kInterpWarps)
     T wa = (T)0, wb = (T)0;
     if (lane < NW) {
         const int t = lane / NT, i = lane - (lane / NT) * NT;
-        wa = window_tap<T, MM>(tab + t * AS, i, frac[t], (T)g.win[t].edge_w);
+        wa = eval_tap<T, MM>(g, tab + t * AS, t, i, frac[t]);
     }
     if (NW > 32 && lane + 32 < NW) {
         const int q = lane + 32, t = q / NT, i = q - (q / NT) * NT;
-        wb = window_tap<T, MM>(tab + t * AS, i, frac[t], (T)g.win[t].edge_w);
+        wb = eval_tap<T, MM>(g, tab + t * AS, t, i, frac[t]);
     }
     C acc = edge ? interp_warp_taps<T, D, MM, 0>(g, grid, base, wa, wb, lane)
                  : interp_warp_taps<T, D, MM, 1>(g, grid, base, wa, wb, lane);
@@ -470,7 +470,7 @@ __device__ __forceinline__ void grad_node(const Geom &g, const T *__restrict__ t
 #pragma unroll
         for (int i = START; i < NT; i++) {
             T w, dw;
-            window_tap_d<T, MM>(tab, i, frac[0], (T)g.win[0].edge_w, (T)g.win[0].edge_dw, w, dw);
+            eval_tap_d<T, MM>(g, tab, 0, i, frac[0], w, dw);
             const C v = grid[wrapn(base[0] - MM + i, n0)];
             acc[0].x += v.x * dw;
             acc[0].y += v.y * dw;
@@ -479,12 +479,11 @@ __device__ __forceinline__ void grad_node(const Geom &g, const T *__restrict__ t
         T w1[NT], d1[NT];
 #pragma unroll
         for (int i = START; i < NT; i++)
-            window_tap_d<T, MM>(tab + AS, i, frac[1], (T)g.win[1].edge_w, (T)g.win[1].edge_dw,
-                                w1[i], d1[i]);
+            eval_tap_d<T, MM>(g, tab + AS, 1, i, frac[1], w1[i], d1[i]);
         const int n0 = g.n[0], n1 = g.n[1];
         for (int i0 = START; i0 < NT; i0++) {
             T w0, d0;
-            window_tap_d<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w, (T)g.win[0].edge_dw, w0, d0);
+            eval_tap_d<T, MM>(g, tab, 0, i0, frac[0], w0, d0);
             const C *row = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1;
             C s0, s1;
             s0.x = s0.y = s1.x = s1.y = (T)0;
@@ -505,15 +504,13 @@ __device__ __forceinline__ void grad_node(const Geom &g, const T *__restrict__ t
         T w1[NT], d1[NT], w2[NT], d2[NT];
 #pragma unroll
         for (int i = START; i < NT; i++) {
-            window_tap_d<T, MM>(tab + AS, i, frac[1], (T)g.win[1].edge_w, (T)g.win[1].edge_dw,
-                                w1[i], d1[i]);
-            window_tap_d<T, MM>(tab + 2 * AS, i, frac[2], (T)g.win[2].edge_w,
-                                (T)g.win[2].edge_dw, w2[i], d2[i]);
+            eval_tap_d<T, MM>(g, tab + AS, 1, i, frac[1], w1[i], d1[i]);
+            eval_tap_d<T, MM>(g, tab + 2 * AS, 2, i, frac[2], w2[i], d2[i]);
         }
         const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
         for (int i0 = START; i0 < NT; i0++) {
             T w0, d0;
-            window_tap_d<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w, (T)g.win[0].edge_dw, w0, d0);
+            eval_tap_d<T, MM>(g, tab, 0, i0, frac[0], w0, d0);
             const C *plane = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1 * n2;
             C p0, p1, p2;  // plane sums for the three partial derivatives
             p0.x = p0.y = p1.x = p1.y = p2.x = p2.y = (T)0;

@@ -212,6 +212,8 @@ struct gbnfft_plan {
     int64_t sub_req = 0;             // requested nodes per spreading subproblem (0 = default)
     int sub_max = kMaxSub;
     int window = 0;  // WindowKind
+    int lin_k = 0;            // PRE_LIN_PSI: samples per unit of t of the window tables, 0 = off
+    void *lin_tab = nullptr;  // device tables (plan precision), d x (K + 1) x 2m values
     // plan-owned device tables: [deconv_t, twiddles_t]_t, window polynomials, status word
     void *tables = nullptr;
     size_t off_dc[3] = {0, 0, 0}, off_tw[3] = {0, 0, 0}, off_poly = 0, off_status = 0;
@@ -598,7 +600,57 @@ static void set_window_constants(gbnfft_plan *p)
         g.win[t].prm = prm;
         g.win[t].edge_w = psi_host(p->window, double(p->m), p->m, prm) / psi0;
         g.win[t].edge_dw = dpsi_edge_host(p->window, p->m, prm) / psi0;
+        if (p->lin_k > 0) {  // slope of the last table segment inside the support
+            const double K = double(p->lin_k);
+            g.win[t].edge_dw =
+                (g.win[t].edge_w - psi_host(p->window, double(p->m) - 1.0 / K, p->m, prm) / psi0) *
+                K;
+        }
     }
+}
+
+// PRE_LIN_PSI tables for the plan's window: lt[j * 2m + i - 1] = psibar(j / K + m - i) per axis,
+// uploaded to a plan-owned allocation (replaced when K or the window changes).
+static int build_lin_tables(gbnfft_plan *p)
+{
+    Geom &g = p->geom;
+    if (p->lin_tab) {
+        cudaDeviceSynchronize();
+        cudaFree(p->lin_tab);
+        p->lin_tab = nullptr;
+    }
+    g.lin = nullptr;
+    g.lin_k = 0;
+    if (p->lin_k <= 0) return NFFT_OK;
+    const int K = p->lin_k, m = p->m, W = 2 * m;
+    const size_t per_axis = size_t(K + 1) * W;
+    std::vector<double> h(per_axis * p->d);
+    for (int t = 0; t < p->d; t++) {
+        const double prm = g.win[t].prm;
+        const double psi0 = psi_host(p->window, 0.0, m, prm);
+        for (int j = 0; j <= K; j++)
+            for (int i = 1; i <= W; i++)
+                h[t * per_axis + size_t(j) * W + (i - 1)] =
+                    psi_host(p->window, double(j) / K + double(m - i), m, prm) / psi0;
+    }
+    const size_t bytes = h.size() * p->rsize;
+    std::vector<float> hf;
+    const void *src = h.data();
+    if (p->dtype == NFFT_FP32) {
+        hf.assign(h.begin(), h.end());
+        src = hf.data();
+    }
+    cudaError_t e = cudaMalloc(&p->lin_tab, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(p->lin_tab, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (p->lin_tab) cudaFree(p->lin_tab);
+        p->lin_tab = nullptr;
+        return e == cudaErrorMemoryAllocation ? NFFT_ENOMEM : NFFT_ECUDA;
+    }
+    g.lin = p->lin_tab;
+    g.lin_k = K;
+    return NFFT_OK;
 }
 
 // Host image of the tables below off_status (the layout is fixed by d, N, n, m and precision).
@@ -721,7 +773,7 @@ static int set_window(gbnfft_plan *p, int kind)
         cudaGetLastError();
         return NFFT_ECUDA;
     }
-    return NFFT_OK;
+    return build_lin_tables(p);  // the lookup tables follow the window (no-op when off)
 }
 
 int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const int64_t *n, int m,
@@ -866,6 +918,7 @@ int nfft_destroy(nfft_plan p)
     if (p->stream) cudaStreamSynchronize(p->stream);
     else cudaDeviceSynchronize();
     if (p->tables) cudaFree(p->tables);
+    if (p->lin_tab) cudaFree(p->lin_tab);
     if (p->ws_owned && p->ws) cudaFree(p->ws);
     if (p->stage) cudaFree(p->stage);
     for (auto &pp : p->prof) {
@@ -922,6 +975,7 @@ int nfft_get_info(nfft_plan p, nfft_info *info)
     }
     info->workspace_bytes = p->ws_need;
     info->window = p->window;
+    info->window_table = p->lin_k;
     return NFFT_OK;
 }
 
@@ -1012,6 +1066,20 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
         if (value < kWinKB || value > kWinSinc) return NFFT_EINVAL;
         set_device(p);
         return set_window(p, (int)value);
+    case NFFT_OPT_WINDOW_TABLE: {
+        if (value < 0 || value == 1 || value > 65536) return NFFT_EINVAL;
+        set_device(p);
+        const int old = p->lin_k;
+        p->lin_k = (int)value;
+        set_window_constants(p);
+        const int rc = build_lin_tables(p);
+        if (rc) {
+            p->lin_k = old;
+            set_window_constants(p);
+            build_lin_tables(p);
+        }
+        return rc;
+    }
     case NFFT_OPT_SUBPROBLEM: {
         if (value < 0 || value > kMaxSub || (value > 0 && (value < 32 || !is_pow2(value))))
             return NFFT_EINVAL;

@@ -71,7 +71,7 @@ __device__ __forceinline__ void spread_node(const Geom &g, const T *__restrict__
     constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
     if (D == 1) {
         T w0[NT];
-        window_taps<T, MM, START>(tab, frac[0], (T)g.win[0].edge_w, w0);
+        eval_taps<T, MM, START>(g, tab, 0, frac[0], w0);
 #pragma unroll
         for (int i = START; i < NT; i++) {
             T *c = tile + 2 * (loc[0] + i);
@@ -80,9 +80,9 @@ __device__ __forceinline__ void spread_node(const Geom &g, const T *__restrict__
         }
     } else if (D == 2) {
         T w1[NT];
-        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
+        eval_taps<T, MM, START>(g, tab + AS, 1, frac[1], w1);
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
+            const T w0 = eval_tap<T, MM>(g, tab, 0, i0, frac[0]);
             const T ar = vr * w0, ai = vi * w0;
             T *row = tile + 2 * ((loc[0] + i0) * tdim[1] + loc[1]);
 #pragma unroll
@@ -93,10 +93,10 @@ __device__ __forceinline__ void spread_node(const Geom &g, const T *__restrict__
         }
     } else {
         T w1[NT], w2[NT];
-        window_taps<T, MM, START>(tab + AS, frac[1], (T)g.win[1].edge_w, w1);
-        window_taps<T, MM, START>(tab + 2 * AS, frac[2], (T)g.win[2].edge_w, w2);
+        eval_taps<T, MM, START>(g, tab + AS, 1, frac[1], w1);
+        eval_taps<T, MM, START>(g, tab + 2 * AS, 2, frac[2], w2);
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = window_tap<T, MM>(tab, i0, frac[0], (T)g.win[0].edge_w);
+            const T w0 = eval_tap<T, MM>(g, tab, 0, i0, frac[0]);
             const T ar = vr * w0, ai = vi * w0;
             T *plane = tile + 2 * ((loc[0] + i0) * tdim[1] * tdim[2]);
 #pragma unroll
@@ -421,11 +421,20 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
                         if (ta == t) fa = frac[t];
                         if (tb == t) fb = frac[t];
                     }
-                    if (lane < NW) wa = ia > 0 ? poly_horner<T, DEG>(ca, (T)2 * fa - (T)1)
-                                               : (fa == (T)0 ? ea : (T)0);
-                    if (NW > 32 && lane + 32 < NW)
-                        wb = ib > 0 ? poly_horner<T, DEG>(cb, (T)2 * fb - (T)1)
-                                    : (fb == (T)0 ? eb : (T)0);
+                    if (g.lin_k) {  // lookup-table window
+                        if (lane < NW)
+                            wa = lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, ta), g.lin_k, ia,
+                                                fa, ea);
+                        if (NW > 32 && lane + 32 < NW)
+                            wb = lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, tb), g.lin_k, ib,
+                                                fb, eb);
+                    } else {
+                        if (lane < NW) wa = ia > 0 ? poly_horner<T, DEG>(ca, (T)2 * fa - (T)1)
+                                                   : (fa == (T)0 ? ea : (T)0);
+                        if (NW > 32 && lane + 32 < NW)
+                            wb = ib > 0 ? poly_horner<T, DEG>(cb, (T)2 * fb - (T)1)
+                                        : (fb == (T)0 ? eb : (T)0);
+                    }
                 }
                 int off = 0;
 #pragma unroll
@@ -519,7 +528,7 @@ __device__ __forceinline__ void spread_octet_node(typename Cplx<T>::type *tile, 
                                                   T frac0, T frac1, const T *ca, T ea,
                                                   const T *cb, T eb,
                                                   typename Cplx<T>::type v, int l,
-                                                  unsigned mask)
+                                                  unsigned mask, const T *la, const T *lb, int K)
 {
     using C = typename Cplx<T>::type;
     constexpr int DEG = PolyDeg<T, MM>::value;
@@ -530,13 +539,18 @@ __device__ __forceinline__ void spread_octet_node(typename Cplx<T>::type *tile, 
     T w1a = (T)0, w1b = (T)0, w0a = (T)0, w0b = (T)0;
     if (l < PER) {
         const int i = START + l;
-        w1a = i == 0 ? (frac1 == (T)0 ? eb : (T)0) : poly_horner_tap<T, DEG>(cb, i, z1);
-        w0a = i == 0 ? (frac0 == (T)0 ? ea : (T)0) : poly_horner_tap<T, DEG>(ca, i, z0);
+        if (K) {  // lookup-table window (la, lb: the axes' tables)
+            w1a = lin_tap<T, MM>(lb, K, i, frac1, eb);
+            w0a = lin_tap<T, MM>(la, K, i, frac0, ea);
+        } else {
+            w1a = i == 0 ? (frac1 == (T)0 ? eb : (T)0) : poly_horner_tap<T, DEG>(cb, i, z1);
+            w0a = i == 0 ? (frac0 == (T)0 ? ea : (T)0) : poly_horner_tap<T, DEG>(ca, i, z0);
+        }
     }
     if (PER > 8 && l + 8 < PER) {
         const int i = START + l + 8;
-        w1b = poly_horner_tap<T, DEG>(cb, i, z1);
-        w0b = poly_horner_tap<T, DEG>(ca, i, z0);
+        w1b = K ? lin_tap<T, MM>(lb, K, i, frac1, eb) : poly_horner_tap<T, DEG>(cb, i, z1);
+        w0b = K ? lin_tap<T, MM>(la, K, i, frac0, ea) : poly_horner_tap<T, DEG>(ca, i, z0);
     }
     const T ar = w1a * v.x, ai = w1a * v.y, br = w1b * v.x, bi = w1b * v.y;
     C *col = tile + off + l;
@@ -584,6 +598,8 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
     C *st_val = reinterpret_cast<C *>(st_rec + kSpreadChunk);
     const T *ca = tab, *cb = tab + AS;
     const T ea = (T)g.win[0].edge_w, eb = (T)g.win[1].edge_w;
+    const T *la = g.lin_k ? lin_axis<T, MM>(g.lin, g.lin_k, 0) : nullptr;
+    const T *lb = g.lin_k ? lin_axis<T, MM>(g.lin, g.lin_k, 1) : nullptr;
     const int nsub = nsub_total[0];
     __shared__ int s_sp;
     for (int sp = next_subproblem(nsub_total, &s_sp); sp < nsub;
@@ -623,10 +639,10 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
                 const T fr0 = r.fr[0], fr1 = r.fr[1];
                 if (fr0 == (T)0 || fr1 == (T)0)  // uniform inside the group (one node)
                     spread_octet_node<T, MM, 0>(mine, td1, loc0 * td1 + loc1, fr0, fr1, ca, ea,
-                                                cb, eb, v, l, mask);
+                                                cb, eb, v, l, mask, la, lb, g.lin_k);
                 else
                     spread_octet_node<T, MM, 1>(mine, td1, (loc0 + 1) * td1 + loc1 + 1, fr0,
-                                                fr1, ca, ea, cb, eb, v, l, mask);
+                                                fr1, ca, ea, cb, eb, v, l, mask, la, lb, g.lin_k);
                 __syncwarp(mask);
             }
             __syncthreads();
@@ -776,8 +792,18 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
                 const int loc0 = ((r.cell >> g.cbits[1]) & g.cmask[0]) - org0;
                 const T fr0 = r.fr[0], fr1 = r.fr[1];
                 if (fr0 != (T)0 && fr1 != (T)0) {  // uniform inside the half (one node)
-                    const T w1 = poly_horner<T, DEG>(cc, (T)2 * fr1 - (T)1);
-                    const T w0h = poly_horner<T, DEG>(cr, (T)2 * fr0 - (T)1);
+                    T w1, w0h;
+                    if (g.lin_k) {  // lookup-table window
+                        w1 = c < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 1), g.lin_k,
+                                                      c + 1, fr1, e1)
+                                     : (T)0;
+                        w0h = h < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 0),
+                                                       g.lin_k, h + 1, fr0, e0)
+                                      : (T)0;
+                    } else {
+                        w1 = poly_horner<T, DEG>(cc, (T)2 * fr1 - (T)1);
+                        w0h = poly_horner<T, DEG>(cr, (T)2 * fr0 - (T)1);
+                    }
                     const T ar = w1 * v.x, ai = w1 * v.y;
                     C *col = mine + (loc0 + 1) * pitch + loc1 + 1 + c;
 #pragma unroll
@@ -794,8 +820,8 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
                 } else {
                     for (int q = h; q < NT * NT; q += 16) {
                         const int a0 = q / NT, a1 = q - a0 * NT;
-                        const T w = window_tap<T, MM>(tab, a0, fr0, e0) *
-                                    window_tap<T, MM>(tab + AS, a1, fr1, e1);
+                        const T w = eval_tap<T, MM>(g, tab, 0, a0, fr0) *
+                                    eval_tap<T, MM>(g, tab + AS, 1, a1, fr1);
                         C *p = mine + (loc0 + a0) * pitch + loc1 + a1;
                         C a = *p;
                         a.x += w * v.x;

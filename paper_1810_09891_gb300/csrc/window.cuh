@@ -97,6 +97,112 @@ __device__ __forceinline__ T poly_horner_tap(const T *c, int i, T z)
     return acc;
 }
 
+// ------------------------------------------------------------------- lookup table (PRE_LIN_PSI)
+// With NFFT_OPT_WINDOW_TABLE = K the window comes from a table of psibar at K points per unit
+// of t, linearly interpolated (Section 3.1, Table tab:nfftflags, PRE_LIN_PSI). The table of an
+// axis is laid out per offset sample: lt[j * 2m + (i - 1)] = psibar(j / K + m - i) for tap
+// i = 1..2m and j = 0..K, so that the 2m taps of a node share one interpolation position
+// frac * K and read two runs of 2m neighbouring values. The derivative at a sample is the
+// slope of the segment above it (the right derivative in t).
+template <typename T>
+__device__ __forceinline__ void lin_pos(T frac, int K, int &j, T &lam)
+{
+    const T u = frac * (T)K;  // frac in [0, 1]
+    j = (int)u;
+    if (j > K - 1) j = K - 1;
+    lam = u - (T)j;
+}
+
+template <typename T, int MM>
+__device__ __forceinline__ T lin_at(const T *__restrict__ lt, int j, T lam, int i)
+{
+    const T a = lt[j * (2 * MM) + i - 1], b = lt[(j + 1) * (2 * MM) + i - 1];
+    return fma(lam, b - a, a);
+}
+
+// All taps of one axis (as window_taps).
+template <typename T, int MM, int START>
+__device__ __forceinline__ void lin_taps(const T *__restrict__ lt, int K, T frac, T edge_w, T *w)
+{
+    int j;
+    T lam;
+    lin_pos(frac, K, j, lam);
+#pragma unroll
+    for (int i = 1; i <= 2 * MM; i++) w[i] = lin_at<T, MM>(lt, j, lam, i);
+    if (START == 0) w[0] = frac == (T)0 ? edge_w : (T)0;
+}
+
+// One tap i (0..2m) of one axis (as window_tap).
+template <typename T, int MM>
+__device__ __forceinline__ T lin_tap(const T *__restrict__ lt, int K, int i, T frac, T edge_w)
+{
+    if (i == 0) return frac == (T)0 ? edge_w : (T)0;
+    int j;
+    T lam;
+    lin_pos(frac, K, j, lam);
+    return lin_at<T, MM>(lt, j, lam, i);
+}
+
+// Value and t-derivative of one tap (as window_tap_d; edge_dw is the plan's edge slope).
+template <typename T, int MM>
+__device__ __forceinline__ void lin_tap_d(const T *__restrict__ lt, int K, int i, T frac,
+                                          T edge_w, T edge_dw, T &w, T &dw)
+{
+    if (i == 0) {
+        const bool on = frac == (T)0;
+        w = on ? edge_w : (T)0;
+        dw = on ? edge_dw : (T)0;
+        return;
+    }
+    int j;
+    T lam;
+    lin_pos(frac, K, j, lam);
+    const T a = lt[j * (2 * MM) + i - 1], b = lt[(j + 1) * (2 * MM) + i - 1];
+    w = fma(lam, b - a, a);
+    dw = (b - a) * (T)K;
+}
+
+// Axis t's table inside the plan's table block.
+template <typename T, int MM>
+__device__ __forceinline__ const T *lin_axis(const void *lin, int K, int t)
+{
+    return static_cast<const T *>(lin) + (size_t)t * (K + 1) * (2 * MM);
+}
+
+// Window evaluation on axis t of a plan: the lookup table when the plan has one (g.lin_k > 0,
+// a uniform branch), else the per-tap polynomials `poly` of that axis.
+template <typename T, int MM, int START>
+__device__ __forceinline__ void eval_taps(const Geom &g, const T *__restrict__ poly, int t, T frac,
+                                          T *w)
+{
+    if (g.lin_k)
+        lin_taps<T, MM, START>(lin_axis<T, MM>(g.lin, g.lin_k, t), g.lin_k, frac,
+                               (T)g.win[t].edge_w, w);
+    else
+        window_taps<T, MM, START>(poly, frac, (T)g.win[t].edge_w, w);
+}
+
+template <typename T, int MM>
+__device__ __forceinline__ T eval_tap(const Geom &g, const T *__restrict__ poly, int t, int i,
+                                      T frac)
+{
+    if (g.lin_k)
+        return lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, t), g.lin_k, i, frac,
+                              (T)g.win[t].edge_w);
+    return window_tap<T, MM>(poly, i, frac, (T)g.win[t].edge_w);
+}
+
+template <typename T, int MM>
+__device__ __forceinline__ void eval_tap_d(const Geom &g, const T *__restrict__ poly, int t, int i,
+                                           T frac, T &w, T &dw)
+{
+    if (g.lin_k)
+        lin_tap_d<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, t), g.lin_k, i, frac, (T)g.win[t].edge_w,
+                         (T)g.win[t].edge_dw, w, dw);
+    else
+        window_tap_d<T, MM>(poly, i, frac, (T)g.win[t].edge_w, (T)g.win[t].edge_dw, w, dw);
+}
+
 // Copy the window tables (d axes) into shared memory; every thread of the CTA must call it.
 template <typename T, int MM>
 __device__ __forceinline__ void load_window_tables(T *dst, const void *src, int d)

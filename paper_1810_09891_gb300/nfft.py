@@ -114,13 +114,18 @@ class Plan:
 
     # ------------------------------------------------------------------ API
     def set_option(self, key: str, value) -> None:
-        """``window`` in {kaiser_bessel, gaussian, bspline, sinc} (changes the approximation;
-        waits for the device to go idle), or tuning: ``spread_method`` in {auto, thread,
+        """``window`` in {kaiser_bessel, gaussian, bspline, sinc} and ``window_table`` (K > 0:
+        the window from a K-point-per-cell lookup table, PRE_LIN_PSI; 0: polynomials) change the
+        approximation (they wait for the device to go idle); tuning: ``spread_method`` in {auto, thread,
         warp_atomic, warp_private, octet, half}, ``interp_method`` in {auto, thread, warp, tile}, or
         ``bin0`` / ``bin1`` / ``bin2`` (power-of-two bin sizes), ``subproblem`` (nodes per
         spreading work item, a power of two in 32..1024). Changing a bin or subproblem size
         discards the node precomputation; set the nodes again afterwards."""
         L = _lib.lib()
+        if key == "window_table":
+            check(L.nfft_set_option(self._h, _lib.OPT_WINDOW_TABLE, int(value)),
+                  "nfft_set_option")
+            return
         if key == "window":
             if value not in _lib.WINDOWS:
                 raise ValueError(f"window must be one of {sorted(_lib.WINDOWS)}")
@@ -204,7 +209,8 @@ class Plan:
                     N=tuple(int(i.N[t]) for t in range(i.d)),
                     n=tuple(int(i.n[t]) for t in range(i.d)),
                     bin=tuple(int(i.bin[t]) for t in range(i.d)),
-                    workspace_bytes=int(i.workspace_bytes), window=inv[int(i.window)])
+                    workspace_bytes=int(i.workspace_bytes), window=inv[int(i.window)],
+                    window_table=int(i.window_table))
 
     def status(self) -> int:
         """Wait for the stream; return (and clear) the device-side error code."""
