@@ -77,7 +77,7 @@ __device__ __forceinline__ float2 row_dot_pairs(const float2 *__restrict__ row, 
     return in;
 }
 
-template <typename T, int D, int MM, int START>
+template <typename T, int D, int MM, int START, int MODE>
 __device__ __forceinline__ typename Cplx<T>::type
 interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::type *__restrict__ grid,
             const int *base, const T *frac)
@@ -92,7 +92,7 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
     acc.y = (T)0;
     if (D == 1) {
         T w0[NT];
-        eval_taps<T, MM, START>(g, tab, 0, frac[0], w0);
+        eval_taps<T, MM, START, MODE>(g, tab, 0, frac[0], w0);
         const int n0 = g.n[0];
         if constexpr (PAIRS) {
             const int s0 = base[0] - MM + START, odd = s0 & 1;
@@ -111,14 +111,14 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
         }
     } else if (D == 2) {
         T w1[NT];
-        eval_taps<T, MM, START>(g, tab + AS, 1, frac[1], w1);
+        eval_taps<T, MM, START, MODE>(g, tab + AS, 1, frac[1], w1);
         const int n0 = g.n[0], n1 = g.n[1];
         const int s1 = base[1] - MM + START, odd = s1 & 1;
         float wv[NW];
         if constexpr (PAIRS) pair_weights<MM, START>(w1, odd, wv);
 #pragma unroll
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = eval_tap<T, MM>(g, tab, 0, i0, frac[0]);
+            const T w0 = eval_tap<T, MM, MODE>(g, tab, 0, i0, frac[0]);
             const C *row = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1;
             C in;
             if constexpr (PAIRS) {
@@ -138,14 +138,14 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
         }
     } else {
         T w1[NT], w2[NT];
-        eval_taps<T, MM, START>(g, tab + AS, 1, frac[1], w1);
-        eval_taps<T, MM, START>(g, tab + 2 * AS, 2, frac[2], w2);
+        eval_taps<T, MM, START, MODE>(g, tab + AS, 1, frac[1], w1);
+        eval_taps<T, MM, START, MODE>(g, tab + 2 * AS, 2, frac[2], w2);
         const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
         const int s2 = base[2] - MM + START, odd = s2 & 1;
         float wv[NW];
         if constexpr (PAIRS) pair_weights<MM, START>(w2, odd, wv);
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = eval_tap<T, MM>(g, tab, 0, i0, frac[0]);
+            const T w0 = eval_tap<T, MM, MODE>(g, tab, 0, i0, frac[0]);
             const C *plane = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1 * n2;
             C pl;
             pl.x = (T)0;
@@ -176,7 +176,7 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
     return acc;
 }
 
-template <typename T, int D, int MM>
+template <typename T, int D, int MM, bool LIN>
 __global__ void __launch_bounds__(kInterpThreads)
     interp_kernel(Geom g, const __grid_constant__ WinCoef<T, MM> wc,
                   const typename Cplx<T>::type *__restrict__ grid,
@@ -192,10 +192,11 @@ __global__ void __launch_bounds__(kInterpThreads)
     bool edge;
     decode_node<T, D>(g, r, base, frac, edge);
     typename Cplx<T>::type v;
+    constexpr int MODE = LIN ? 2 : 1;
     if (!edge)
-        v = interp_node<T, D, MM, 1>(g, tab, grid, base, frac);
+        v = interp_node<T, D, MM, 1, MODE>(g, tab, grid, base, frac);
     else
-        v = interp_node<T, D, MM, 0>(g, tab, grid, base, frac);
+        v = interp_node<T, D, MM, 0, MODE>(g, tab, grid, base, frac);
     f[perm[s]] = v;
 }
 
@@ -605,8 +606,12 @@ cudaError_t launch_interp_m(const Geom &g, const typename Cplx<T>::type *grid,
             g, grid, rec, perm, (int)M, f);
     } else {
         const int64_t blocks = (M + kInterpThreads - 1) / kInterpThreads;
-        interp_kernel<T, D, MM><<<(unsigned)blocks, kInterpThreads, 0, stream>>>(
-            g, make_wincoef<T, MM>(g), grid, rec, perm, (int)M, f);
+        if (g.lin_k)
+            interp_kernel<T, D, MM, true><<<(unsigned)blocks, kInterpThreads, 0, stream>>>(
+                g, make_wincoef<T, MM>(g), grid, rec, perm, (int)M, f);
+        else
+            interp_kernel<T, D, MM, false><<<(unsigned)blocks, kInterpThreads, 0, stream>>>(
+                g, make_wincoef<T, MM>(g), grid, rec, perm, (int)M, f);
     }
     return cudaGetLastError();
 }

@@ -716,7 +716,7 @@ __host__ __device__ constexpr size_t half_stage_bytes()
     return kHalfChunk * (sizeof(typename RecOf<T>::type) + sizeof(typename Cplx<T>::type));
 }
 
-template <typename T, int MM>
+template <typename T, int MM, bool LIN>
 __global__ void __launch_bounds__(32 * kHalfWarps)
     spread_half_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
                        const typename RecOf<T>::type *__restrict__ rec,
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
                 const T fr0 = r.fr[0], fr1 = r.fr[1];
                 if (fr0 != (T)0 && fr1 != (T)0) {  // uniform inside the half (one node)
                     T w1, w0h;
-                    if (g.lin_k) {  // lookup-table window
+                    if constexpr (LIN) {  // lookup-table window
                         w1 = c < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 1), g.lin_k,
                                                       c + 1, fr1, e1)
                                      : (T)0;
@@ -820,8 +820,8 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
                 } else {
                     for (int q = h; q < NT * NT; q += 16) {
                         const int a0 = q / NT, a1 = q - a0 * NT;
-                        const T w = eval_tap<T, MM>(g, tab, 0, a0, fr0) *
-                                    eval_tap<T, MM>(g, tab + AS, 1, a1, fr1);
+                        const T w = eval_tap<T, MM, LIN ? 2 : 1>(g, tab, 0, a0, fr0) *
+                                    eval_tap<T, MM, LIN ? 2 : 1>(g, tab + AS, 1, a1, fr1);
                         C *p = mine + (loc0 + a0) * pitch + loc1 + a1;
                         C a = *p;
                         a.x += w * v.x;
@@ -939,11 +939,19 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
     } else if (method == kSpreadHalf) {
         if constexpr (D == 2) {
             const size_t smem = half_tiles + half_stage_bytes<T>();
-            e = launch_persistent(spread_half_kernel<T, MM>, smem, 32 * kHalfWarps, max_subs,
-                                  blocks);
-            if (e != cudaSuccess) return e;
-            spread_half_kernel<T, MM><<<blocks, 32 * kHalfWarps, smem, stream>>>(
-                g, f, rec, perm, subs, nsub_total, grid);
+            if (g.lin_k) {
+                e = launch_persistent(spread_half_kernel<T, MM, true>, smem, 32 * kHalfWarps,
+                                      max_subs, blocks);
+                if (e != cudaSuccess) return e;
+                spread_half_kernel<T, MM, true><<<blocks, 32 * kHalfWarps, smem, stream>>>(
+                    g, f, rec, perm, subs, nsub_total, grid);
+            } else {
+                e = launch_persistent(spread_half_kernel<T, MM, false>, smem, 32 * kHalfWarps,
+                                      max_subs, blocks);
+                if (e != cudaSuccess) return e;
+                spread_half_kernel<T, MM, false><<<blocks, 32 * kHalfWarps, smem, stream>>>(
+                    g, f, rec, perm, subs, nsub_total, grid);
+            }
         }
     } else if (method == kSpreadWarpPrivate) {
         const size_t smem = (tile * kSpreadWarps + 15) / 16 * 16 + spread_stage_bytes<T>();

@@ -169,34 +169,40 @@ __device__ __forceinline__ const T *lin_axis(const void *lin, int K, int t)
     return static_cast<const T *>(lin) + (size_t)t * (K + 1) * (2 * MM);
 }
 
-// Window evaluation on axis t of a plan: the lookup table when the plan has one (g.lin_k > 0,
-// a uniform branch), else the per-tap polynomials `poly` of that axis.
-template <typename T, int MM, int START>
+// Window evaluation on axis t of a plan: the lookup table when the plan has one (g.lin_k > 0),
+// else the per-tap polynomials `poly` of that axis. MODE 0 decides at run time (a uniform
+// branch); kernels instantiated per evaluation pass MODE 1 (polynomials) or 2 (table).
+template <int MODE> __device__ __forceinline__ bool use_table(const Geom &g)
+{
+    return MODE == 2 || (MODE == 0 && g.lin_k > 0);
+}
+
+template <typename T, int MM, int START, int MODE = 0>
 __device__ __forceinline__ void eval_taps(const Geom &g, const T *__restrict__ poly, int t, T frac,
                                           T *w)
 {
-    if (g.lin_k)
+    if (use_table<MODE>(g))
         lin_taps<T, MM, START>(lin_axis<T, MM>(g.lin, g.lin_k, t), g.lin_k, frac,
                                (T)g.win[t].edge_w, w);
     else
         window_taps<T, MM, START>(poly, frac, (T)g.win[t].edge_w, w);
 }
 
-template <typename T, int MM>
+template <typename T, int MM, int MODE = 0>
 __device__ __forceinline__ T eval_tap(const Geom &g, const T *__restrict__ poly, int t, int i,
                                       T frac)
 {
-    if (g.lin_k)
+    if (use_table<MODE>(g))
         return lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, t), g.lin_k, i, frac,
                               (T)g.win[t].edge_w);
     return window_tap<T, MM>(poly, i, frac, (T)g.win[t].edge_w);
 }
 
-template <typename T, int MM>
+template <typename T, int MM, int MODE = 0>
 __device__ __forceinline__ void eval_tap_d(const Geom &g, const T *__restrict__ poly, int t, int i,
                                            T frac, T &w, T &dw)
 {
-    if (g.lin_k)
+    if (use_table<MODE>(g))
         lin_tap_d<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, t), g.lin_k, i, frac, (T)g.win[t].edge_w,
                          (T)g.win[t].edge_dw, w, dw);
     else
