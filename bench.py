@@ -151,6 +151,71 @@ def profiled_traffic(stage: str, workload_name: str):
         return None
 
 
+NUM_SMS = 152  # GB300
+
+
+def profiled_value(stage: str, workload_name: str, key: str):
+    """A counter from a committed ncu summary taken on the current kernel source, else None."""
+    path = os.path.join(ROOT, "profiles", f"{stage}_{workload_name}.txt")
+    if not os.path.exists(path) or stage not in STAGE_SOURCES:
+        return None
+    vals = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha") != source_sha(STAGE_SOURCES[stage]):
+        return None
+    try:
+        return float(vals[key])
+    except (KeyError, ValueError):
+        return None
+
+
+def _clock_ghz(clk) -> float:
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    return float(mhz) / 1000.0
+
+
+def onchip_roofline(stage, wl, M, m, ms, clk):
+    """The spreading kernel against the L1 / shared-memory data pipe, which carries its tile
+    read-modify-writes: one 128-byte wavefront per cycle per SM. The tap floor is 2 (load and
+    store) x (2m)^d taps x 8 bytes (FP32 complex) / 128 per node; the measured wavefront count
+    comes from the committed ncu summary when it matches the kernel source."""
+    if stage != "spread":
+        return None
+    d = len(wl["N"])
+    peak = NUM_SMS * _clock_ghz(clk) * 1e9  # wavefronts / s
+    floor = M * (2 * m) ** d * 2 * 8 / 128.0
+    out = {"resource": "L1/shared-memory data pipe (128-byte wavefronts)", "kernel": stage,
+           "peak_wavefronts_per_s": peak, "tap_floor_wavefronts": floor,
+           "tap_floor_frac": floor / (ms * 1e-3) / peak}
+    w = profiled_value(stage, wl["name"], "shared_wavefronts")
+    if w is not None:
+        out.update({"wavefronts_per_launch": w, "achieved_wavefronts_per_s": w / (ms * 1e-3),
+                    "frac": w / (ms * 1e-3) / peak})
+    return out
+
+
+POLY_DEG = {False: {1: 11, 2: 10, 3: 9}, True: {1: 18, 2: 18, 3: 16, 4: 16, 5: 15}}
+
+
+def alu_roofline(d, m, fp64, M, stages, clk):
+    """B and B^H against the FMA rate: per node, d 2m window values by Horner (degree DEG FMAs
+    each) and (2m)^d taps of 2 FMAs (complex value times real weight); an FMA is 2 flops. Peak:
+    152 SMs x 128 FP32 lanes x 2 flops x clock; FP64 at 1/64 of that (GB300)."""
+    deg = POLY_DEG[fp64].get(m, 14 if fp64 else 8)
+    flops = 2.0 * (d * 2 * m * deg + 2 * (2 * m) ** d) * M
+    peak = NUM_SMS * 128 * 2 * _clock_ghz(clk) * 1e9 / (64.0 if fp64 else 1.0)
+    out = {"flops_per_node": flops / M, "peak_tflops": peak / 1e12}
+    for st in ("interp", "spread"):
+        if st in stages:
+            t = stages[st]["ms_per_launch"] * 1e-3
+            out[st] = {"tflops": flops / t / 1e12, "frac": flops / t / peak}
+    return out
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
 
@@ -443,6 +508,34 @@ def ours(args):
                 "traffic": profiled_traffic(dom, wl["name"]),
                 "peak_kind": peak_kind}
 
+    # the two further roofline views of the spreading kernel and of the window arithmetic
+    onchip = onchip_roofline(dom, wl, M, args.m, kernel_stages[dom]["ms_per_launch"], clk)
+    alu = {"f32": alu_roofline(d, args.m, False, M, kernel_stages, clk)}
+
+    # cuFFT as a timed comparison for step F only: the full (unpruned) forward 2-D/3-D FFT of
+    # the oversampled grid, complex64, torch.fft (cuFFT), no deconvolution or zero padding
+    cufft = None
+    try:
+        z = torch.randn(tuple(wl["n"]), dtype=torch.complex64, device=dev)
+        dims = tuple(range(d))
+        for _ in range(5):
+            torch.fft.fftn(z, dim=dims)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 50
+        a0.record()
+        for _ in range(reps):
+            torch.fft.fftn(z, dim=dims)
+        a1.record()
+        torch.cuda.synchronize()
+        cufft = {"cufft_fftn_us": a0.elapsed_time(a1) / reps * 1e3,
+                 "ours_fft_forward_us": stages["fft_forward"]["ms_per_launch"] * 1e3,
+                 "ours_fft_adjoint_us": stages["fft_adjoint"]["ms_per_launch"] * 1e3,
+                 "note": "cuFFT: full n-point FFT of the grid (torch.fft.fftn, complex64); ours: "
+                         "pruned passes with D (or D^H) and zero padding (or cropping) fused"}
+        del z
+    except Exception as exc:  # the comparison is optional context
+        cufft = {"unavailable": str(exc)[:120]}
+
     # end to end through the host-buffer entry points (pinned host memory)
     pin_fh = torch.tensor(wl["fhat"].astype(np.complex64)).pin_memory()
     pin_f = torch.tensor(wl["f"].astype(np.complex64)).pin_memory()
@@ -484,6 +577,19 @@ def ours(args):
                        "nodes_per_s": M * kv / ((sum(fw) + sum(ad)) * 1e-3),
                        "fwd_nodes_per_s": M * kv / (sum(fw) * 1e-3),
                        "adj_nodes_per_s": M * kv / (sum(ad) * 1e-3)}
+                if dt_t == torch.float64 and mm == args.m:
+                    # FP64 window and tap arithmetic against the FP64 FMA rate
+                    pv.set_nodes(xv)
+                    Lv = _lib.lib()
+                    Lv.nfft_profile(pv._h, 1)
+                    run_variant(pv, fhv, fv, 5, flush, torch)
+                    msv = (ctypes.c_double * 7)()
+                    cv = (ctypes.c_int64 * 7)()
+                    Lv.nfft_profile_read(pv._h, msv, cv, 7)
+                    Lv.nfft_profile(pv._h, 0)
+                    st64 = {nm: {"ms_per_launch": msv[i] / cv[i]}
+                            for i, nm in enumerate(_lib.STAGES) if cv[i]}
+                    alu["f64"] = alu_roofline(d, mm, True, M, st64, clk)
                 if not args.no_parity:
                     ef, ea = parity(wv, yv.cpu().numpy(), hv.cpu().numpy(), mm, pv.n)
                     ent.update({"fwd_rel_l2_vs_oracle_nfft": ef, "adj_rel_l2_vs_oracle_nfft": ea})
@@ -507,11 +613,15 @@ def ours(args):
                        "m": args.m, "M": M, "precision": "FP32 data, FP64 phihat and offsets",
                        "l2": "flushed (256 MiB write) between timed steps, outside the events",
                        "parallelism": f"{world} independent replica(s)"},
+            "ms_per_step_median": statistics.median([a + b for a, b in zip(fwd, adj)]),
             "fwd_nodes_per_s": M * args.steps / (sum(fwd) * 1e-3),
             "adj_nodes_per_s": M * args.steps / (sum(adj) * 1e-3),
             "set_nodes_ms": set_nodes_ms,
             "errors": errors,
             "roofline": roofline,
+            "onchip": onchip,
+            "alu": alu,
+            "fft_vs_cufft": cufft,
             "stages": stages,
             "variants": variants,
             "cpu_baseline": cpu,

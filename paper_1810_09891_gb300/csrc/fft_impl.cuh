@@ -362,6 +362,9 @@ template <typename C, int LOGR, bool INV> __device__ __forceinline__ void dft_re
 // per 16, which keeps the stride-8 writes of the first stages free of bank conflicts.
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
+constexpr int kFftLogR = 3;  // largest stage radix 2^kFftLogR (radix 4 measured slower)
+constexpr int kFftR = 1 << kFftLogR;
+
 struct LineIO {
     int Nt, half, pad_mode;
     long long es;
@@ -422,10 +425,10 @@ __device__ __forceinline__ void r8_stage(const typename Cplx<T>::type *src,
 {
     using C = typename Cplx<T>::type;
     constexpr int L = 1 << LOGL;
-    constexpr int TL = L / 8;
-    constexpr int LOGRS = (LOGL - LOGNS) >= 3 ? 3 : (LOGL - LOGNS);
+    constexpr int TL = L / kFftR;
+    constexpr int LOGRS = (LOGL - LOGNS) >= kFftLogR ? kFftLogR : (LOGL - LOGNS);
     constexpr int RS = 1 << LOGRS;
-    constexpr int K = 8 / RS;
+    constexpr int K = kFftR / RS;
     constexpr int NS = 1 << LOGNS;
     constexpr bool FIRST = LOGNS == 0;
     constexpr bool LAST = LOGNS + LOGRS == LOGL;
@@ -472,7 +475,7 @@ __global__ void __launch_bounds__(FftMaxThreads<T>::value)
 {
     using C = typename Cplx<T>::type;
     constexpr int L = 1 << LOGL;
-    constexpr int TL = L / 8;
+    constexpr int TL = L / kFftR;
     constexpr int BUF = L + L / 16;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *S = reinterpret_cast<C *>(smem_raw);
@@ -525,7 +528,7 @@ cudaError_t launch_fftr(const typename Cplx<T>::type *in, typename Cplx<T>::type
 {
     using C = typename Cplx<T>::type;
     constexpr int L = 1 << LOGL;
-    constexpr int TL = L / 8;
+    constexpr int TL = L / kFftR;
     const int64_t lines = outer * inner;
     const int64_t min_ctas = 2 * (int64_t)num_sms();
     int P = inner > 1 ? (int)(32 / sizeof(C)) : 1;

@@ -288,14 +288,14 @@ void layout_workspace(gbnfft_plan *p)
 }
 
 // Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 8 x 16,
-// 3-D 8 x 8 x 8), clipped to n_t; nodes per spreading work item: the requested number, else 128
+// 3-D 8 x 8 x 16), clipped to n_t; nodes per spreading work item: the requested number, else 128
 // for 2-D FP32 and 1024 otherwise (the fastest choices measured with the default spreading forms
 // on a radial trajectory, whose bins hold very different node counts). Recomputes the bin
 // counts and the workspace layout.
 void setup_bins(gbnfft_plan *p)
 {
     Geom &g = p->geom;
-    const int64_t bin_default[3][3] = {{1024, 0, 0}, {8, 16, 0}, {8, 8, 8}};
+    const int64_t bin_default[3][3] = {{1024, 0, 0}, {8, 16, 0}, {8, 8, 16}};
     int64_t nbins = 1;
     for (int t = 0; t < kMaxDim; t++) {
         if (t >= p->d) {
