@@ -20,6 +20,13 @@ import torch
 
 from .nfft import Plan
 
+
+def _prod(v) -> int:
+    r = 1
+    for x in v:
+        r *= int(x)
+    return r
+
 # Candidate options per dimension: (spread_method, bins, nodes per spreading work item)
 CANDIDATES = {
     1: [(s, (b,), w) for s in ("warp_private", "warp_atomic") for b in (256, 1024, 4096)
@@ -111,15 +118,43 @@ class TuningCache:
 
 
 class PlanBatch:
-    """A batch of independent NFFT problems (uneven N and M) on one device."""
+    """A batch of independent NFFT problems (uneven N and M) on one device.
 
-    def __init__(self, specs, dtype=torch.float32, device=None):
+    The plans run on ``streams`` side streams, forked from and joined back into the caller's
+    stream, so that small problems execute concurrently (in a captured graph they become
+    parallel branches). Plans are assigned to streams largest first, each to the stream with
+    the least work so far (work ~ M + |I_n|)."""
+
+    def __init__(self, specs, dtype=torch.float32, device=None, streams: int = 8):
         """specs: iterable of dicts with keys N, M and optionally n, m (default 4)."""
+        specs = list(specs)
         self.plans = [Plan(s["N"], s["M"], n=s.get("n"), m=s.get("m", 4), dtype=dtype,
                            device=device) for s in specs]
         self.device = self.plans[0].device if self.plans else device
         self.dtype = dtype
         self.graph = None
+        k = max(1, min(int(streams), len(self.plans)))
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(k)]
+        load = [0.0] * k
+        self.lane = [0] * len(self.plans)
+        work = [p.M + _prod(p.n) for p in self.plans]
+        for i in sorted(range(len(self.plans)), key=lambda i: -work[i]):
+            j = min(range(k), key=lambda j: load[j])
+            self.lane[i] = j
+            load[j] += work[i]
+
+    def _each(self, fn, args) -> list:
+        """fn(plan, arg) for every plan on its side stream; the caller's stream waits for all."""
+        main = torch.cuda.current_stream(self.device)
+        for s in self.streams:
+            s.wait_stream(main)
+        out = [None] * len(self.plans)
+        for i, (p, a) in enumerate(zip(self.plans, args)):
+            with torch.cuda.stream(self.streams[self.lane[i]]):
+                out[i] = fn(p, a)
+        for s in self.streams:
+            main.wait_stream(s)
+        return out
 
     def __len__(self):
         return len(self.plans)
@@ -145,10 +180,10 @@ class PlanBatch:
         return out
 
     def trafo(self, fhats) -> list:
-        return [p.trafo(fh) for p, fh in zip(self.plans, fhats)]
+        return self._each(lambda p, fh: p.trafo(fh), fhats)
 
     def adjoint(self, fs) -> list:
-        return [p.adjoint(f) for p, f in zip(self.plans, fs)]
+        return self._each(lambda p, f: p.adjoint(f), fs)
 
     def capture(self, fhats, fs) -> None:
         """Record forward(fhats) and adjoint(fs) of the whole batch into one CUDA graph. The
