@@ -313,8 +313,24 @@ void setup_bins(gbnfft_plan *p)
             if (bs > cap) bs = cap;
         }
         g.bs[t] = (int)bs;
-        g.bslog[t] = ilog2(bs);
-        g.nb[t] = (int)((p->n[t] + bs - 1) / bs);
+    }
+    // default bins shrink (largest first) until one tile with its 2m halo fits in shared memory
+    // beside the window tables (large m in FP64 3-D)
+    const size_t tile_limit = 200 * 1024;
+    for (;;) {
+        size_t cells = 1;
+        int big = -1;
+        for (int t = 0; t < p->d; t++) {
+            cells *= size_t(g.bs[t] + 2 * p->m);
+            if (p->bin_req[t] <= 0 && g.bs[t] > 1 && (big < 0 || g.bs[t] > g.bs[big])) big = t;
+        }
+        if (cells * p->csize <= tile_limit || big < 0) break;
+        g.bs[big] /= 2;
+    }
+    for (int t = 0; t < kMaxDim; t++) {
+        if (t >= p->d) continue;
+        g.bslog[t] = ilog2(g.bs[t]);
+        g.nb[t] = (int)((p->n[t] + g.bs[t] - 1) / g.bs[t]);
         nbins *= g.nb[t];
     }
     p->nbins = (int)nbins;

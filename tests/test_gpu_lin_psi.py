@@ -114,3 +114,19 @@ def test_table_error_converges_on_gpu():
         errs.append(oracle.error_E2(exact, plan.trafo(to_dev(fh, torch.float64)).cpu().numpy()))
     for a, b in zip(errs, errs[1:]):
         assert 3.0 <= a / b <= 5.0, errs
+
+
+@pytest.mark.parametrize("interp", ["thread", "warp", "tile"])
+@pytest.mark.parametrize("d", [2, 3])
+def test_table_window_interp_forms(interp, d):
+    N = {2: (40, 36), 3: (12, 10, 8)}[d]
+    n = {2: (80, 72), 3: (24, 20, 16)}[d]
+    m, K, M = 4, 64, 2500
+    x = W.uniform_nodes(M, d, 1250 + d)
+    fh = W.gaussian_fhat(N, 1251)
+    plan = Plan(N, M, n=n, m=m, dtype=torch.float64, device=DEV)
+    plan.set_option("window_table", K)
+    plan.set_option("interp_method", interp)
+    plan.set_nodes(to_dev(x, torch.float64))
+    out = plan.trafo(to_dev(fh, torch.float64)).cpu().numpy()
+    assert rel_l2(out, oracle.nfft(x, fh, n=n, m=m, lin_psi=K)) <= 1e-12
