@@ -202,11 +202,12 @@ POLY_DEG = {False: {1: 11, 2: 10, 3: 9}, True: {1: 18, 2: 18, 3: 16, 4: 16, 5: 1
 
 
 def alu_roofline(d, m, fp64, M, stages, clk):
-    """B and B^H against the FMA rate: per node, d 2m window values by Horner (degree DEG FMAs
-    each) and (2m)^d taps of 2 FMAs (complex value times real weight); an FMA is 2 flops. Peak:
-    152 SMs x 128 FP32 lanes x 2 flops x clock; FP64 at 1/64 of that (GB300)."""
+    """B and B^H against the FMA rate: per node, the 2m window values of each of the d axes as m
+    mirrored pairs (one even/odd Horner evaluation of degree DEG, DEG + 2 FMAs per pair) and
+    (2m)^d taps of 2 FMAs (complex value times real weight); an FMA is 2 flops. Peak: 152 SMs x
+    128 FP32 lanes x 2 flops x clock; FP64 at 1/64 of that (GB300)."""
     deg = POLY_DEG[fp64].get(m, 14 if fp64 else 8)
-    flops = 2.0 * (d * 2 * m * deg + 2 * (2 * m) ** d) * M
+    flops = 2.0 * (d * m * (deg + 2) + 2 * (2 * m) ** d) * M
     peak = NUM_SMS * 128 * 2 * _clock_ghz(clk) * 1e9 / (64.0 if fp64 else 1.0)
     out = {"flops_per_node": flops / M, "peak_tflops": peak / 1e12}
     for st in ("interp", "spread"):

@@ -110,15 +110,16 @@ interp_node(const Geom &g, const T *__restrict__ tab, const typename Cplx<T>::ty
             }
         }
     } else if (D == 2) {
-        T w1[NT];
+        T w1[NT], w0a[NT];
         eval_taps<T, MM, START, MODE>(g, tab + AS, 1, frac[1], w1);
+        eval_taps<T, MM, START, MODE>(g, tab, 0, frac[0], w0a);
         const int n0 = g.n[0], n1 = g.n[1];
         const int s1 = base[1] - MM + START, odd = s1 & 1;
         float wv[NW];
         if constexpr (PAIRS) pair_weights<MM, START>(w1, odd, wv);
 #pragma unroll
         for (int i0 = START; i0 < NT; i0++) {
-            const T w0 = eval_tap<T, MM, MODE>(g, tab, 0, i0, frac[0]);
+            const T w0 = w0a[i0];
             const C *row = grid + (size_t)wrapn(base[0] - MM + i0, n0) * n1;
             C in;
             if constexpr (PAIRS) {

@@ -535,6 +535,73 @@ __device__ __forceinline__ void spread_octet_node(typename Cplx<T>::type *tile, 
     constexpr int NT = 2 * MM + 1;
     constexpr int PER = NT - START;
     const T z0 = (T)2 * frac0 - (T)1, z1 = (T)2 * frac1 - (T)1;
+    if (START == 1 && K == 0) {
+        // Mirrored taps (see window_taps): pair p < m holds column taps p + 1 and 2m - p, pair
+        // m + q holds row taps q + 1 and 2m - q, each as (E + zO, E - zO) from one even/odd
+        // Horner evaluation; lane l evaluates pairs l and l + 8.
+        constexpr int KE = DEG - (DEG & 1), KO = DEG - 1 + (DEG & 1), NP = 2 * MM;
+        T pa = (T)0, ma = (T)0, pb = (T)0, mb = (T)0;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int pp = l + 8 * h;
+            if ((h == 0 || NP > 8) && pp < NP) {
+                const bool colp = pp < MM;
+                const T *cc = colp ? cb : ca;
+                const T z = colp ? z1 : z0;
+                const int i = (colp ? pp : pp - MM) + 1;
+                const T u = z * z;
+                T e = cc[KE * kPolyTaps + i - 1], o = cc[KO * kPolyTaps + i - 1];
+#pragma unroll
+                for (int k = KE - 2; k >= 0; k -= 2) e = fma(e, u, cc[k * kPolyTaps + i - 1]);
+#pragma unroll
+                for (int k = KO - 2; k >= 1; k -= 2) o = fma(o, u, cc[k * kPolyTaps + i - 1]);
+                if (h == 0) {
+                    pa = fma(z, o, e);
+                    ma = fma(-z, o, e);
+                } else {
+                    pb = fma(z, o, e);
+                    mb = fma(-z, o, e);
+                }
+            }
+        }
+        // column weights of this lane: columns a = l and l + 8 hold taps a + 1
+        T w1[2] = {(T)0, (T)0};
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            if (h == 1 && PER <= 8) break;
+            const int t = l + 8 * h + 1;
+            const int pp = t <= MM ? t - 1 : 2 * MM - t;  // column pair of tap t (or its mirror)
+            const int src = pp & 7;
+            const T vpa = __shfl_sync(mask, pa, src, 8), vma = __shfl_sync(mask, ma, src, 8);
+            const T vpb = NP > 8 ? __shfl_sync(mask, pb, src, 8) : (T)0;
+            const T vmb = NP > 8 ? __shfl_sync(mask, mb, src, 8) : (T)0;
+            const T plus = pp < 8 ? vpa : vpb, minus = pp < 8 ? vma : vmb;
+            w1[h] = t <= PER ? (t <= MM ? plus : minus) : (T)0;
+        }
+        const T ar = w1[0] * v.x, ai = w1[0] * v.y, br = w1[1] * v.x, bi = w1[1] * v.y;
+        C *col = tile + off + l;
+#pragma unroll
+        for (int a0 = 0; a0 < PER; a0++) {
+            const int t = a0 + 1;                                  // row tap
+            const int pp = t <= MM ? MM + t - 1 : 3 * MM - t;      // its row pair
+            const T var = pp < 8 ? (t <= MM ? pa : ma) : (t <= MM ? pb : mb);
+            const T w0 = __shfl_sync(mask, var, pp & 7, 8);
+            C *row = col + a0 * st0;
+            if (l < PER) {
+                C c = row[0];
+                c.x += w0 * ar;
+                c.y += w0 * ai;
+                row[0] = c;
+            }
+            if (PER > 8 && l + 8 < PER) {
+                C c = row[8];
+                c.x += w0 * br;
+                c.y += w0 * bi;
+                row[8] = c;
+            }
+        }
+        return;
+    }
     // this lane's columns a1 = l and l + 8, and the row weights a0 = l, l + 8 it broadcasts
     T w1a = (T)0, w1b = (T)0, w0a = (T)0, w0b = (T)0;
     if (l < PER) {

@@ -25,18 +25,40 @@ template <typename T, int MM> struct PolyDeg {
 };
 
 // All taps of one axis: w[i] = psibar(frac + m - i) for i = START..2m. c is the axis' table
-// (shared or global memory); w[0] (START = 0) is the edge tap, nonzero only when frac == 0.
+// (shared, constant or global memory); w[0] (START = 0) is the edge tap, nonzero only when
+// frac == 0. Taps i and 2m + 1 - i mirror each other: psibar is even, so their functions of z
+// are f_i(z) and f_i(-z), and the Chebyshev interpolants, fitted at nodes symmetric about 0,
+// satisfy P_(2m+1-i)(z) = P_i(-z). With P_i(z) = E_i(z^2) + z O_i(z^2) (the even- and
+// odd-degree coefficients) one pair costs about one Horner evaluation:
+// w[i] = E + z O, w[2m + 1 - i] = E - z O.
 template <typename T, int MM, int START>
 __device__ __forceinline__ void window_taps(const T *__restrict__ c, T frac, T edge_w, T *w)
 {
     constexpr int DEG = PolyDeg<T, MM>::value;
+    constexpr int KE = DEG - (DEG & 1);        // highest even degree
+    constexpr int KO = DEG - 1 + (DEG & 1);    // highest odd degree
     const T z = (T)2 * frac - (T)1;
+    const T u = z * z;
+    T e[MM], o[MM];
 #pragma unroll
-    for (int i = 1; i <= 2 * MM; i++) w[i] = c[DEG * kPolyTaps + i - 1];
+    for (int i = 1; i <= MM; i++) {
+        e[i - 1] = c[KE * kPolyTaps + i - 1];
+        o[i - 1] = c[KO * kPolyTaps + i - 1];
+    }
 #pragma unroll
-    for (int k = DEG - 1; k >= 0; k--) {
+    for (int k = KE - 2; k >= 0; k -= 2) {
 #pragma unroll
-        for (int i = 1; i <= 2 * MM; i++) w[i] = fma(w[i], z, c[k * kPolyTaps + i - 1]);
+        for (int i = 1; i <= MM; i++) e[i - 1] = fma(e[i - 1], u, c[k * kPolyTaps + i - 1]);
+    }
+#pragma unroll
+    for (int k = KO - 2; k >= 1; k -= 2) {
+#pragma unroll
+        for (int i = 1; i <= MM; i++) o[i - 1] = fma(o[i - 1], u, c[k * kPolyTaps + i - 1]);
+    }
+#pragma unroll
+    for (int i = 1; i <= MM; i++) {
+        w[i] = fma(z, o[i - 1], e[i - 1]);
+        w[2 * MM + 1 - i] = fma(-z, o[i - 1], e[i - 1]);
     }
     if (START == 0) w[0] = frac == (T)0 ? edge_w : (T)0;
 }

@@ -117,3 +117,36 @@ def test_node_gradient_against_ndft_derivative():
     gx = plan.grad_x(to_dev(fh, torch.float64), to_dev(w, torch.float64)).cpu().numpy()
     ref = np.real(np.conj(w)[:, None] * oracle.ndft_grad(x, fh))
     assert rel_l2(gx, ref) <= 1e-10
+
+
+def test_autograd_3d_clusters_finite_difference():
+    """The 3-D clustered node distribution (half uniform, half in 8 Gaussian clusters): dL/dx by
+    autograd against central differences of the CUDA forward in FP64, and dL/dfhat against the
+    adjoint, for L = Re(<w, NFFT(fhat; x)>) (N = 16^3, m = 4)."""
+    N, m, M = (16, 16, 16), 4, 3000
+    n = oracle.default_n(N)
+    x = W.clustered_nodes(M, 3, seed_offset=515)
+    fh = W.gaussian_fhat(N, 516)
+    w = W.gaussian_values(M, 517)
+    plan = Plan(N, M, m=m, dtype=torch.float64, device=DEV)
+    xt = to_dev(x, torch.float64).requires_grad_(True)
+    fht = to_dev(fh, torch.float64).requires_grad_(True)
+    wt = to_dev(w, torch.float64)
+    torch.real(torch.vdot(wt, nfft(fht, xt, plan))).backward()
+    gx = xt.grad.cpu().numpy()
+    h = 1e-7
+    with torch.no_grad():
+        for t in range(3):
+            e = np.zeros(3)
+            e[t] = h
+            fp = nfft(fht, to_dev(x + e, torch.float64), plan).cpu().numpy()
+            fm = nfft(fht, to_dev(x - e, torch.float64), plan).cpu().numpy()
+            fd = np.real(np.conj(w) * (fp - fm)) / (2 * h)
+            ok = np.ones(M, dtype=bool)
+            for y in (x + e, x - e):
+                ok &= np.ceil(n[t] * y[:, t] - m) == np.ceil(n[t] * x[:, t] - m)
+                ok &= np.floor(n[t] * y[:, t] + m) == np.floor(n[t] * x[:, t] + m)
+            assert ok.sum() > M // 2
+            assert np.max(np.abs(gx[ok, t] - fd[ok])) <= 1e-6 * np.max(np.abs(gx[:, t]))
+    plan.set_nodes(to_dev(x, torch.float64))
+    assert rel_l2(fht.grad.cpu().numpy(), plan.adjoint(wt).cpu().numpy()) <= 1e-14
