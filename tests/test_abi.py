@@ -79,3 +79,21 @@ def test_null_arguments(lib):
     assert lib.nfft_adjoint(None, None, None) == 1
     assert lib.nfft_set_nodes(None, None) == 1
     assert lib.nfft_status(None) == 1
+
+
+def test_plain_c_consumer_compiles_and_links(tmp_path):
+    """include/gbnfft.h is plain C: a C11 program using it compiles and links against the
+    library (running it needs a GPU: tests/test_gpu_c_consumer.py)."""
+    import shutil
+    import subprocess
+    from paper_1810_09891_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None or not os.path.exists(_lib.LIB_PATH):
+        pytest.skip("no C compiler or library not built")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = str(tmp_path / "abi_consumer")
+    subprocess.run([cc, "-O2", "-std=c11", "-Wall", "-Werror",
+                    os.path.join(root, "tests", "c", "abi_consumer.c"),
+                    "-I", os.path.join(root, "include"), _lib.LIB_PATH, "-lm", "-o", exe],
+                   check=True)
+    assert os.path.exists(exe)
