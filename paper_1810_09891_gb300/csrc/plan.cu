@@ -287,8 +287,8 @@ void layout_workspace(gbnfft_plan *p)
     p->ws_need = align_up(off, 256);
 }
 
-// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 8 x 16,
-// 3-D 8 x 8 x 16), clipped to n_t; nodes per spreading work item: the requested number, else 128
+// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 4 x 16 in FP32
+// and 8 x 16 in FP64, 3-D 8 x 8 x 16), clipped to n_t; nodes per spreading work item: the requested number, else 128
 // for 2-D FP32 and 1024 otherwise (the fastest choices measured with the default spreading forms
 // on a radial trajectory, whose bins hold very different node counts). Recomputes the bin
 // counts and the workspace layout.
@@ -305,6 +305,7 @@ void setup_bins(gbnfft_plan *p)
             continue;
         }
         int64_t bs = p->bin_req[t] > 0 ? p->bin_req[t] : bin_default[p->d - 1][t];
+        if (p->bin_req[t] <= 0 && p->d == 2 && p->dtype == NFFT_FP32 && t == 0) bs = 4;
         if (is_pow2(p->n[t])) {
             if (bs > p->n[t]) bs = p->n[t];  // one bin covers the axis
         } else {
