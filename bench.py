@@ -668,7 +668,8 @@ def ncu_step(args):
 def batched(args):
     """64 independent 2-D problems (N_i per axis from {64, ..., 512}, M_i log-uniform in
     [1e4, 1e6], uniform nodes, FP32, m = 4): forward + adjoint of the whole batch captured in one
-    CUDA graph; value = sum of M_i per step / step time."""
+    CUDA graph; value = sum of M_i per step / step time. ``with_backward`` times a second graph
+    that also holds the backward of the forward transform."""
     import torch
 
     from paper_1810_09891_gb300 import workloads as W
@@ -683,22 +684,32 @@ def batched(args):
            for i, s in enumerate(specs)]
     fs = [torch.tensor(W.gaussian_values(s["M"], 3000 + i).astype(np.complex64), device=dev)
           for i, s in enumerate(specs)]
+    gs = [torch.tensor(W.gaussian_values(s["M"], 4000 + i).astype(np.complex64), device=dev)
+          for i, s in enumerate(specs)]
     b.set_nodes(xs)
     tuned = b.tune(fhs, fs) if args.tune else None
-    b.capture(fhs, fs)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    for _ in range(max(3, args.warmup)):
-        b.replay()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for a, c in ev:
-        flush.zero_()
-        a.record()
-        b.replay()
-        c.record()
-    torch.cuda.synchronize()
-    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+
+    def timed_replays():
+        for _ in range(max(3, args.warmup)):
+            b.replay()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for a, c in ev:
+            flush.zero_()
+            a.record()
+            b.replay()
+            c.record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(c) for a, c in ev)
+
+    b.capture(fhs, fs)
+    total_ms = timed_replays()
+    # the same step plus the backward of the forward transform (grad fhat and grad x for an
+    # output gradient per problem) in one graph
+    b.capture(fhs, fs, grad_fs=gs)
+    bwd_ms = timed_replays()
     nodes = sum(s["M"] for s in specs)
     line = {"metric": METRIC, "value": nodes * args.steps / (total_ms * 1e-3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -708,6 +719,10 @@ def batched(args):
                        "nodes_per_step": nodes, "m": 4, "graph": "one CUDA graph per step",
                        "tuned": bool(args.tune),
                        "l2": "flushed (256 MiB write) between timed steps"},
+            "with_backward": {"ms_per_step": bwd_ms / args.steps,
+                              "nodes_per_s": nodes * args.steps / (bwd_ms * 1e-3),
+                              "step": "forward + adjoint + backward of the forward "
+                                      "(adjoint for grad fhat, node-gradient kernel for grad x)"},
             "tuning": [{"N": list(s["N"]), "M": s["M"], "spread": t["spread_method"],
                         "bins": t["bins"]} for s, t in zip(specs, tuned)] if tuned else None}
     print(json.dumps(line))

@@ -185,22 +185,44 @@ class PlanBatch:
     def adjoint(self, fs) -> list:
         return self._each(lambda p, f: p.adjoint(f), fs)
 
-    def capture(self, fhats, fs) -> None:
+    def backward(self, grad_fs, fhats, want_fhat: bool = True, want_x: bool = True) -> tuple:
+        """Backward of the batched forward transform f_i = A_i fhat_i for output gradients
+        grad_f_i: per plan, grad fhat_i = A_i^H grad_f_i (the adjoint kernels) and grad x_i =
+        Re(conj(grad_f_i) d(A_i fhat_i)/dx) (the node-gradient kernel), both on the plan's side
+        stream. Returns (grad_fhats, grad_xs); a list not asked for is all None."""
+        def one(p, a):
+            return (p.adjoint(a[0]) if want_fhat else None,
+                    p.grad_x(a[1], a[0]) if want_x else None)
+        out = self._each(one, list(zip(grad_fs, fhats)))
+        return [o[0] for o in out], [o[1] for o in out]
+
+    def capture(self, fhats, fs, grad_fs=None) -> None:
         """Record forward(fhats) and adjoint(fs) of the whole batch into one CUDA graph. The
         graph reads the given input tensors and writes ``self.out_f`` / ``self.out_h``; copy new
-        inputs into ``fhats`` / ``fs`` before each ``replay``. Nodes must be set beforehand."""
+        inputs into ``fhats`` / ``fs`` before each ``replay``. Nodes must be set beforehand.
+        With ``grad_fs`` the graph also holds the backward of the forward transform for those
+        output gradients (read from ``self.in_grad_f``), written to ``self.out_grad_fhat`` and
+        ``self.out_grad_x``."""
         self.in_fhat = list(fhats)
         self.in_f = list(fs)
+        self.in_grad_f = list(grad_fs) if grad_fs is not None else None
+
+        def step():
+            out = (self.trafo(self.in_fhat), self.adjoint(self.in_f))
+            if self.in_grad_f is not None:
+                out += self.backward(self.in_grad_f, self.in_fhat)
+            return out
+
         s = torch.cuda.Stream(self.device)
         s.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.stream(s):  # warm-up outside the capture (kernel attributes, caches)
-            self.trafo(self.in_fhat)
-            self.adjoint(self.in_f)
+            step()
         torch.cuda.current_stream(self.device).wait_stream(s)
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self.out_f = self.trafo(self.in_fhat)
-            self.out_h = self.adjoint(self.in_f)
+            out = step()
+        self.out_f, self.out_h = out[0], out[1]
+        self.out_grad_fhat, self.out_grad_x = (out[2], out[3]) if len(out) > 2 else (None, None)
         self.graph = g
 
     def replay(self):
@@ -208,6 +230,45 @@ class PlanBatch:
             raise RuntimeError("capture() first")
         self.graph.replay()
         return self.out_f, self.out_h
+
+
+class _BatchNFFTFunction(torch.autograd.Function):
+    """[f_i] = [A_i fhat_i] for every plan of a PlanBatch, differentiable in every fhat_i and
+    every node set x_i; forward and backward run the plans on the batch's side streams."""
+
+    @staticmethod
+    def forward(ctx, batch, *args):
+        k = len(batch.plans)
+        fhats, xs = args[:k], args[k:]
+        for p, x in zip(batch.plans, xs):
+            p.ensure_nodes(x)
+        outs = batch.trafo(fhats)
+        ctx.save_for_backward(*fhats, *xs)
+        ctx.batch = batch
+        return tuple(outs)
+
+    @staticmethod
+    def backward(ctx, *grad_fs):
+        batch = ctx.batch
+        k = len(batch.plans)
+        saved = ctx.saved_tensors
+        fhats, xs = saved[:k], saved[k:]
+        for p, x in zip(batch.plans, xs):
+            p.ensure_nodes(x)
+        gs = [g.contiguous() if g is not None else
+              torch.zeros(p.M, dtype=p.cdtype, device=p.device)
+              for p, g in zip(batch.plans, grad_fs)]
+        g_fhat, g_x = batch.backward(gs, fhats, want_fhat=any(ctx.needs_input_grad[1:1 + k]),
+                                     want_x=any(ctx.needs_input_grad[1 + k:]))
+        return (None, *g_fhat, *g_x)
+
+
+def batch_nfft(fhats, xs, batch: PlanBatch) -> list:
+    """Differentiable forward NFFT of every problem of ``batch`` (with respect to each fhat_i
+    and each node set x_i); returns the list of f_i."""
+    if len(fhats) != len(batch.plans) or len(xs) != len(batch.plans):
+        raise ValueError("one fhat and one node set per plan")
+    return list(_BatchNFFTFunction.apply(batch, *fhats, *xs))
 
 
 def batched_specs(count: int = 64, seed_offset: int = 40, sizes=(64, 128, 256, 512),

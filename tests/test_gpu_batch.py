@@ -89,3 +89,79 @@ def test_batched_workload_specs():
     assert len(specs) == 64
     assert all(s["N"][t] in (64, 128, 256, 512) for s in specs for t in range(2))
     assert all(10 ** 4 <= s["M"] <= 10 ** 6 for s in specs)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_batch_backward_matches_oracle_and_graph_replay(dtype):
+    """Backward of the batched forward transform: grad fhat_i = A_i^H g_i and grad x_i from the
+    node-gradient kernel, per problem against the oracle, eagerly and captured in the graph
+    together with the forward and adjoint."""
+    b = PlanBatch(SPECS, dtype=dtype, device=DEV)
+    xs, fhs, fs = _inputs(SPECS, dtype, 1000)
+    _, _, gs = _inputs(SPECS, dtype, 1300)
+    b.set_nodes([to_dev(x, dtype) for x in xs])
+    fh_t = [to_dev(v, dtype) for v in fhs]
+    f_t = [to_dev(v, dtype) for v in fs]
+    g_t = [to_dev(v, dtype) for v in gs]
+    g_fhat, g_x = b.backward(g_t, fh_t)
+    g_fhat = [t.cpu().numpy() for t in g_fhat]
+    g_x = [t.cpu().numpy() for t in g_x]
+    tol_x = 1e-11 if dtype == torch.float64 else 1e-5
+    for i, s in enumerate(SPECS):
+        n = b.plans[i].n
+        xr, fhr, gr = rounded(xs[i], dtype), rounded(fhs[i], dtype), rounded(gs[i], dtype)
+        assert rel_l2(g_fhat[i], oracle.nfft_adjoint(xr, gr, s["N"], n=n, m=4)) <= TOL[dtype]
+        assert rel_l2(g_x[i], oracle.nfft_grad_x(xr, fhr, gr, n=n, m=4)) <= tol_x
+    b.capture(fh_t, f_t, grad_fs=g_t)
+    b.replay()
+    torch.cuda.synchronize()
+    tol = 1e-13 if dtype == torch.float64 else 1e-6
+    for i in range(len(SPECS)):
+        assert rel_l2(b.out_grad_fhat[i].cpu().numpy(), g_fhat[i]) <= tol
+        assert rel_l2(b.out_grad_x[i].cpu().numpy(), g_x[i]) <= tol
+
+
+def test_batch_autograd_equals_per_plan_autograd():
+    """batch_nfft through torch.autograd: the gradients of a loss over every problem equal
+    those of the single-plan autograd function, problem by problem (FP64)."""
+    from paper_1810_09891_gb300.batch import batch_nfft
+    from paper_1810_09891_gb300.nfft import nfft
+
+    dtype = torch.float64
+    b = PlanBatch(SPECS, dtype=dtype, device=DEV)
+    xs, fhs, _ = _inputs(SPECS, dtype, 1100)
+    _, _, ws = _inputs(SPECS, dtype, 1200)
+    xt = [to_dev(x, dtype).requires_grad_() for x in xs]
+    fht = [to_dev(v, dtype).requires_grad_() for v in fhs]
+    wt = [to_dev(v, dtype) for v in ws]
+    outs = batch_nfft(fht, xt, b)
+    loss = sum((torch.conj(w) * o).real.sum() for w, o in zip(wt, outs))
+    loss.backward()
+    for i, s in enumerate(SPECS):
+        x1 = to_dev(xs[i], dtype).requires_grad_()
+        f1 = to_dev(fhs[i], dtype).requires_grad_()
+        plan = Plan(s["N"], s["M"], m=4, dtype=dtype, device=DEV)
+        (torch.conj(wt[i]) * nfft(f1, x1, plan)).real.sum().backward()
+        assert rel_l2(outs[i].detach().cpu().numpy(),
+                      nfft(f1.detach(), x1.detach(), plan).cpu().numpy()) <= 1e-14
+        assert rel_l2(fht[i].grad.cpu().numpy(), f1.grad.cpu().numpy()) <= 1e-14
+        assert rel_l2(xt[i].grad.cpu().numpy(), x1.grad.cpu().numpy()) <= 1e-14
+        plan.close()
+
+
+def test_batch_autograd_only_fhat():
+    """Nodes without requires_grad: only the adjoint runs in the backward, grad fhat_i equals
+    the oracle adjoint of the output gradient."""
+    from paper_1810_09891_gb300.batch import batch_nfft
+
+    dtype = torch.float64
+    specs = SPECS[:3]
+    b = PlanBatch(specs, dtype=dtype, device=DEV)
+    xs, fhs, _ = _inputs(specs, dtype, 1400)
+    fht = [to_dev(v, dtype).requires_grad_() for v in fhs]
+    outs = batch_nfft(fht, [to_dev(x, dtype) for x in xs], b)
+    sum(o.abs().square().sum() for o in outs).backward()
+    for i, s in enumerate(specs):
+        f = oracle.nfft(xs[i], fhs[i], n=b.plans[i].n, m=4)
+        ref = 2 * oracle.nfft_adjoint(xs[i], f, s["N"], n=b.plans[i].n, m=4)
+        assert rel_l2(fht[i].grad.cpu().numpy(), ref) <= 1e-12
