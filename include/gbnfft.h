@@ -183,7 +183,11 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           2 one warp per node with shared-memory atomics,
  *                           3 one warp per node with a private tile per warp (no atomics),
  *                           4 (d = 2) eight lanes per node, a private tile per eight lanes,
- *                           5 (d = 2) sixteen lanes per node, a private tile per half-warp.
+ *                           5 (d = 2) sixteen lanes per node, a private tile per half-warp,
+ *                           6 (d = 3) one tile per CTA, its planes along axis 0 owned by the
+ *                           CTA's warps (no atomics, no private copies).
+ *                           A form whose tile does not fit or whose d does not match runs as
+ *                           the nearest form that fits (6 -> 2 -> 1, 4/5 -> 3 -> 2 -> 1).
  *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node (gathers from the grid),
  *                           2 one warp per node, 3 one thread per node gathering from a
  *                           shared-memory tile of the node's bin.

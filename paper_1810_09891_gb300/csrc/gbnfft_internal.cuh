@@ -53,6 +53,7 @@ constexpr int kSpreadWarpAtomic = 2;
 constexpr int kSpreadWarpPrivate = 3;
 constexpr int kSpreadOctet = 4;
 constexpr int kSpreadHalf = 5;
+constexpr int kSpreadPlane = 6;
 
 // Interpolation methods (see interp_impl.cuh).
 constexpr int kInterpAuto = 0;

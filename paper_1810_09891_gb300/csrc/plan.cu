@@ -1072,7 +1072,7 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
     if (!p) return NFFT_EINVAL;
     switch (key) {
     case NFFT_OPT_SPREAD_METHOD:
-        if (value < kSpreadAuto || value > kSpreadHalf) return NFFT_EINVAL;
+        if (value < kSpreadAuto || value > kSpreadPlane) return NFFT_EINVAL;
         p->geom.spread_method = (int)value;
         return NFFT_OK;
     case NFFT_OPT_INTERP_METHOD:

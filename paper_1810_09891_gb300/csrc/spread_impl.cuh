@@ -15,7 +15,8 @@
 //   kSpreadWarpPrivate one warp per node as above, but every warp owns a private tile and adds
 //                  with plain loads and stores (no atomics); the tiles are summed at the flush;
 //   kSpreadOctet / kSpreadHalf (d = 2) eight or sixteen lanes per node, a private tile per
-//                  group of lanes (see below).
+//                  group of lanes (see below);
+//   kSpreadPlane   (d = 3) one tile per CTA whose planes are owned by the warps (see below).
 // Coincident and clustered nodes (a radial trajectory puts every spoke through the origin) make
 // the atomics of the first form collide; the warp forms do not.
 #pragma once
@@ -927,6 +928,228 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
     finish_subproblems(nsub_total);
 }
 
+// ----------------------------------------------------------------------------- plane form (d = 3)
+// One shared tile per CTA, no atomics and no private copies: the eight warps own the tile's
+// planes along axis 0 by residue (warp w adds into the planes a0 with a0 mod 8 = w), and every
+// warp walks every node of the subproblem, adding the taps of the node that fall into its own
+// planes. A node's support spans 2m consecutive planes, so for m = 4 each warp takes exactly one
+// plane (2m x 2m taps, two rounds of its lanes) of every node, and no two warps ever touch the
+// same cell. The window values, which every warp would otherwise evaluate again, are computed
+// once per node when a chunk of nodes is staged (three threads per node, one per axis): the
+// axis-1 and axis-2 values, the axis-0 values times f_j, and the tile offset of the node's first
+// tap. Lanes cover a plane row-major (last axis fastest); the row pitch puts the rows written in
+// one round side by side in the banks.
+constexpr int kPlaneWarps = 8;
+constexpr int kPlaneChunk = 64;  // nodes staged at a time
+
+// Row pitch (cells) of the plane tile: for FP32 with 2m = 8 an access of 16 lanes covers 2 rows
+// of 8 cells, which share a 128-byte wavefront when the pitch is 8 mod 16 cells. FP64 rows of 8
+// cells fill a wavefront by themselves.
+template <typename T> __host__ __device__ inline int plane_pitch(int td2)
+{
+    if (sizeof(T) == 8) return td2;
+    return td2 + ((8 - td2 % 16) + 16) % 16;
+}
+
+// Staged data per node: a packed offset word, NT complex axis-0 terms and 2 NT + 1 reals
+// (axis-1 values, axis-2 values, one pad to an odd stride).
+template <typename T, int MM>
+__host__ __device__ constexpr size_t plane_stage_bytes()
+{
+    return kPlaneChunk * (sizeof(unsigned) + (2 * MM + 1) * sizeof(typename Cplx<T>::type) +
+                          (4 * MM + 3) * sizeof(T)) +
+           16;
+}
+
+// The taps of one node in the planes i0, i0 + 8, ... (< P) of one warp: P x P taps per plane,
+// weight w_0(i0) f_j (staged in ak) times w_1(i1) w_2(i2) (staged in wk).
+template <typename T, int MM, int START>
+__device__ __forceinline__ void plane_taps(typename Cplx<T>::type *first, int i0, int pstride,
+                                           int pitch, const T *wk,
+                                           const typename Cplx<T>::type *ak, int lane)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int NT = 2 * MM + 1;
+    constexpr int P = NT - START;
+    constexpr int TAPS = P * P;
+    constexpr int ITER = (TAPS + 31) / 32;
+    for (; i0 < P; i0 += kPlaneWarps) {
+        const C A = ak[i0 + START];
+        C *row0 = first + i0 * pstride;
+        if constexpr (32 % P == 0) {  // the lane's column is the same in every round
+            const int i2 = lane % P;
+            const T w2 = wk[NT + i2 + START];
+            const T br = w2 * A.x, bi = w2 * A.y;
+#pragma unroll
+            for (int k = 0; k < ITER; k++) {
+                const int i1 = lane / P + k * (32 / P);
+                if (i1 < P) {
+                    const T w1 = wk[i1 + START];
+                    C *p = row0 + i1 * pitch + i2;
+                    C a = *p;
+                    a.x += w1 * br;
+                    a.y += w1 * bi;
+                    *p = a;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < ITER; k++) {
+                const int q = lane + 32 * k;
+                if (q < TAPS) {
+                    const int i1 = q / P, i2 = q - (q / P) * P;
+                    const T w = wk[i1 + START] * wk[NT + i2 + START];
+                    C *p = row0 + i1 * pitch + i2;
+                    C a = *p;
+                    a.x += w * A.x;
+                    a.y += w * A.y;
+                    *p = a;
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int MM, bool LIN>
+__global__ void __launch_bounds__(32 * kPlaneWarps)
+    spread_plane_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
+                        const typename RecOf<T>::type *__restrict__ rec,
+                        const int *__restrict__ perm, const SubProb *__restrict__ subs,
+                        int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    constexpr int NT = 2 * MM + 1;  // tap slots per axis (slot 0 only on a grid point)
+    constexpr int SW = 2 * NT + 1;  // staged reals per node
+    constexpr int MODE = LIN ? 2 : 1;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    static_assert(32 * kPlaneWarps >= 3 * kPlaneChunk, "three staging threads per node");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) T tab[kMaxDim * AS];
+    load_window_tables<T, MM>(tab, g.poly, 3);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int s_ax = tid / kPlaneChunk, s_nd = tid - s_ax * kPlaneChunk;  // staging role
+    const int td0 = g.bs[0] + 2 * MM, td1 = g.bs[1] + 2 * MM, td2 = g.bs[2] + 2 * MM;
+    const int pitch = plane_pitch<T>(td2);
+    const int pstride = td1 * pitch;
+    const int tcells = td0 * pstride;
+    C *tile = reinterpret_cast<C *>(smem_raw);
+    C *st_a = reinterpret_cast<C *>(smem_raw + ((size_t)tcells * sizeof(C) + 15) / 16 * 16);
+    T *st_w = reinterpret_cast<T *>(st_a + kPlaneChunk * NT);
+    unsigned *st_pk = reinterpret_cast<unsigned *>(st_w + kPlaneChunk * SW);
+    {
+        C z;
+        z.x = (T)0;
+        z.y = (T)0;
+        for (int e = tid; e < tcells; e += 32 * kPlaneWarps) tile[e] = z;
+    }
+    const int nsub = nsub_total[0];
+    __shared__ int s_sp;
+    for (int sp = next_subproblem(nsub_total, &s_sp); sp < nsub;
+         sp = next_subproblem(nsub_total, &s_sp)) {
+        const SubProb P = subs[sp];
+        int org[3];
+        {
+            int b = P.bin;
+#pragma unroll
+            for (int t = 2; t >= 0; t--) {
+                org[t] = (b % g.nb[t]) * g.bs[t];
+                b /= g.nb[t];
+            }
+        }
+        // staging: thread (axis s_ax < 3, node s_nd) evaluates one axis of one node
+        Rec r_next;
+        C v_next;
+        if (s_ax < 3 && s_nd < P.count) {
+            r_next = rec[P.start + s_nd];
+            if (s_ax == 0) v_next = f[perm[P.start + s_nd]];
+        }
+        for (int c0 = 0; c0 < P.count; c0 += kPlaneChunk) {
+            const int cnt = min(kPlaneChunk, P.count - c0);
+            if (s_ax < 3 && s_nd < cnt) {
+                int cell = r_next.cell;
+                const int loc2 = (cell & g.cmask[2]) - org[2];
+                cell >>= g.cbits[2];
+                const int loc1 = (cell & g.cmask[1]) - org[1];
+                cell >>= g.cbits[1];
+                const int loc0 = (cell & g.cmask[0]) - org[0];
+                const T fr0 = r_next.fr[0], fr1 = r_next.fr[1], fr2 = r_next.fr[2];
+                const int start = (fr0 == (T)0 || fr1 == (T)0 || fr2 == (T)0) ? 0 : 1;
+                const T frt = s_ax == 0 ? fr0 : (s_ax == 1 ? fr1 : fr2);
+                T w[NT];
+                if (start) {
+                    eval_taps<T, MM, 1, MODE>(g, tab + s_ax * AS, s_ax, frt, w);
+                    w[0] = (T)0;
+                } else {
+                    eval_taps<T, MM, 0, MODE>(g, tab + s_ax * AS, s_ax, frt, w);
+                }
+                if (s_ax > 0) {
+                    T *dst = st_w + s_nd * SW + (s_ax - 1) * NT;
+#pragma unroll
+                    for (int i = 0; i < NT; i++) dst[i] = w[i];
+                } else {
+                    C *a = st_a + s_nd * NT;
+#pragma unroll
+                    for (int i = 0; i < NT; i++) {
+                        C t;
+                        t.x = w[i] * v_next.x;
+                        t.y = w[i] * v_next.y;
+                        a[i] = t;
+                    }
+                    const unsigned first =
+                        (unsigned)(((loc0 + start) * td1 + loc1 + start) * pitch + loc2 + start);
+                    st_pk[s_nd] = first | ((unsigned)((loc0 + start) & 7) << 28) |
+                                  ((unsigned)start << 31);
+                }
+            }
+            __syncthreads();  // (also orders the previous flush's zeroing before these adds)
+            {
+                const int nx = c0 + kPlaneChunk + s_nd;  // prefetch the next chunk
+                if (s_ax < 3 && nx < P.count) {
+                    r_next = rec[P.start + nx];
+                    if (s_ax == 0) v_next = f[perm[P.start + nx]];
+                }
+            }
+            for (int k = 0; k < cnt; k++) {
+                const unsigned pk = st_pk[k];
+                const int start = (int)(pk >> 31);
+                // the planes of this warp: a0 = (first plane) + i0 with a0 mod 8 = warp
+                const int i0 = (warp - (int)((pk >> 28) & 7u)) & (kPlaneWarps - 1);
+                C *first = tile + (pk & 0x0fffffffu);
+                if (start)
+                    plane_taps<T, MM, 1>(first, i0, pstride, pitch, st_w + k * SW, st_a + k * NT,
+                                         lane);
+                else
+                    plane_taps<T, MM, 0>(first, i0, pstride, pitch, st_w + k * SW, st_a + k * NT,
+                                         lane);
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+
+        // flush: cell (a0, a1, a2) of the tile is grid point ((org_t - m + a_t) mod n_t);
+        // consecutive lanes take consecutive cells of a row; each cell is zeroed after reading
+        C z;
+        z.x = (T)0;
+        z.y = (T)0;
+        const int rows = td0 * td1;
+        for (int row = warp; row < rows; row += kPlaneWarps) {
+            const int a0 = row / td1, a1 = row - a0 * td1;
+            const size_t gbase = ((size_t)wrapn(org[0] - MM + a0, g.n[0]) * g.n[1] +
+                                  (size_t)wrapn(org[1] - MM + a1, g.n[1])) *
+                                 g.n[2];
+            for (int a2 = lane; a2 < td2; a2 += 32) {
+                C *p = tile + (size_t)row * pitch + a2;
+                const C cv = *p;
+                if (cv.x == (T)0 && cv.y == (T)0) continue;
+                *p = z;
+                global_add(grid + gbase + (size_t)wrapn(org[2] - MM + a2, g.n[2]), cv.x, cv.y);
+            }
+        }
+    }
+    finish_subproblems(nsub_total);
+}
+
 // Shared memory left for the dynamic part once the static window tables are placed.
 template <typename T, int MM> constexpr size_t spread_dyn_limit()
 {
@@ -962,6 +1185,7 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
         method = tile * kSpreadWarps <= 64 * 1024 ? kSpreadWarpPrivate : kSpreadWarpAtomic;
         // measured fastest for 2-D: sixteen lanes per node in FP32, eight in FP64
         if (D == 2) method = sizeof(T) == 8 ? kSpreadOctet : kSpreadHalf;
+        if (D == 3) method = kSpreadPlane;
     }
     // a form whose shared memory does not fit falls back to the one-tile form
     constexpr size_t limit = spread_dyn_limit<T, MM>();
@@ -975,6 +1199,12 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
         method = kSpreadWarpPrivate;
     if (method == kSpreadHalf && (D != 2 || half_tiles + half_stage_bytes<T>() > 227 * 1024))
         method = kSpreadWarpPrivate;
+    const size_t plane_tile = D == 3 ? ((size_t)(g.bs[0] + 2 * MM) * (size_t)(g.bs[1] + 2 * MM) *
+                                           (size_t)plane_pitch<T>(g.bs[D - 1] + 2 * MM) *
+                                           sizeof(typename Cplx<T>::type) + 15) / 16 * 16
+                                     : 0;
+    if (method == kSpreadPlane && (D != 3 || plane_tile + plane_stage_bytes<T, MM>() > limit))
+        method = kSpreadWarpAtomic;
     if (method == kSpreadWarpPrivate && tile * kSpreadWarps + 16 + spread_stage_bytes<T>() > limit)
         method = kSpreadWarpAtomic;
     if (method == kSpreadWarpAtomic && tile + 16 + spread_stage_bytes<T>() > limit)
@@ -1017,6 +1247,23 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
                                       max_subs, blocks);
                 if (e != cudaSuccess) return e;
                 spread_half_kernel<T, MM, false><<<blocks, 32 * kHalfWarps, smem, stream>>>(
+                    g, f, rec, perm, subs, nsub_total, grid);
+            }
+        }
+    } else if (method == kSpreadPlane) {
+        if constexpr (D == 3) {
+            const size_t smem = plane_tile + plane_stage_bytes<T, MM>();
+            if (g.lin_k) {
+                e = launch_persistent(spread_plane_kernel<T, MM, true>, smem, 32 * kPlaneWarps,
+                                      max_subs, blocks);
+                if (e != cudaSuccess) return e;
+                spread_plane_kernel<T, MM, true><<<blocks, 32 * kPlaneWarps, smem, stream>>>(
+                    g, f, rec, perm, subs, nsub_total, grid);
+            } else {
+                e = launch_persistent(spread_plane_kernel<T, MM, false>, smem, 32 * kPlaneWarps,
+                                      max_subs, blocks);
+                if (e != cudaSuccess) return e;
+                spread_plane_kernel<T, MM, false><<<blocks, 32 * kPlaneWarps, smem, stream>>>(
                     g, f, rec, perm, subs, nsub_total, grid);
             }
         }

@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 METHODS = ["thread", "warp_atomic", "warp_private"]
 METHODS_2D = METHODS + ["octet", "half"]  # the group forms exist for d = 2 only
+METHODS_3D = METHODS + ["plane"]  # the plane form exists for d = 3 only
 INTERP = ["thread", "warp", "tile"]
 
 
@@ -52,7 +53,7 @@ def test_radial_reduced(dtype, method, interp, m):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("method", METHODS_3D)
 @pytest.mark.parametrize("interp", INTERP)
 def test_clusters_reduced(dtype, method, interp):
     N = (32, 32, 32)
@@ -98,6 +99,27 @@ def test_bin_sizes(bins):
         yh = plan.adjoint(to_dev(f, torch.float64)).cpu().numpy()
         assert rel_l2(yf, oracle.nfft(x, fh, n=n, m=m)) <= 1e-12
         assert rel_l2(yh, oracle.nfft_adjoint(x, f, N, n=n, m=m)) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("bins,sub", [((8, 8, 8), 1024), ((16, 16, 8), 256), ((4, 4, 8), 32),
+                                      ((2, 32, 4), 128), ((8, 16, 16), 1024)])
+def test_plane_form_bins_and_subproblems(dtype, bins, sub):
+    """The d = 3 plane form over tile shapes (padded and unpadded row pitch), subproblem sizes
+    below and above one staged chunk of nodes, and clustered nodes (bins split into many
+    subproblems): the same transform as the oracle."""
+    N, n, m = (24, 32, 16), (48, 64, 32), 4
+    x = W.round_nodes(W.clustered_nodes(40000, 3, seed_offset=607),
+                      np.float32 if dtype == torch.float32 else np.float64)
+    M = x.shape[0]
+    f = W.gaussian_values(M, 608)
+    plan = _plan(N, n, m, M, dtype, "plane", bins)
+    plan.set_option("subproblem", sub)
+    plan.set_nodes(to_dev(x, dtype))
+    yh = plan.adjoint(to_dev(f, dtype)).cpu().numpy()
+    assert plan.status() == 0
+    xr, fr = rounded(x, dtype), rounded(f, dtype)
+    assert rel_l2(yh, oracle.nfft_adjoint(xr, fr, N, n=n, m=m)) <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
