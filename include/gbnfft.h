@@ -190,7 +190,8 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           the nearest form that fits (6 -> 2 -> 1, 4/5 -> 3 -> 2 -> 1).
  *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node (gathers from the grid),
  *                           2 one warp per node, 3 one thread per node gathering from a
- *                           shared-memory tile of the node's bin.
+ *                           shared-memory tile of the node's bin, 4 (d = 2, 3 and m <= 4;
+ *                           else 1) eight lanes per node reading contiguous row segments.
  *   NFFT_OPT_BIN_0..2       bin (tile) size on axis 0..d-1: a power of two, 0 = default;
  *                           clipped to n_t (power-of-two n_t) or to the largest power of two
  *                           <= n_t / 2 (other n_t, whose last bin is then partial).

@@ -81,7 +81,7 @@ OPT_WINDOW = 6
 OPT_SUBPROBLEM = 7
 OPT_WINDOW_TABLE = 8
 WINDOWS = {"kaiser_bessel": 0, "gaussian": 1, "bspline": 2, "sinc": 3}
-INTERP_METHODS = {"auto": 0, "thread": 1, "warp": 2, "tile": 3}
+INTERP_METHODS = {"auto": 0, "thread": 1, "warp": 2, "tile": 3, "octet": 4}
 SPREAD_METHODS = {"auto": 0, "thread": 1, "warp_atomic": 2, "warp_private": 3, "octet": 4,
                   "half": 5, "plane": 6}
 

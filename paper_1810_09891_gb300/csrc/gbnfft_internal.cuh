@@ -60,6 +60,7 @@ constexpr int kInterpAuto = 0;
 constexpr int kInterpThread = 1;
 constexpr int kInterpWarp = 2;
 constexpr int kInterpTile = 3;
+constexpr int kInterpOctet = 4;
 
 // Geometry passed by value to every kernel.
 struct Geom {

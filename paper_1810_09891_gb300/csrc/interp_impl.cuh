@@ -2,15 +2,17 @@
 //   f_j = sum_{l in I_{n,m}(x_j)} g_{l mod n} prod_t psi_t(n_t x_{j,t} - l_t),
 // and the derivative of the same sum with respect to the node coordinates (node gradient).
 //
-// Thread form (default): one thread per node, nodes visited in bin-sorted order so that the
-// threads of a warp read neighbouring grid cells (L1/L2 reuse of the oversampled grid). The
-// window values of the inner axes are evaluated once per node into registers from the per-tap
-// polynomials (tables staged in shared memory, read as warp-wide broadcasts); the outermost
-// axis' value is evaluated in the outer loop. Nodes whose offset on some axis is exactly 0 (a
+// Thread form (default but for 3-D FP32): one thread per node, nodes visited in bin-sorted
+// order so that the threads of a warp read neighbouring grid cells (L1/L2 reuse of the
+// oversampled grid). The window values of the inner axes are evaluated once per node into
+// registers from the per-tap polynomials (kernel-argument tables, read as warp-wide
+// broadcasts); the outermost axis' value is evaluated in the outer loop. Nodes whose offset on some axis is exactly 0 (a
 // node on a grid point) use 2m+1 taps per axis; all other nodes use 2m (the closed support of
 // eq. Inm).
 //
-// Warp form (option): one warp per node, the lanes cover the node's taps.
+// Warp form (option): one warp per node, the lanes cover the node's taps. Octet form (default
+// for 3-D FP32 with m <= 4): eight lanes per node along the last axis (see below). Tiled form
+// (option): gathers from a shared-memory copy of the bin's tile.
 #pragma once
 
 #include "gbnfft_internal.cuh"
@@ -201,6 +203,106 @@ __global__ void __launch_bounds__(kInterpThreads)
     f[perm[s]] = v;
 }
 
+
+// ------------------------------------------------------------------------- octet form of B
+// Eight lanes per node, four nodes per warp (d = 2, 3; 2m <= 8). Lane l of a group reads cell
+// l of every row segment of its node (the 2m cells of a row along the last axis), so one load
+// instruction of the group reads a contiguous 8 x 8 (FP32) or 8 x 16 (FP64) bytes and a row
+// costs two or three 32-byte sectors instead of one sector per cell pair. Lane l evaluates tap
+// l + 1 of every axis; the outer-axis values reach the other lanes by shuffles, the lane's own
+// last-axis value scales its partial sum, and three shuffle steps add the eight partial sums.
+// A node on a grid point (2m + 1 taps on some axis) is done by the group's first lane alone.
+template <typename T, int D, int MM, bool LIN>
+__global__ void __launch_bounds__(kInterpThreads)
+    interp_octet_kernel(Geom g, const typename Cplx<T>::type *__restrict__ grid,
+                        const typename RecOf<T>::type *__restrict__ rec,
+                        const int *__restrict__ perm, int M,
+                        typename Cplx<T>::type *__restrict__ f)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int PT = 2 * MM;  // taps per axis of a node off the grid points
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    constexpr int MODE = LIN ? 2 : 1;
+    static_assert(PT <= 8 && D >= 2, "octet form: d = 2, 3 and m <= 4");
+    const T *poly = static_cast<const T *>(g.poly);
+    const int lane = threadIdx.x & 31, l = lane & 7;
+    const unsigned omask = 0xffu << (lane & 24);
+    const int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    if (s >= M) return;  // uniform in the group
+    const typename RecOf<T>::type r = rec[s];
+    int base[D];
+    T frac[D];
+    bool edge;
+    decode_node<T, D>(g, r, base, frac, edge);
+    if (edge) {  // uniform in the group
+        if (l == 0) f[perm[s]] = interp_node<T, D, MM, 0, MODE>(g, poly, grid, base, frac);
+        return;
+    }
+    const bool on = l < PT;
+    T wl[D];  // psibar of tap l + 1 on each axis (0 for lanes past the 2m taps)
+#pragma unroll
+    for (int t = 0; t < D; t++) {
+        if constexpr (LIN)
+            wl[t] = on ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, t), g.lin_k, l + 1,
+                                        frac[t], (T)0)
+                       : (T)0;
+        else
+            wl[t] = on ? poly_horner_tap<T, DEG>(poly + t * AS, l + 1, (T)2 * frac[t] - (T)1)
+                       : (T)0;
+    }
+    const int nl = g.n[D - 1];
+    const int col = on ? wrapn(base[D - 1] - MM + 1 + l, nl) : 0;
+    C acc;
+    acc.x = (T)0;
+    acc.y = (T)0;
+    if constexpr (D == 2) {
+        const int n0 = g.n[0];
+#pragma unroll
+        for (int i0 = 0; i0 < PT; i0++) {
+            const T w0 = __shfl_sync(omask, wl[0], i0, 8);
+            if (on) {
+                const C v = __ldg(grid + (size_t)wrapn(base[0] - MM + 1 + i0, n0) * nl + col);
+                acc.x += v.x * w0;
+                acc.y += v.y * w0;
+            }
+        }
+    } else {
+        const int n0 = g.n[0], n1 = g.n[1];
+        T w1[PT];
+        int roff[PT];
+#pragma unroll
+        for (int i1 = 0; i1 < PT; i1++) {
+            w1[i1] = __shfl_sync(omask, wl[1], i1, 8);
+            roff[i1] = wrapn(base[1] - MM + 1 + i1, n1) * nl + col;
+        }
+        for (int i0 = 0; i0 < PT; i0++) {
+            const T w0 = __shfl_sync(omask, wl[0], i0, 8);
+            const C *plane = grid + (size_t)wrapn(base[0] - MM + 1 + i0, n0) * n1 * nl;
+            C pl;
+            pl.x = (T)0;
+            pl.y = (T)0;
+#pragma unroll
+            for (int i1 = 0; i1 < PT; i1++) {
+                if (on) {
+                    const C v = __ldg(plane + roff[i1]);
+                    pl.x += v.x * w1[i1];
+                    pl.y += v.y * w1[i1];
+                }
+            }
+            acc.x += pl.x * w0;
+            acc.y += pl.y * w0;
+        }
+    }
+    acc.x *= wl[D - 1];
+    acc.y *= wl[D - 1];
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(omask, acc.x, o, 8);
+        acc.y += __shfl_xor_sync(omask, acc.y, o, 8);
+    }
+    if (l == 0) f[perm[s]] = acc;
+}
 
 // ------------------------------------------------------------------------- tiled form of B
 // One CTA per subproblem (up to kMaxSub sorted nodes of one bin, the list built by set_nodes):
@@ -587,7 +689,10 @@ cudaError_t launch_interp_m(const Geom &g, const typename Cplx<T>::type *grid,
     const size_t tile = cells * sizeof(C);
     constexpr size_t tables = kMaxDim * poly_axis_stride(sizeof(T) == 8, MM) * sizeof(T);
     int method = g.interp_method;
-    if (method == kInterpAuto) method = kInterpThread;  // measured fastest on the GB300
+    // measured fastest on the GB300: the octet form for 3-D FP32 (m <= 4; clustered 3-D
+    // workload 1.53 ms against 1.71 ms), the thread form everywhere else
+    if (method == kInterpAuto)
+        method = (D == 3 && sizeof(T) == 4 && 2 * MM <= 8) ? kInterpOctet : kInterpThread;
     if (method == kInterpTile && tile + tables > 227 * 1024) method = kInterpThread;
     if (method == kInterpTile) {
         cudaError_t e = ensure_dynamic_smem(interp_tile_kernel<T, D, MM>, tile);
@@ -601,6 +706,16 @@ cudaError_t launch_interp_m(const Geom &g, const typename Cplx<T>::type *grid,
         if (blocks > max_subs) blocks = max_subs;
         interp_tile_kernel<T, D, MM><<<blocks, kInterpTileThreads, tile, stream>>>(
             g, grid, rec, perm, subs, nsub_total, f);
+    } else if (method == kInterpOctet && D >= 2 && 2 * MM <= 8) {
+        if constexpr (D >= 2 && 2 * MM <= 8) {
+            const int64_t blocks = (8 * M + kInterpThreads - 1) / kInterpThreads;
+            if (g.lin_k)
+                interp_octet_kernel<T, D, MM, true><<<(unsigned)blocks, kInterpThreads, 0,
+                                                      stream>>>(g, grid, rec, perm, (int)M, f);
+            else
+                interp_octet_kernel<T, D, MM, false><<<(unsigned)blocks, kInterpThreads, 0,
+                                                       stream>>>(g, grid, rec, perm, (int)M, f);
+        }
     } else if (method == kInterpWarp) {
         const int64_t blocks = (M + kInterpWarps - 1) / kInterpWarps;
         interp_warp_kernel<T, D, MM><<<(unsigned)blocks, 32 * kInterpWarps, 0, stream>>>(

@@ -1076,7 +1076,7 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
         p->geom.spread_method = (int)value;
         return NFFT_OK;
     case NFFT_OPT_INTERP_METHOD:
-        if (value < kInterpAuto || value > kInterpTile) return NFFT_EINVAL;
+        if (value < kInterpAuto || value > kInterpOctet) return NFFT_EINVAL;
         p->geom.interp_method = (int)value;
         return NFFT_OK;
     case NFFT_OPT_WINDOW:

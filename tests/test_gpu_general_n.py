@@ -56,7 +56,7 @@ def test_general_n_parity(N, n, m, M, dtype):
 
 
 @pytest.mark.parametrize("spread", ["thread", "warp_atomic", "warp_private", "octet", "half", "plane"])
-@pytest.mark.parametrize("interp", ["thread", "warp", "tile"])
+@pytest.mark.parametrize("interp", ["thread", "warp", "tile", "octet"])
 def test_general_n_every_form(spread, interp):
     """Radial nodes (dense centre) on a 2-D grid whose last bins are partial."""
     N, n, m = (96, 80), (200, 162), 4

@@ -116,7 +116,7 @@ def test_table_error_converges_on_gpu():
         assert 3.0 <= a / b <= 5.0, errs
 
 
-@pytest.mark.parametrize("interp", ["thread", "warp", "tile"])
+@pytest.mark.parametrize("interp", ["thread", "warp", "tile", "octet"])
 @pytest.mark.parametrize("d", [2, 3])
 def test_table_window_interp_forms(interp, d):
     N = {2: (40, 36), 3: (12, 10, 8)}[d]

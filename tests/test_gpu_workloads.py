@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 METHODS = ["thread", "warp_atomic", "warp_private"]
 METHODS_2D = METHODS + ["octet", "half"]  # the group forms exist for d = 2 only
 METHODS_3D = METHODS + ["plane"]  # the plane form exists for d = 3 only
-INTERP = ["thread", "warp", "tile"]
+INTERP = ["thread", "warp", "tile", "octet"]
 
 
 def _plan(N, n, m, M, dtype, method=None, bins=None, interp=None):
