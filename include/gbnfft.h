@@ -130,6 +130,37 @@ int nfft_adjoint_host(nfft_plan plan, const void *f_host, void *fhat_host);
  * call (NFFT_OK if none), then clear it. A CUDA error seen while waiting gives NFFT_ECUDA. */
 int nfft_status(nfft_plan plan);
 
+/* Batches: many independent transforms of uneven N and M run concurrently (the paper's plan
+ * of Section 3.1, many times over). A batch borrows `count` plans created on one device (they
+ * stay owned by the caller and must outlive the batch; their nodes are set with
+ * nfft_set_nodes as usual). Every batch call enqueues on the batch's stream
+ * (nfft_batch_set_stream; NULL = legacy default): it forks into `streams` side streams owned by
+ * the batch (0 = 8, at most count and 64), runs plan i on side stream lane i (plans assigned
+ * largest first to the least-loaded lane, work ~ M_i + |I_n,i|; the plan's own stream is
+ * restored afterwards) and joins the side streams back into the batch's stream, so later work
+ * on that stream sees every result. The calls record into a CUDA graph as parallel branches.
+ * Pointer arrays hold one device pointer per plan, with the layouts of nfft_trafo,
+ * nfft_adjoint and nfft_grad_x. Every plan is checked (nodes set, pointers non-null and
+ * aligned) before any work is enqueued; a failure returns NFFT_ENOTREADY or NFFT_EINVAL with
+ * nothing enqueued. A CUDA error while enqueuing stops issuing the remaining plans, still joins
+ * the side streams, and returns NFFT_ECUDA. The arrays are read during the call only. */
+typedef struct gbnfft_batch *nfft_batch;
+int nfft_batch_create(nfft_batch *out, const nfft_plan *plans, int count, int streams);
+/* Wait for the batch's side streams and release them. NULL gives NFFT_EINVAL. */
+int nfft_batch_destroy(nfft_batch batch);
+int nfft_batch_set_stream(nfft_batch batch, void *cuda_stream);
+/* Number of plans and of side streams (either pointer may be NULL). */
+int nfft_batch_size(nfft_batch batch, int *count, int *streams);
+/* Side stream lane of plan i, or -1 for an invalid batch or index. */
+int nfft_batch_lane(nfft_batch batch, int i);
+/* Forward NFFT of every plan: f[i] = NFFT_i(fhat[i]). */
+int nfft_batch_trafo(nfft_batch batch, const void *const *fhat, void *const *f);
+/* Adjoint NFFT of every plan: fhat[i] = NFFT_i^H(f[i]). */
+int nfft_batch_adjoint(nfft_batch batch, const void *const *f, void *const *fhat);
+/* Node gradient of every plan: gx[i] = nfft_grad_x(plan i, coef[i], w[i]). */
+int nfft_batch_grad_x(nfft_batch batch, const void *const *coef, const void *const *w,
+                      void *const *gx);
+
 /* Plan parameters after defaults: d, N[3], n[3], M, m, dtype, the tile (bin) size used to
  * sort the nodes, the workspace size and the window (NFFT_OPT_WINDOW). Unused trailing entries
  * are 0. */

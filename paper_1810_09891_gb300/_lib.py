@@ -72,6 +72,15 @@ SIGNATURES = {
     "nfft_profile": ([_P, _I], _I),
     "nfft_profile_read": ([_P, ctypes.POINTER(ctypes.c_double), _PI64, _I], _I),
     "nfft_trafo_1d_noalloc": ([_I64, _I64, _PI64, _I, _P, _P, _P, _P], _I),
+    # batches: pointer arrays are passed as the address of a ctypes array of c_void_p
+    "nfft_batch_create": ([ctypes.POINTER(_P), _P, _I, _I], _I),
+    "nfft_batch_destroy": ([_P], _I),
+    "nfft_batch_set_stream": ([_P, _P], _I),
+    "nfft_batch_size": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "nfft_batch_lane": ([_P, _I], _I),
+    "nfft_batch_trafo": ([_P, _P, _P], _I),
+    "nfft_batch_adjoint": ([_P, _P, _P], _I),
+    "nfft_batch_grad_x": ([_P, _P, _P, _P], _I),
 }
 
 OPT_SPREAD_METHOD = 1

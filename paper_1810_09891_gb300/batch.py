@@ -1,16 +1,19 @@
 """Many NFFTs of uneven size at once: a batch of plans, captured in one CUDA graph, with
 per-plan tuning by measurement.
 
-``PlanBatch`` owns one ``Plan`` per problem (its own N, M, n, m, precision). ``trafo`` /
-``adjoint`` run every plan's kernels on the current stream; ``capture`` records the forward and
-the adjoint of the whole batch into one CUDA graph over static input and output buffers, and
-``replay`` launches the batch with a single graph launch (no per-kernel host overhead).
+``PlanBatch`` owns one ``Plan`` per problem (its own N, M, n, m, precision) and one library
+batch over them (``nfft_batch_*`` of the C ABI: the plans run concurrently on side streams
+forked from and joined into the current stream). ``trafo`` / ``adjoint`` / ``backward`` call the
+library batch; ``capture`` records the forward and the adjoint of the whole batch into one CUDA
+graph over static input and output buffers, and ``replay`` launches the batch with a single
+graph launch (no per-kernel host overhead).
 ``autotune`` chooses, per plan, the spreading method and bin sizes by timing candidates on the
 plan's own nodes (the measured counterpart of the plan search the paper's FFTW flags select,
 Section 3.1, Table tab:fttwflags). Every candidate computes the same transform up to rounding.
 """
 from __future__ import annotations
 
+import ctypes
 import itertools
 import json
 import os
@@ -18,6 +21,8 @@ import statistics
 
 import torch
 
+from . import _lib
+from ._lib import check
 from .nfft import Plan
 
 
@@ -35,8 +40,9 @@ CANDIDATES = {
         ("half", (16, 16), 256), ("octet", (8, 16), 1024), ("octet", (8, 16), 256),
         ("warp_private", (16, 16), 256), ("warp_private", (8, 16), 256),
         ("warp_private", (16, 16), 1024), ("warp_atomic", (16, 16), 256)],
-    3: [(s, b, w) for s in ("warp_atomic", "thread") for b in ((8, 8, 8), (4, 8, 8), (8, 8, 16))
-        for w in (256, 1024)] + [("warp_private", (8, 8, 8), w) for w in (256, 1024)],
+    3: [("plane", b, w) for b in ((8, 8, 16), (4, 16, 16), (8, 8, 8)) for w in (512, 1024)] +
+       [(s, b, w) for s in ("warp_atomic", "thread") for b in ((8, 8, 8), (8, 8, 16))
+        for w in (256, 1024)],
 }
 
 
@@ -120,41 +126,67 @@ class TuningCache:
 class PlanBatch:
     """A batch of independent NFFT problems (uneven N and M) on one device.
 
-    The plans run on ``streams`` side streams, forked from and joined back into the caller's
-    stream, so that small problems execute concurrently (in a captured graph they become
-    parallel branches). Plans are assigned to streams largest first, each to the stream with
-    the least work so far (work ~ M + |I_n|)."""
+    The plans run on ``streams`` side streams of the library batch, forked from and joined
+    back into the caller's stream, so that small problems execute concurrently (in a captured
+    graph they become parallel branches). The library assigns plans to side streams largest
+    first, each to the stream with the least work so far (work ~ M + |I_n|)."""
 
     def __init__(self, specs, dtype=torch.float32, device=None, streams: int = 8):
         """specs: iterable of dicts with keys N, M and optionally n, m (default 4)."""
         specs = list(specs)
+        if not specs:
+            raise ValueError("a batch needs at least one problem")
         self.plans = [Plan(s["N"], s["M"], n=s.get("n"), m=s.get("m", 4), dtype=dtype,
                            device=device) for s in specs]
-        self.device = self.plans[0].device if self.plans else device
+        self.device = self.plans[0].device
         self.dtype = dtype
         self.graph = None
-        k = max(1, min(int(streams), len(self.plans)))
-        self.streams = [torch.cuda.Stream(self.device) for _ in range(k)]
-        load = [0.0] * k
-        self.lane = [0] * len(self.plans)
-        work = [p.M + _prod(p.n) for p in self.plans]
-        for i in sorted(range(len(self.plans)), key=lambda i: -work[i]):
-            j = min(range(k), key=lambda j: load[j])
-            self.lane[i] = j
-            load[j] += work[i]
+        k = len(self.plans)
+        L = _lib.lib()
+        handles = (ctypes.c_void_p * k)(*[p._h.value for p in self.plans])
+        self._b = ctypes.c_void_p()
+        check(L.nfft_batch_create(ctypes.byref(self._b), ctypes.cast(handles, ctypes.c_void_p),
+                                  k, int(streams)), "nfft_batch_create")
+        cnt, ns = ctypes.c_int(), ctypes.c_int()
+        check(L.nfft_batch_size(self._b, ctypes.byref(cnt), ctypes.byref(ns)), "nfft_batch_size")
+        self.n_streams = ns.value
+        self.lane = [L.nfft_batch_lane(self._b, i) for i in range(k)]
 
-    def _each(self, fn, args) -> list:
-        """fn(plan, arg) for every plan on its side stream; the caller's stream waits for all."""
-        main = torch.cuda.current_stream(self.device)
-        for s in self.streams:
-            s.wait_stream(main)
-        out = [None] * len(self.plans)
-        for i, (p, a) in enumerate(zip(self.plans, args)):
-            with torch.cuda.stream(self.streams[self.lane[i]]):
-                out[i] = fn(p, a)
-        for s in self.streams:
-            main.wait_stream(s)
-        return out
+    def close(self):
+        b = getattr(self, "_b", None)
+        if b is not None and b.value:
+            _lib.lib().nfft_batch_destroy(b)
+            self._b = ctypes.c_void_p()
+        for p in getattr(self, "plans", []):
+            p.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name: str, *arrays) -> None:
+        """One library batch call on the current stream; each argument is a list of tensors
+        (one per plan) passed as an array of device pointers."""
+        L = _lib.lib()
+        stream = torch.cuda.current_stream(self.device)
+        check(L.nfft_batch_set_stream(self._b, ctypes.c_void_p(stream.cuda_stream)),
+              "nfft_batch_set_stream")
+        k = len(self.plans)
+        ptrs = [ctypes.cast((ctypes.c_void_p * k)(*[t.data_ptr() for t in a]), ctypes.c_void_p)
+                for a in arrays]
+        check(getattr(L, name)(self._b, *ptrs), name)
+
+    def _fhats(self, fhats, name="fhat") -> list:
+        if len(fhats) != len(self.plans):
+            raise ValueError(f"one {name} per plan")
+        return [p._complex_in(t, _prod(p.N), name) for p, t in zip(self.plans, fhats)]
+
+    def _fs(self, fs, name="f") -> list:
+        if len(fs) != len(self.plans):
+            raise ValueError(f"one {name} per plan")
+        return [p._complex_in(t, p.M, name) for p, t in zip(self.plans, fs)]
 
     def __len__(self):
         return len(self.plans)
@@ -180,21 +212,34 @@ class PlanBatch:
         return out
 
     def trafo(self, fhats) -> list:
-        return self._each(lambda p, fh: p.trafo(fh), fhats)
+        """Forward NFFT of every problem (Algorithm "NFFT"); returns the list of f_i."""
+        ins = self._fhats(fhats)
+        outs = [torch.empty(p.M, dtype=p.cdtype, device=p.device) for p in self.plans]
+        self._call("nfft_batch_trafo", ins, outs)
+        return outs
 
     def adjoint(self, fs) -> list:
-        return self._each(lambda p, f: p.adjoint(f), fs)
+        """Adjoint NFFT of every problem (Algorithm "adjoint NFFT"); returns the hhat_i."""
+        ins = self._fs(fs)
+        outs = [torch.empty(p.N, dtype=p.cdtype, device=p.device) for p in self.plans]
+        self._call("nfft_batch_adjoint", ins, outs)
+        return outs
 
     def backward(self, grad_fs, fhats, want_fhat: bool = True, want_x: bool = True) -> tuple:
         """Backward of the batched forward transform f_i = A_i fhat_i for output gradients
         grad_f_i: per plan, grad fhat_i = A_i^H grad_f_i (the adjoint kernels) and grad x_i =
         Re(conj(grad_f_i) d(A_i fhat_i)/dx) (the node-gradient kernel), both on the plan's side
         stream. Returns (grad_fhats, grad_xs); a list not asked for is all None."""
-        def one(p, a):
-            return (p.adjoint(a[0]) if want_fhat else None,
-                    p.grad_x(a[1], a[0]) if want_x else None)
-        out = self._each(one, list(zip(grad_fs, fhats)))
-        return [o[0] for o in out], [o[1] for o in out]
+        k = len(self.plans)
+        g_fhat, g_x = [None] * k, [None] * k
+        if want_fhat:
+            g_fhat = self.adjoint(grad_fs)
+        if want_x:
+            coef = self._fhats(fhats)
+            w = self._fs(grad_fs, "grad_f")
+            g_x = [torch.empty((p.M, p.d), dtype=p.dtype, device=p.device) for p in self.plans]
+            self._call("nfft_batch_grad_x", coef, w, g_x)
+        return g_fhat, g_x
 
     def capture(self, fhats, fs, grad_fs=None) -> None:
         """Record forward(fhats) and adjoint(fs) of the whole batch into one CUDA graph. The

@@ -1274,3 +1274,184 @@ int nfft_adjoint_host(nfft_plan p, const void *f_host, void *fhat_host)
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------ batches
+// A batch runs many independent plans (uneven N and M) concurrently: every call forks the
+// batch's stream into a few side streams with one event, issues plan i on side stream lane[i]
+// (the plan's own stream is swapped for the duration of the call), and joins the side streams
+// back with one event each. Plans go to lanes largest first, each to the lane with the least
+// work so far (work ~ M + |I_n|). The pattern records into a CUDA graph as parallel branches.
+struct gbnfft_batch {
+    std::vector<gbnfft_plan *> plans;
+    std::vector<int> lane;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+};
+
+namespace {
+
+void batch_free(gbnfft_batch *b)
+{
+    for (cudaStream_t s : b->side)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+// fn(plan, i) for every plan of the batch on its lane; the batch stream waits for all of them.
+// The side streams are always joined back (also after a failed call), and the first error is
+// returned; plans after a failure are not issued.
+template <typename Fn> int batch_run(gbnfft_batch *b, Fn fn)
+{
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return NFFT_ECUDA;
+    if (cur != b->device && cudaSetDevice(b->device) != cudaSuccess) return NFFT_ECUDA;
+    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return NFFT_ECUDA;
+    int rc = NFFT_OK;
+    for (cudaStream_t s : b->side)
+        if (cudaStreamWaitEvent(s, b->fork, 0) != cudaSuccess) rc = NFFT_ECUDA;
+    for (size_t i = 0; i < b->plans.size() && rc == NFFT_OK; i++) {
+        gbnfft_plan *p = b->plans[i];
+        cudaStream_t keep = p->stream;
+        p->stream = b->side[b->lane[i]];
+        rc = fn(p, i);
+        p->stream = keep;
+    }
+    for (size_t j = 0; j < b->side.size(); j++) {
+        if (cudaEventRecord(b->join[j], b->side[j]) != cudaSuccess ||
+            cudaStreamWaitEvent(b->stream, b->join[j], 0) != cudaSuccess)
+            rc = rc ? rc : NFFT_ECUDA;
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nfft_batch_create(nfft_batch *out, const nfft_plan *plans, int count, int streams)
+{
+    if (!out || !plans || count < 1) return NFFT_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < count; i++) {
+        if (!plans[i]) return NFFT_EINVAL;
+        if (plans[i]->device != plans[0]->device) return NFFT_EINVAL;
+    }
+    if (streams <= 0) streams = 8;
+    if (streams > count) streams = count;
+    if (streams > 64) streams = 64;
+    gbnfft_batch *b = new (std::nothrow) gbnfft_batch;
+    if (!b) return NFFT_ENOMEM;
+    b->device = plans[0]->device;
+    b->plans.assign(plans, plans + count);
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess ||
+        (cur != b->device && cudaSetDevice(b->device) != cudaSuccess)) {
+        batch_free(b);
+        return NFFT_ECUDA;
+    }
+    b->side.assign(streams, nullptr);
+    b->join.assign(streams, nullptr);
+    bool ok = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int j = 0; j < streams && ok; j++) {
+        ok = cudaStreamCreateWithFlags(&b->side[j], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->join[j], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        batch_free(b);
+        return NFFT_ECUDA;
+    }
+    std::vector<int> order(count);
+    std::vector<double> work(count), load(streams, 0.0);
+    for (int i = 0; i < count; i++) {
+        order[i] = i;
+        work[i] = double(plans[i]->M) + double(plans[i]->G);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+    b->lane.assign(count, 0);
+    for (int i : order) {
+        int best = 0;
+        for (int j = 1; j < streams; j++)
+            if (load[j] < load[best]) best = j;
+        b->lane[i] = best;
+        load[best] += work[i];
+    }
+    *out = b;
+    return NFFT_OK;
+}
+
+int nfft_batch_destroy(nfft_batch b)
+{
+    if (!b) return NFFT_EINVAL;
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != b->device) cudaSetDevice(b->device);
+    for (cudaStream_t s : b->side)
+        if (s) cudaStreamSynchronize(s);
+    batch_free(b);
+    return NFFT_OK;
+}
+
+int nfft_batch_set_stream(nfft_batch b, void *stream)
+{
+    if (!b) return NFFT_EINVAL;
+    b->stream = static_cast<cudaStream_t>(stream);
+    return NFFT_OK;
+}
+
+int nfft_batch_size(nfft_batch b, int *count, int *streams)
+{
+    if (!b) return NFFT_EINVAL;
+    if (count) *count = (int)b->plans.size();
+    if (streams) *streams = (int)b->side.size();
+    return NFFT_OK;
+}
+
+int nfft_batch_lane(nfft_batch b, int i)
+{
+    if (!b || i < 0 || i >= (int)b->plans.size()) return -1;
+    return b->lane[i];
+}
+
+int nfft_batch_trafo(nfft_batch b, const void *const *fhat, void *const *f)
+{
+    if (!b || !fhat || !f) return NFFT_EINVAL;
+    for (size_t i = 0; i < b->plans.size(); i++) {
+        const gbnfft_plan *p = b->plans[i];
+        if (!p->nodes_ready) return NFFT_ENOTREADY;
+        if (check_dev_ptr(p, fhat[i], p->NN) || check_dev_ptr(p, f[i], p->M)) return NFFT_EINVAL;
+    }
+    return batch_run(b, [&](gbnfft_plan *p, size_t i) { return nfft_trafo(p, fhat[i], f[i]); });
+}
+
+int nfft_batch_adjoint(nfft_batch b, const void *const *f, void *const *fhat)
+{
+    if (!b || !f || !fhat) return NFFT_EINVAL;
+    for (size_t i = 0; i < b->plans.size(); i++) {
+        const gbnfft_plan *p = b->plans[i];
+        if (!p->nodes_ready) return NFFT_ENOTREADY;
+        if (check_dev_ptr(p, f[i], p->M) || check_dev_ptr(p, fhat[i], p->NN)) return NFFT_EINVAL;
+    }
+    return batch_run(b, [&](gbnfft_plan *p, size_t i) { return nfft_adjoint(p, f[i], fhat[i]); });
+}
+
+int nfft_batch_grad_x(nfft_batch b, const void *const *coef, const void *const *w,
+                      void *const *gx)
+{
+    if (!b || !coef || !w || !gx) return NFFT_EINVAL;
+    for (size_t i = 0; i < b->plans.size(); i++) {
+        const gbnfft_plan *p = b->plans[i];
+        if (!p->nodes_ready) return NFFT_ENOTREADY;
+        if (check_dev_ptr(p, coef[i], p->NN) || check_dev_ptr(p, w[i], p->M)) return NFFT_EINVAL;
+        if (p->M > 0 && (!gx[i] || !aligned(gx[i], p->rsize))) return NFFT_EINVAL;
+    }
+    return batch_run(b, [&](gbnfft_plan *p, size_t i) {
+        return nfft_grad_x(p, coef[i], w[i], gx[i]);
+    });
+}
+
+}  // extern "C"

@@ -27,7 +27,9 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for must in ["nfft_plan_create", "nfft_set_nodes", "nfft_trafo", "nfft_adjoint",
                  "nfft_destroy", "nfft_grad_x", "nfft_status", "nfft_workspace_size",
-                 "nfft_set_workspace", "nfft_set_stream", "nfft_strerror"]:
+                 "nfft_set_workspace", "nfft_set_stream", "nfft_strerror",
+                 "nfft_batch_create", "nfft_batch_trafo", "nfft_batch_adjoint",
+                 "nfft_batch_destroy"]:
         assert must in names
 
 
@@ -79,6 +81,21 @@ def test_null_arguments(lib):
     assert lib.nfft_adjoint(None, None, None) == 1
     assert lib.nfft_set_nodes(None, None) == 1
     assert lib.nfft_status(None) == 1
+    # batches: argument checks come before any CUDA call
+    b = ctypes.c_void_p()
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    assert lib.nfft_batch_create(None, None, 1, 0) == 1
+    assert lib.nfft_batch_create(ctypes.byref(b), None, 1, 0) == 1
+    assert lib.nfft_batch_create(ctypes.byref(b), ctypes.cast(nulls, ctypes.c_void_p), 0, 0) == 1
+    assert lib.nfft_batch_create(ctypes.byref(b), ctypes.cast(nulls, ctypes.c_void_p), 2, 0) == 1
+    assert not b.value
+    assert lib.nfft_batch_destroy(None) == 1
+    assert lib.nfft_batch_set_stream(None, None) == 1
+    assert lib.nfft_batch_size(None, None, None) == 1
+    assert lib.nfft_batch_lane(None, 0) == -1
+    assert lib.nfft_batch_trafo(None, None, None) == 1
+    assert lib.nfft_batch_adjoint(None, None, None) == 1
+    assert lib.nfft_batch_grad_x(None, None, None, None) == 1
 
 
 def test_plain_c_consumer_compiles_and_links(tmp_path):

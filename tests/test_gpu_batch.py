@@ -165,3 +165,96 @@ def test_batch_autograd_only_fhat():
         f = oracle.nfft(xs[i], fhs[i], n=b.plans[i].n, m=4)
         ref = 2 * oracle.nfft_adjoint(xs[i], f, s["N"], n=b.plans[i].n, m=4)
         assert rel_l2(fht[i].grad.cpu().numpy(), ref) <= 1e-12
+
+
+def _lib_batch(plans, streams=0):
+    import ctypes
+
+    from paper_1810_09891_gb300 import _lib
+    L = _lib.lib()
+    arr = (ctypes.c_void_p * len(plans))(*[p._h.value for p in plans])
+    b = ctypes.c_void_p()
+    assert L.nfft_batch_create(ctypes.byref(b), ctypes.cast(arr, ctypes.c_void_p), len(plans),
+                               streams) == 0
+    return L, b
+
+
+def _ptr_array(ts):
+    import ctypes
+    return ctypes.cast((ctypes.c_void_p * len(ts))(*[t.data_ptr() for t in ts]), ctypes.c_void_p)
+
+
+def test_library_batch_mixed_dimensions_and_precisions():
+    """The C-ABI batch over plans of different d and precision: every forward, adjoint and node
+    gradient equals the oracle's, and the lanes balance the work."""
+    import ctypes
+    cases = [((40,), 900, torch.float64), ((32, 24), 3000, torch.float32),
+             ((8, 12, 10), 2500, torch.float32), ((8, 8, 8), 1200, torch.float64),
+             ((64, 64), 20000, torch.float32)]
+    plans, xs, fhs, fs = [], [], [], []
+    for i, (N, M, dt) in enumerate(cases):
+        p = Plan(N, M, m=4, dtype=dt, device=DEV)
+        x = W.round_nodes(W.uniform_nodes(M, len(N), seed_offset=1500 + i),
+                          np.float32 if dt == torch.float32 else np.float64)
+        p.set_nodes(to_dev(x, dt))
+        plans.append(p)
+        xs.append(x)
+        fhs.append(W.gaussian_fhat(N, 1510 + i))
+        fs.append(W.gaussian_values(M, 1520 + i))
+    L, b = _lib_batch(plans, streams=3)
+    cnt, ns = ctypes.c_int(), ctypes.c_int()
+    assert L.nfft_batch_size(b, ctypes.byref(cnt), ctypes.byref(ns)) == 0
+    assert (cnt.value, ns.value) == (len(cases), 3)
+    lanes = [L.nfft_batch_lane(b, i) for i in range(len(cases))]
+    assert all(0 <= v < 3 for v in lanes) and L.nfft_batch_lane(b, len(cases)) == -1
+    work = [p.M + int(np.prod(p.n)) for p in plans]
+    load = [sum(w for w, v in zip(work, lanes) if v == j) for j in range(3)]
+    assert max(load) - min(load) <= max(work)
+    stream = torch.cuda.current_stream(DEV)
+    assert L.nfft_batch_set_stream(b, ctypes.c_void_p(stream.cuda_stream)) == 0
+    fht = [to_dev(v, p.dtype) for v, p in zip(fhs, plans)]
+    ft = [to_dev(v, p.dtype) for v, p in zip(fs, plans)]
+    out_f = [torch.empty(p.M, dtype=p.cdtype, device=DEV) for p in plans]
+    out_h = [torch.empty(p.N, dtype=p.cdtype, device=DEV) for p in plans]
+    out_g = [torch.empty((p.M, p.d), dtype=p.dtype, device=DEV) for p in plans]
+    assert L.nfft_batch_trafo(b, _ptr_array(fht), _ptr_array(out_f)) == 0
+    assert L.nfft_batch_adjoint(b, _ptr_array(ft), _ptr_array(out_h)) == 0
+    assert L.nfft_batch_grad_x(b, _ptr_array(fht), _ptr_array(ft), _ptr_array(out_g)) == 0
+    torch.cuda.synchronize()
+    for i, (N, M, dt) in enumerate(cases):
+        n = plans[i].n
+        xr, fhr, fr = rounded(xs[i], dt), rounded(fhs[i], dt), rounded(fs[i], dt)
+        assert rel_l2(out_f[i].cpu().numpy(), oracle.nfft(xr, fhr, n=n, m=4)) <= TOL[dt]
+        assert rel_l2(out_h[i].cpu().numpy(), oracle.nfft_adjoint(xr, fr, N, n=n, m=4)) <= TOL[dt]
+        tol_x = 1e-11 if dt == torch.float64 else 1e-5
+        assert rel_l2(out_g[i].cpu().numpy(), oracle.nfft_grad_x(xr, fhr, fr, n=n, m=4)) <= tol_x
+    assert L.nfft_batch_destroy(b) == 0
+
+
+def test_library_batch_checks_every_plan_before_enqueuing():
+    """A plan without nodes or a null pointer in the arrays fails the whole call with nothing
+    enqueued: the outputs of the other plans keep their previous contents."""
+    import ctypes
+    specs = [((32, 32), 2000), ((16, 48), 1000), ((24, 24), 500)]
+    plans = [Plan(N, M, m=4, dtype=torch.float64, device=DEV) for N, M in specs]
+    for i, p in enumerate(plans[:2]):
+        p.set_nodes(to_dev(W.uniform_nodes(p.M, 2, seed_offset=1530 + i), torch.float64))
+    L, b = _lib_batch(plans)
+    stream = torch.cuda.current_stream(DEV)
+    assert L.nfft_batch_set_stream(b, ctypes.c_void_p(stream.cuda_stream)) == 0
+    fht = [to_dev(W.gaussian_fhat(p.N, 1540), torch.float64) for p in plans]
+    outs = [torch.full((p.M,), 7.0 + 0j, dtype=p.cdtype, device=DEV) for p in plans]
+    assert L.nfft_batch_trafo(b, _ptr_array(fht), _ptr_array(outs)) == 4  # NFFT_ENOTREADY
+    plans[2].set_nodes(to_dev(W.uniform_nodes(plans[2].M, 2, seed_offset=1532), torch.float64))
+    bad = ctypes.cast((ctypes.c_void_p * 3)(outs[0].data_ptr(), None, outs[2].data_ptr()),
+                      ctypes.c_void_p)
+    assert L.nfft_batch_trafo(b, _ptr_array(fht), bad) == 1  # NFFT_EINVAL
+    torch.cuda.synchronize()
+    for o in outs:
+        assert bool((o == 7.0).all())
+    assert L.nfft_batch_trafo(b, _ptr_array(fht), _ptr_array(outs)) == 0
+    torch.cuda.synchronize()
+    for p, fh, o in zip(plans, fht, outs):
+        assert rel_l2(o.cpu().numpy(), p.trafo(fh).cpu().numpy()) <= 1e-14
+        assert p.status() == 0
+    assert L.nfft_batch_destroy(b) == 0

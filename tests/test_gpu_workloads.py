@@ -192,3 +192,27 @@ def test_subproblem_sizes(dtype):
     for bad in (16, 33, 2048, -1):
         with pytest.raises(NfftError, match="NFFT_EINVAL"):
             plan.set_option("subproblem", bad)
+
+
+def test_method_option_ranges():
+    """NFFT_OPT_SPREAD_METHOD takes 0..6 and NFFT_OPT_INTERP_METHOD 0..4; other values are
+    rejected with NFFT_EINVAL and leave the plan usable."""
+    from paper_1810_09891_gb300 import _lib
+
+    L = _lib.lib()
+    plan = Plan((16, 16, 16), 100, m=4, dtype=torch.float32, device=DEV)
+    for v in range(0, 7):
+        assert L.nfft_set_option(plan._h, _lib.OPT_SPREAD_METHOD, v) == 0
+    for v in range(0, 5):
+        assert L.nfft_set_option(plan._h, _lib.OPT_INTERP_METHOD, v) == 0
+    einval = L.nfft_set_option(plan._h, _lib.OPT_SPREAD_METHOD, 7)
+    assert einval != 0
+    assert L.nfft_set_option(plan._h, _lib.OPT_SPREAD_METHOD, -1) == einval
+    assert L.nfft_set_option(plan._h, _lib.OPT_INTERP_METHOD, 5) == einval
+    assert _lib.SPREAD_METHODS["plane"] == 6 and _lib.INTERP_METHODS["octet"] == 4
+    x = W.uniform_nodes(100, 3, seed_offset=609)
+    fh = W.gaussian_fhat((16, 16, 16), 610)
+    plan.set_nodes(to_dev(x, torch.float32))
+    y = plan.trafo(to_dev(fh, torch.float32)).cpu().numpy()
+    assert rel_l2(y, oracle.nfft(rounded(x, torch.float32), rounded(fh, torch.float32),
+                                 n=plan.n, m=4)) <= TOL[torch.float32]
