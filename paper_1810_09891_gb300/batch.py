@@ -14,7 +14,6 @@ Section 3.1, Table tab:fttwflags). Every candidate computes the same transform u
 from __future__ import annotations
 
 import ctypes
-import itertools
 import json
 import os
 import statistics
