@@ -34,7 +34,14 @@
  * Errors: every function returns an nfft_status_code. Argument errors are detected on the host
  * before anything is enqueued. Errors found on the GPU (a node that is NaN or infinite) are
  * recorded in a device-side status word and reported by nfft_status() (which waits for the
- * stream).
+ * stream). For tests of the out-of-memory paths, the environment variable GBNFFT_FAIL_ALLOC
+ * makes the library refuse its own device allocations on the host, as if the device were out of
+ * memory (NFFT_ENOMEM): it names the allocation sites to refuse, comma-separated ("tables" in
+ * nfft_plan_create, "workspace" in nfft_set_nodes, "stage" in the _host calls, "lin" in
+ * NFFT_OPT_WINDOW_TABLE), or "all". It is read at every allocation.
+ *
+ * Tracing: every stage of every call is wrapped in an NVTX range named "gbnfft <stage>" (see
+ * enum nfft_stage), visible in any profiler that records NVTX.
  *
  * Threads: a plan is not thread-safe; distinct plans may be used from distinct threads.
  */
@@ -139,8 +146,9 @@ int nfft_status(nfft_plan plan);
  * largest first to the least-loaded lane, work ~ M_i + |I_n,i|; the plan's own stream is
  * restored afterwards) and joins the side streams back into the batch's stream, so later work
  * on that stream sees every result. The calls record into a CUDA graph as parallel branches.
- * Pointer arrays hold one device pointer per plan, with the layouts of nfft_trafo,
- * nfft_adjoint and nfft_grad_x. Every plan is checked (nodes set, pointers non-null and
+ * A plan may appear only once in a batch (a repeated plan gives NFFT_EINVAL: its two copies
+ * would run at once over one workspace). Pointer arrays hold one device pointer per plan, with
+ * the layouts of nfft_trafo, nfft_adjoint and nfft_grad_x. Every plan is checked (nodes set, pointers non-null and
  * aligned) before any work is enqueued; a failure returns NFFT_ENOTREADY or NFFT_EINVAL with
  * nothing enqueued. A CUDA error while enqueuing stops issuing the remaining plans, still joins
  * the side streams, and returns NFFT_ECUDA. The arrays are read during the call only. */
@@ -263,32 +271,37 @@ const char *nfft_strerror(int code);
  * next nfft_plan_create binds). */
 int nfft_use_device(int device);
 
-/* Forward 1-D NFFT in FP64 that allocates no device memory (the paper has no counterpart: its
- * library always allocates through its plan).
+/* Forward 1-D NFFT in FP64 that allocates no device memory. The paper has no counterpart: its
+ * library always allocates through its plan.
  *
- * For callers that must not call cudaMalloc where they transform: code running while a CUDA
- * graph is captured, code whose device memory belongs to another allocator, and latency-bound
- * loops that cannot take the device synchronisation that cudaMalloc / cudaFree imply. The
- * planned path cannot serve them, because nfft_plan_create and nfft_set_nodes allocate.
+ * For callers that cannot call cudaMalloc where they transform: code whose device memory is
+ * owned by another allocator (a framework's caching pool or a host application's memory budget
+ * that forbids raw allocations), and latency-bound loops that cannot take the device
+ * synchronisation that cudaMalloc / cudaFree imply. The planned path cannot serve them, because
+ * nfft_plan_create and nfft_set_nodes allocate.
  *
- * Computes f_j ~ sum_{k=-N/2}^{N/2-1} fhat_k e^{-2 pi i k x_j} (Algorithm "NFFT", d = 1), the
- * same transform as nfft_trafo on a 1-D NFFT_FP64 plan with the same N, n, m, up to rounding.
+ * Computes f_j ~ sum_{k=-N/2}^{N/2-1} fhat_k e^{-2 pi i k x_j}, the same transform as nfft_trafo
+ * on a 1-D NFFT_FP64 plan with the same N, n, m (Kaiser-Bessel window), up to rounding.
  *   N       even bandwidth, 2 <= N <= 4096.
  *   M       number of nodes, 0 <= M < 2^31.
  *   n       pointer to the FFT length (power of two, N < n <= 8192, 2m + 2 <= n), or NULL for
  *           the default 2^(ceil(log2 N) + 1).
  *   m       window cutoff 1..8 (<= 0 selects 8).
- *   x       M node coordinates (device, FP64, any finite real, taken mod 1).
+ *   x       M node coordinates (device, FP64), taken mod 1; |x_j| must be below 2^52 / n, and
+ *           a node that is not finite or not below that bound gives NaN in f_j.
  *   fhat    N complex128 coefficients, index k + N/2 (device, 16-byte aligned).
- *   f       M complex128 outputs (device, 16-byte aligned); a non-finite node gives NaN.
+ *   f       M complex128 outputs (device, 16-byte aligned).
  *   stream  cudaStream_t to enqueue on (NULL = legacy default stream).
  * Scratch: a fixed 288 KiB array in device memory inside the library, held by every GPU that
  * loads the library until the process exits. Sizes beyond it (n > 8192 or N > 4096) return
  * NFFT_ESCRATCH. Nothing in it has to start at zero: each call rewrites what it reads. All calls
  * share the array: calls that overlap on the GPU (other streams, other threads) race and give
  * wrong results, so serialise them.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture begins. Returns without waiting for the GPU. */
+ * Set-up: the first call on a device looks up the array's device address there
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that first call before
+ * any stream capture begins. The kept address does not survive cudaDeviceReset (or any other
+ * destruction of the device's primary context): do not call this entry point after one.
+ * Returns without waiting for the GPU. */
 int nfft_trafo_1d_noalloc(int64_t N, int64_t M, const int64_t *n, int m, const double *x,
                           const void *fhat, void *f, void *stream);
 

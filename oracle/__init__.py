@@ -63,6 +63,9 @@ def _load():
         sigs = {
             "ora_version": ([], Int),
             "ora_max_threads": ([], Int),
+            "ora_set_threads": ([Int], Int),
+            "ora_ndft_tab": ([Int, P, I64, P, P, P], None),
+            "ora_ndft_adjoint_at": ([Int, P, I64, P, P, I64, P, P], None),
             "ora_ndft": ([Int, P, I64, P, P, P], None),
             "ora_ndft_adjoint": ([Int, P, I64, P, P, P], None),
             "ora_ndft_grad": ([Int, P, I64, P, P, P], None),
@@ -222,6 +225,41 @@ def ndft_adjoint(x, f, N) -> np.ndarray:
     out = np.zeros(N, dtype=np.complex128)
     _load().ora_ndft_adjoint(d, _p(_i64(N)), x.shape[0], _p(x), _p(f), _p(out))
     return out
+
+
+def ndft_tab(x, fhat) -> np.ndarray:
+    """The NDFT of Section 1 (eq. NDFT) with every term's exponential formed from its per-axis
+    factors e^{-2 pi i k_t x_t} (a node's factors are computed once): the same sum as ``ndft``,
+    much faster for large |I_N|."""
+    fhat = _c128(fhat)
+    d = fhat.ndim
+    N = _i64(fhat.shape)
+    x = _nodes(x, d)
+    M = x.shape[0]
+    f = np.zeros(M, dtype=np.complex128)
+    _load().ora_ndft_tab(d, _p(N), M, _p(x), _p(fhat), _p(f))
+    return f
+
+
+def ndft_adjoint_at(x, f, N, kidx) -> np.ndarray:
+    """The adjoint NDFT (Section 1) at selected coefficients: sum_j f_j exp(+2 pi i k.x_j) for
+    the multi-indices k at row-major positions ``kidx`` of I_N (axis t at k_t + N_t/2)."""
+    N = tuple(int(v) for v in N)
+    d = len(N)
+    x = _nodes(x, d)
+    f = _c128(f).reshape(-1)
+    kidx = _i64(kidx)
+    if kidx.size and (kidx.min() < 0 or kidx.max() >= int(np.prod(N))):
+        raise ValueError("kidx outside I_N")
+    out = np.zeros(kidx.size, dtype=np.complex128)
+    _load().ora_ndft_adjoint_at(d, _p(_i64(N)), x.shape[0], _p(x), _p(f), kidx.size, _p(kidx),
+                                _p(out))
+    return out
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads of later oracle calls; returns the number in effect."""
+    return int(_load().ora_set_threads(int(n)))
 
 
 def ndft_grad(x, fhat) -> np.ndarray:

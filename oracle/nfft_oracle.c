@@ -52,6 +52,18 @@ int ora_max_threads(void)
 #endif
 }
 
+/* Number of OpenMP threads for later calls (n >= 1); returns the number in effect. */
+int ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Small helpers                                                                              */
 /* ------------------------------------------------------------------------------------------ */
@@ -128,6 +140,110 @@ void ora_ndft_adjoint(int d, const int64_t *N, int64_t M, const double *x, const
         }
         fhat[idx] = acc;
     }
+}
+
+/* The one-dimensional factors of the NDFT's exponential on every axis of one node: since
+ * e^{sign 2 pi i k.x} = prod_t e^{sign 2 pi i k_t x_t}, row t of E (N_t values, position
+ * k_t + N_t/2) holds e^{sign 2 pi i k_t x_t}, each evaluated with the exact phase reduction. */
+static void axis_factors(int d, const int64_t *N, const double *xj, int sign, cplx *E)
+{
+    int64_t off = 0;
+    for (int t = 0; t < d; t++) {
+        for (int64_t i = 0; i < N[t]; i++) {
+            double ph = 2.0 * ORA_PI * reduced_product(i - N[t] / 2, xj[t]);
+            E[off + i] = cos(ph) + sign * I * sin(ph);
+        }
+        off += N[t];
+    }
+}
+
+/* The NDFT of Section 1 (eq. NDFT), f_j = sum_{k in I_N} fhat_k e^{-2 pi i k.x_j}, with each
+ * term's exponential formed as the product of its per-axis factors (axis_factors) instead of
+ * one cosine and sine of the summed phase. Same sum in the same order as ora_ndft; only the
+ * rounding of the exponentials differs. */
+void ora_ndft_tab(int d, const int64_t *N, int64_t M, const double *x, const cplx *fhat,
+                  cplx *f)
+{
+    const int64_t nk = prod64(d, N);
+    int64_t tot = 0;
+    for (int t = 0; t < d; t++) tot += N[t];
+#pragma omp parallel
+    {
+        cplx *E = (cplx *)malloc((size_t)tot * sizeof(cplx));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t j = 0; j < M; j++) {
+            axis_factors(d, N, x + j * d, -1, E);
+            cplx acc = 0;
+            for (int64_t idx = 0; idx < nk; idx++) {
+                int64_t rem = idx, off = 0, kk[3] = {0, 0, 0};
+                for (int t = d - 1; t >= 0; t--) {
+                    kk[t] = rem % N[t];
+                    rem /= N[t];
+                }
+                cplx e = 1.0;
+                for (int t = 0; t < d; t++) {
+                    e *= E[off + kk[t]];
+                    off += N[t];
+                }
+                acc += fhat[idx] * e;
+            }
+            f[j] = acc;
+        }
+        free(E);
+    }
+}
+
+/* The adjoint NDFT of Section 1 at the K listed coefficients only:
+ * out[q] = sum_{j=0}^{M-1} f_j e^{+2 pi i k.x_j}, k the multi-index at row-major position
+ * kidx[q] of I_N (axis t at k_t + N_t/2). Exponentials as in ora_ndft_tab. The sum over j is
+ * split into contiguous node ranges, one per thread, whose partial sums are added in range
+ * order (the same sum as ora_ndft_adjoint up to rounding order). */
+void ora_ndft_adjoint_at(int d, const int64_t *N, int64_t M, const double *x, const cplx *f,
+                         int64_t K, const int64_t *kidx, cplx *out)
+{
+    int64_t tot = 0;
+    for (int t = 0; t < d; t++) tot += N[t];
+    int64_t *pos = (int64_t *)malloc((size_t)(K > 0 ? K : 1) * 3 * sizeof(int64_t));
+    for (int64_t q = 0; q < K; q++) {
+        int64_t rem = kidx[q], off = tot;
+        for (int t = d - 1; t >= 0; t--) {
+            off -= N[t];
+            pos[q * 3 + t] = off + rem % N[t];  /* position of k_t's factor in E */
+            rem /= N[t];
+        }
+    }
+    int nth = 1;
+#ifdef _OPENMP
+    nth = omp_get_max_threads();
+#endif
+    cplx *part = (cplx *)calloc((size_t)nth * (size_t)(K > 0 ? K : 1), sizeof(cplx));
+#pragma omp parallel num_threads(nth)
+    {
+        int me = 0, nt = 1;
+#ifdef _OPENMP
+        me = omp_get_thread_num();
+        nt = omp_get_num_threads();
+#endif
+        const int64_t j0 = M * me / nt, j1 = M * (me + 1) / nt;
+        cplx *E = (cplx *)malloc((size_t)tot * sizeof(cplx));
+        cplx *acc = part + (size_t)me * (size_t)K;
+        for (int64_t j = j0; j < j1; j++) {
+            axis_factors(d, N, x + j * d, +1, E);
+            for (int64_t q = 0; q < K; q++) {
+                cplx e = 1.0;
+                for (int t = 0; t < d; t++) e *= E[pos[q * 3 + t]];
+                acc[q] += f[j] * e;
+            }
+        }
+        free(E);
+    }
+    for (int64_t q = 0; q < K; q++) {
+        cplx s = 0;
+        for (int r = 0; r < nth; r++) s += part[(size_t)r * (size_t)K + q];
+        out[q] = s;
+    }
+    free(part);
+    free(pos);
 }
 
 /* Partial derivatives of the trigonometric polynomial (Section 2, eq. trigpoly):
@@ -513,7 +629,10 @@ void ora_nfft_B_w(int w, int d, const int64_t *N, const int64_t *n, int m, int64
 }
 
 /* Step B^H (Algorithm "adjoint NFFT", first loop):
- * g_l = sum_{j in I^T_{n,m}(l)} f_j psi~(x_j - l/n); evaluated node by node. */
+ * g_l = sum_{j in I^T_{n,m}(l)} f_j psi~(x_j - l/n); evaluated node by node. The grid is split
+ * into slabs of consecutive indices l_0 on the first axis, one slab per thread; every thread
+ * visits all nodes in order and adds only the taps in its own slab, so every g_l receives its
+ * terms in node order, exactly as a single thread would add them. */
 void ora_nfft_BH_w(int w, int d, const int64_t *N, const int64_t *n, int m, int64_t M,
                   const double *x,
                  const cplx *f, cplx *g)
@@ -521,26 +640,44 @@ void ora_nfft_BH_w(int w, int d, const int64_t *N, const int64_t *n, int m, int6
     double b[3] = {0, 0, 0};
     for (int t = 0; t < d; t++) b[t] = ora_window_param(w, n[t], N[t], m);
     memset(g, 0, (size_t)prod64(d, n) * sizeof(cplx));
-    for (int64_t j = 0; j < M; j++) {
-        double nx[3];
-        int64_t lo[3], hi[3], l[3];
-        support_box(d, n, m, x + j * d, nx, lo, hi);
-        for (int t = 0; t < d; t++) l[t] = lo[t];
-        for (;;) {
-            double wt = 1.0;
-            int64_t gi = 0;
-            for (int t = 0; t < d; t++) {
-                wt *= ora_window_psi_eval(w, nx[t] - (double)l[t], m, b[t]);
-                gi = gi * n[t] + mod64(l[t], n[t]);
+#pragma omp parallel
+    {
+        int me = 0, nt = 1;
+#ifdef _OPENMP
+        me = omp_get_thread_num();
+        nt = omp_get_num_threads();
+#endif
+        const int64_t s0 = n[0] * me / nt, s1 = n[0] * (me + 1) / nt;  /* rows [s0, s1) */
+        for (int64_t j = 0; j < M; j++) {
+            double nx[3];
+            int64_t lo[3], hi[3], l[3];
+            support_box(d, n, m, x + j * d, nx, lo, hi);
+            int mine = 0;
+            for (int64_t l0 = lo[0]; l0 <= hi[0]; l0++) {
+                const int64_t r = mod64(l0, n[0]);
+                if (r >= s0 && r < s1) mine = 1;
             }
-            g[gi] += f[j] * wt;
-            int t = d - 1;
-            while (t >= 0 && l[t] == hi[t]) {
-                l[t] = lo[t];
-                t--;
+            if (!mine) continue;
+            for (int t = 0; t < d; t++) l[t] = lo[t];
+            for (;;) {
+                const int64_t r0 = mod64(l[0], n[0]);
+                if (r0 >= s0 && r0 < s1) {
+                    double wt = 1.0;
+                    int64_t gi = 0;
+                    for (int t = 0; t < d; t++) {
+                        wt *= ora_window_psi_eval(w, nx[t] - (double)l[t], m, b[t]);
+                        gi = gi * n[t] + mod64(l[t], n[t]);
+                    }
+                    g[gi] += f[j] * wt;
+                }
+                int t = d - 1;
+                while (t >= 0 && l[t] == hi[t]) {
+                    l[t] = lo[t];
+                    t--;
+                }
+                if (t < 0) break;
+                l[t]++;
             }
-            if (t < 0) break;
-            l[t]++;
         }
     }
 }

@@ -1,9 +1,8 @@
 // A forward 1-D NFFT that allocates no device memory at all: nfft_trafo_1d_noalloc.
 //
-// Who needs it: code that may not call cudaMalloc at the point where it transforms. That
-// includes code running while a CUDA graph is being captured (allocation is not a stream
-// operation and is refused or unsafe during capture). It includes code whose device memory is
-// owned by another allocator that forbids raw allocations. It includes latency-bound loops
+// Who needs it: code that cannot call cudaMalloc at the point where it transforms. That
+// includes code whose device memory is owned by another allocator (a framework's caching pool,
+// or a host application's memory budget) that forbids raw allocations, and latency-bound loops
 // that cannot afford the implicit device synchronisation of cudaMalloc / cudaFree. The planned
 // path (nfft_plan_create, nfft_set_nodes) allocates tables and a workspace, so those callers
 // cannot use it there.
@@ -19,8 +18,10 @@
 // overlap on the GPU (different streams, or different host threads) race on the array and give
 // wrong results: serialise them.
 //
-// Method: the same three steps as nfft_trafo (Algorithm "NFFT": D, F, B), FP64, Kaiser-Bessel
-// window evaluated directly from its formula, nodes processed in the caller's order (no sort).
+// Method: the same three steps as nfft_trafo (deconvolution, FFT, window interpolation), FP64,
+// Kaiser-Bessel window evaluated directly from its formula, nodes processed in the caller's order
+// (no sort). The device address of the array is looked up once per device and kept for the life
+// of the process, so it does not survive cudaDeviceReset.
 #include <cmath>
 #include <mutex>
 
@@ -44,7 +45,8 @@ constexpr size_t kScratchBytes = kDcOff + sizeof(double) * kNoallocMaxN;  // 288
 // must use the address from cudaGetSymbolAddress (see scratch_address), never the name itself.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of g_noalloc_scratch on the current device, looked up once per device.
+// Device address of g_noalloc_scratch on the current device, looked up once per device (with
+// that device current) and kept for the life of the process.
 int scratch_address(int dev, unsigned char **out)
 {
     static std::mutex mu;

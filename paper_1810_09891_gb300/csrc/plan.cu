@@ -10,6 +10,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbnfft_internal.cuh"
 
 using namespace gbnfft;
@@ -193,6 +195,33 @@ struct Region {
     size_t off = 0, bytes = 0;
 };
 
+// Every device allocation of the library goes through here. Failure injection for tests (host
+// side only, nothing reaches the GPU): when the environment variable GBNFFT_FAIL_ALLOC names this
+// allocation's site ("tables", "workspace", "stage", "lin"; a comma-separated list, or "all"),
+// the allocation is refused as if the device were out of memory.
+bool alloc_refused(const char *site)
+{
+    const char *v = std::getenv("GBNFFT_FAIL_ALLOC");
+    if (!v || !*v) return false;
+    if (std::strcmp(v, "all") == 0) return true;
+    const size_t n = std::strlen(site);
+    for (const char *q = v; *q;) {
+        const char *e = std::strchr(q, ',');
+        const size_t len = e ? size_t(e - q) : std::strlen(q);
+        if (len == n && std::strncmp(q, site, n) == 0) return true;
+        if (!e) break;
+        q = e + 1;
+    }
+    return false;
+}
+
+cudaError_t dev_alloc(void **ptr, size_t bytes, const char *site)
+{
+    *ptr = nullptr;
+    if (alloc_refused(site)) return cudaErrorMemoryAllocation;
+    return cudaMalloc(ptr, bytes);
+}
+
 }  // namespace
 
 struct gbnfft_plan {
@@ -350,7 +379,7 @@ int ensure_workspace(gbnfft_plan *p)
 {
     if (p->ws) return NFFT_OK;
     void *ptr = nullptr;
-    cudaError_t e = cudaMalloc(&ptr, p->ws_need);
+    cudaError_t e = dev_alloc(&ptr, p->ws_need, "workspace");
     if (e != cudaSuccess) {
         cudaGetLastError();
         return NFFT_ENOMEM;
@@ -385,11 +414,24 @@ void prof_end(gbnfft_plan *p, int idx)
     if (idx >= 0) cudaEventRecord(p->prof[idx].b, p->stream);
 }
 
+// Names of the stages for NVTX ranges (one range per stage and call, on the calling thread;
+// a profiler that records NVTX shows them around the stage's launches).
+const char *const kStageName[NFFT_NUM_STAGES] = {
+    "gbnfft set_nodes", "gbnfft fft_forward", "gbnfft interp", "gbnfft zero_grid",
+    "gbnfft spread",    "gbnfft fft_adjoint", "gbnfft grad"};
+
 struct ProfScope {
     gbnfft_plan *p;
     int idx;
-    ProfScope(gbnfft_plan *pp, int stage) : p(pp), idx(prof_begin(pp, stage)) {}
-    ~ProfScope() { prof_end(p, idx); }
+    ProfScope(gbnfft_plan *pp, int stage) : p(pp), idx(prof_begin(pp, stage))
+    {
+        nvtxRangePushA(kStageName[stage]);
+    }
+    ~ProfScope()
+    {
+        prof_end(p, idx);
+        nvtxRangePop();
+    }
 };
 
 // One axis pass of the oversampled FFT along axis t: the power-of-two kernels, or Bluestein
@@ -657,7 +699,7 @@ static int build_lin_tables(gbnfft_plan *p)
         hf.assign(h.begin(), h.end());
         src = hf.data();
     }
-    cudaError_t e = cudaMalloc(&p->lin_tab, bytes);
+    cudaError_t e = dev_alloc(&p->lin_tab, bytes, "lin");
     if (e == cudaSuccess) e = cudaMemcpy(p->lin_tab, src, bytes, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -908,7 +950,7 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
     }
     fill_tables(p, host);
     keep_poly_host(p, host);
-    cudaError_t e = cudaMalloc(&p->tables, tbytes);
+    cudaError_t e = dev_alloc(&p->tables, tbytes, "tables");
     if (e == cudaSuccess) e = cudaMemcpy(p->tables, host, tbytes, cudaMemcpyHostToDevice);
     std::free(host);
     if (e != cudaSuccess) {
@@ -1199,7 +1241,7 @@ static int ensure_stage(gbnfft_plan *p)
     if (p->stage && p->stage_bytes >= need) return NFFT_OK;
     if (p->stage) cudaFree(p->stage);
     p->stage = nullptr;
-    if (cudaMalloc(&p->stage, need) != cudaSuccess) {
+    if (dev_alloc(&p->stage, need, "stage") != cudaSuccess) {
         cudaGetLastError();
         p->stage_bytes = 0;
         return NFFT_ENOMEM;
@@ -1341,6 +1383,12 @@ int nfft_batch_create(nfft_batch *out, const nfft_plan *plans, int count, int st
     for (int i = 0; i < count; i++) {
         if (!plans[i]) return NFFT_EINVAL;
         if (plans[i]->device != plans[0]->device) return NFFT_EINVAL;
+    }
+    // a plan listed twice would run on two side streams at once over one workspace
+    {
+        std::vector<const gbnfft_plan *> sorted(plans, plans + count);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) return NFFT_EINVAL;
     }
     if (streams <= 0) streams = 8;
     if (streams > count) streams = count;

@@ -50,6 +50,26 @@ def test_paper_window_errors(d):
             assert e2 <= 5 * ref, (d, m, e2, ref)
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_paper_window_errors_einf(d):
+    """E_inf of the oracle NFFT on the paper's polynomial f_d tracks the printed curve of
+    Fig. window_size_error (b): within a factor 1/4..5 of each printed value for m = 2..7 and
+    at most 5x the printed value at m = 8 (rounding floor)."""
+    gold = _golden()
+    wl = gold["workloads"][str(d)]
+    N = tuple(wl["N"])
+    fh = W.paper_fhat(N)
+    x = W.uniform_nodes(wl["M"], d, seed_offset=50 + d)[:4096]
+    f_exact = oracle.ndft(x, fh)
+    for m in ([2, 3, 4, 5, 6, 7, 8] if d < 3 else [2, 4, 6, 8]):
+        einf = oracle.error_Einf(f_exact, oracle.nfft(x, fh, m=m), fh)
+        ref = gold["Einf"][str(d)][str(m)]
+        if m < 8:
+            assert ref / 4 <= einf <= 5 * ref, (d, m, einf, ref)
+        else:
+            assert einf <= 5 * ref, (d, m, einf, ref)
+
+
 def test_paper_table_einf_m8():
     gold = _golden()["Einf_table_m8"]
     for d, N, M in [(1, (512,), 1024), (2, (128, 128), 32768)]:

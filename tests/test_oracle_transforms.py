@@ -125,3 +125,68 @@ def test_ndft_grad_matches_finite_difference(N):
         e[t] = h
         fd = (oracle.ndft(x + e, fh) - oracle.ndft(x - e, fh)) / (2 * h)
         assert np.max(np.abs(df[:, t] - fd)) <= 1e-7 * np.max(np.abs(df[:, t]))
+
+
+# ---------------------------------------------------------------- the faster direct sums
+# ndft_tab and ndft_adjoint_at evaluate the same sums as ndft / ndft_adjoint with each term's
+# exponential built from per-axis factors; they are what the GPU is checked against at full size.
+
+@pytest.mark.parametrize("N", [(2,), (16,), (30,), (8, 6), (12, 10), (4, 6, 8), (6, 4, 10)])
+def test_ndft_tab_closed_forms_and_direct_sum(N):
+    d = len(N)
+    x = W.uniform_nodes(60, d, 40) * 7.0  # nodes far outside the torus too
+    g = np.random.default_rng(41)
+    # single coefficient: a pure exponential
+    k = [int(g.integers(-v // 2, v // 2)) for v in N]
+    fh = np.zeros(N, dtype=complex)
+    fh[tuple(kk + v // 2 for kk, v in zip(k, N))] = 1.0
+    want = np.exp(-2j * np.pi * (x @ np.array(k, dtype=float)))
+    assert np.max(np.abs(oracle.ndft_tab(x, fh) - want)) < 1e-13
+    # x = 0 with fhat = 1 sums to |I_N|
+    assert abs(oracle.ndft_tab(np.zeros((1, d)), np.ones(N))[0] - np.prod(N)) < 1e-12
+    # a random polynomial: the plain direct sum
+    fh = g.standard_normal(N) + 1j * g.standard_normal(N)
+    ref = oracle.ndft(x, fh)
+    assert np.max(np.abs(oracle.ndft_tab(x, fh) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("N", [(16,), (10, 8), (4, 6, 8)])
+def test_ndft_adjoint_at_closed_form_and_direct_sum(N):
+    d = len(N)
+    g = np.random.default_rng(42)
+    nk = int(np.prod(N))
+    kidx = np.concatenate([[0, nk - 1], g.choice(nk, 9, replace=False)])
+    # one node: hhat_k = f_j e^{+2 pi i k.x_j}
+    x1 = W.uniform_nodes(1, d, 43)
+    ks = np.stack(np.unravel_index(kidx, N), axis=1) - np.array(N) // 2
+    want = (0.3 + 0.9j) * np.exp(2j * np.pi * (ks @ x1[0]))
+    got = oracle.ndft_adjoint_at(x1, np.array([0.3 + 0.9j]), N, kidx)
+    assert np.max(np.abs(got - want)) < 1e-14
+    # many nodes (more than threads, ragged split): the plain adjoint sum at those indices
+    x = W.uniform_nodes(1003, d, 44)
+    f = g.standard_normal(1003) + 1j * g.standard_normal(1003)
+    ref = oracle.ndft_adjoint(x, f, N).reshape(-1)[kidx]
+    got = oracle.ndft_adjoint_at(x, f, N, kidx)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    with pytest.raises(ValueError):
+        oracle.ndft_adjoint_at(x, f, N, [nk])
+
+
+@pytest.mark.parametrize("N,n,m", [((16, 12), (32, 32), 3), ((8, 6, 10), (16, 16, 32), 2),
+                                   ((40,), (128,), 5)])
+def test_spreading_is_the_same_with_any_thread_count(N, n, m):
+    """The oracle's B^H splits the grid into per-thread slabs; every grid value still receives
+    its terms in node order, so any thread count gives the same bits."""
+    d = len(N)
+    x = W.uniform_nodes(3001, d, 45)
+    x[:40] = 0.0  # coincident nodes on a grid point
+    f = W.gaussian_values(3001, 46)
+    keep = oracle.max_threads()
+    try:
+        oracle.set_threads(1)
+        one = oracle.nfft_BH(x, f, N, n, m)
+        oracle.set_threads(5)
+        five = oracle.nfft_BH(x, f, N, n, m)
+    finally:
+        oracle.set_threads(keep)
+    assert np.array_equal(one, five)

@@ -1,11 +1,12 @@
 """The no-allocation entry point nfft_trafo_1d_noalloc, called through the C ABI.
 
-It is meant for callers that may not allocate device memory where they transform (inside a
-CUDA graph capture, under a foreign allocator, or in loops that cannot take the synchronisation
-of cudaMalloc). This test checks that it gives the same result as the planned nfft_trafo, within
-the FP64 tolerance of the other parity tests, on two calls in a row with different sizes (the
-second call runs on scratch the first one left behind), and that sizes beyond its fixed scratch
-are refused. This file is collected last on purpose.
+It is meant for callers that cannot allocate device memory where they transform: their device
+memory belongs to another allocator, or they run latency-bound loops that cannot take the
+synchronisation of cudaMalloc / cudaFree. This test checks that it gives the same result as the
+planned nfft_trafo, within the FP64 tolerance of the other parity tests, on calls in a row with
+different sizes (the largest size its scratch allows first, so that the later calls run on scratch
+an earlier call left behind), and that sizes beyond its fixed scratch are refused. This file is
+collected last on purpose.
 """
 import ctypes
 
@@ -39,7 +40,8 @@ def _noalloc(lib, N, x, fh, m, n=None):
 def test_noalloc_matches_planned_forward_on_two_calls():
     torch.cuda.set_device(DEV)
     lib = _lib.lib()
-    cases = [(512, 5000, 8, None, 70), (96, 1234, 4, 256, 71)]  # large first, then smaller
+    # the largest size the scratch holds (n = 8192, N = 4096) first, then smaller ones
+    cases = [(4096, 2000, 8, 8192, 69), (512, 5000, 8, None, 70), (96, 1234, 4, 256, 71)]
     for N, M, m, n, seed in cases:
         x = torch.tensor(W.uniform_nodes(M, 1, seed_offset=seed).reshape(-1), device=DEV)
         fh = torch.tensor(W.gaussian_fhat((N,), seed_offset=seed + 1), device=DEV)
