@@ -55,6 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-variants", action="store_true", help="skip the FP64 / m=6 variants")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed CPU oracle")
     ap.add_argument("--no-parity", action="store_true", help="skip the oracle error check")
+    ap.add_argument("--no-subrecords", action="store_true",
+                    help="skip the clustered 3-D and batched sub-records")
     ap.add_argument("--ncu-step", action="store_true",
                     help="only build the workload's plan and run --steps untimed forward + adjoint "
                          "pairs (a short program for ncu captures of the timed kernels)")
@@ -209,7 +211,8 @@ def alu_roofline(d, m, fp64, M, stages, clk):
     deg = POLY_DEG[fp64].get(m, 14 if fp64 else 8)
     flops = 2.0 * (d * m * (deg + 2) + 2 * (2 * m) ** d) * M
     peak = NUM_SMS * 128 * 2 * _clock_ghz(clk) * 1e9 / (64.0 if fp64 else 1.0)
-    out = {"flops_per_node": flops / M, "peak_tflops": peak / 1e12}
+    out = {"flops_per_node": flops / M, "peak_tflops": peak / 1e12,
+           "peak_kind": "nominal (FMA lanes x clock; FP64 at 1/64 of FP32), not measured"}
     for st in ("interp", "spread"):
         if st in stages:
             t = stages[st]["ms_per_launch"] * 1e-3
@@ -371,6 +374,45 @@ def reference_arm(args):
 
 # ------------------------------------------------------------------------------ GPU arm
 
+KERNEL_STAGES = ("fft_forward", "interp", "spread", "fft_adjoint")
+
+
+def profile_stages(plan, fh, f, steps, flush, torch):
+    """Per-stage milliseconds per launch from the library's own CUDA events (nfft_profile) over
+    `steps` forward + adjoint steps with the L2 flushed between steps."""
+    import ctypes
+
+    from paper_1810_09891_gb300 import _lib
+    L = _lib.lib()
+    L.nfft_profile(plan._h, 1)
+    run_variant(plan, fh, f, steps, flush, torch)
+    ms = (ctypes.c_double * 7)()
+    cnt = (ctypes.c_int64 * 7)()
+    L.nfft_profile_read(plan._h, ms, cnt, 7)
+    L.nfft_profile(plan._h, 0)
+    return {name: {"ms_per_launch": ms[i] / cnt[i], "launches": int(cnt[i])}
+            for i, name in enumerate(_lib.STAGES) if cnt[i]}
+
+
+def roofline_of(stages, wl, M, p, peak, peak_kind, workload_name=None):
+    """HBM roofline of the step's dominant kernel: its algorithmic bytes per launch over its
+    event time, against the measured copy bandwidth. Adds bytes, GB/s and share to `stages`."""
+    d = len(wl["N"])
+    ks = {k: v for k, v in stages.items() if k in KERNEL_STAGES}
+    step_ms = sum(v["ms_per_launch"] for v in ks.values())
+    for k, v in stages.items():
+        b = algorithmic_bytes(k, d, wl["N"], wl["n"], M, p)
+        v["algorithmic_bytes"] = b
+        v["GBps"] = b / (v["ms_per_launch"] * 1e-3) / 1e9 if b else None
+        v["share"] = v["ms_per_launch"] / step_ms if k in ks else None
+    dom = max(ks, key=lambda k: ks[k]["ms_per_launch"])
+    achieved = stages[dom]["GBps"]
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": profiled_traffic(dom, workload_name) if workload_name else None,
+            "peak_kind": peak_kind}
+
+
 def run_variant(plan, fh, f, steps, flush, torch):
     """Times `steps` steps (forward + adjoint) with an L2 flush between steps outside the timed
     events; returns per-step forward / adjoint / total milliseconds."""
@@ -396,7 +438,7 @@ def run_variant(plan, fh, f, steps, flush, torch):
 _NDFT_CACHE = {}
 
 
-def parity(wl, y, h, m, n, sample=4096, seed=1):
+def parity(wl, y, h, m, n, sample=4096, seed=1, full_adjoint=True):
     """Errors of the GPU outputs on the same (rounded) inputs:
     against the FP64 oracle NFFT (rel. l2; forward on a seeded node sample, adjoint over all
     coefficients, spreading all M nodes), and against the direct NDFT, the exact transform
@@ -411,7 +453,7 @@ def parity(wl, y, h, m, n, sample=4096, seed=1):
     nk = int(np.prod(wl["N"]))
     kidx = np.sort(g.choice(nk, min(sample, nk), replace=False))
     ref_f = oracle.nfft(x[idx], wl["fhat_r"], n=n, m=m)
-    ref_h = oracle.nfft_adjoint(x, wl["f_r"], wl["N"], n=n, m=m)
+    ref_h = oracle.nfft_adjoint(x, wl["f_r"], wl["N"], n=n, m=m) if full_adjoint else None
     key = (wl["name"], str(wl["x"].dtype), sample, seed)
     if key not in _NDFT_CACHE:  # the exact transform does not depend on m
         _NDFT_CACHE[key] = (oracle.ndft_tab(x[idx], wl["fhat_r"]),
@@ -419,13 +461,69 @@ def parity(wl, y, h, m, n, sample=4096, seed=1):
     nd_f, nd_h = _NDFT_CACHE[key]
     hs = np.asarray(h).reshape(-1)[kidx]
     return {"fwd_rel_l2_vs_oracle_nfft": rel_l2(y[idx], ref_f),
-            "adj_rel_l2_vs_oracle_nfft": rel_l2(h, ref_h),
+            "adj_rel_l2_vs_oracle_nfft": rel_l2(h, ref_h) if full_adjoint else None,
             "fwd_rel_l2_vs_ndft": rel_l2(y[idx], nd_f),
             "adj_rel_l2_vs_ndft": rel_l2(hs, nd_h),
             "fwd_einf_vs_ndft": float(np.max(np.abs(y[idx] - nd_f)) /
                                       np.sum(np.abs(wl["fhat_r"]))),
             "adj_einf_vs_ndft": float(np.max(np.abs(hs - nd_h)) / np.sum(np.abs(wl["f_r"]))),
             "sample_nodes": int(idx.size), "sample_coefficients": int(kidx.size)}
+
+
+def timed_steps(plan, fh, f, steps, warmup, flush, uuid, torch):
+    """Warm-up, then `steps` timed forward + adjoint steps with the SM clocks sampled during the
+    timed region; returns (forward ms, adjoint ms, outputs, clocks)."""
+    run_variant(plan, fh, f, max(3, warmup), flush, torch)
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    run_variant(plan, fh, f, 20, flush, torch)  # keeps the GPU busy while the sampler starts
+    torch.cuda.synchronize()
+    t0 = time.time()
+    fwd, adj, outs = run_variant(plan, fh, f, steps, flush, torch)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    return fwd, adj, outs, clocks.stop(t0, t1)
+
+
+def clusters_record(args, flush, dev, hbm_peak, peak_kind, uuid, torch):
+    """The 3-D clustered workload: N = (128,)*3, n = 2N, m = 4, M = 4,194,304 nodes (half
+    uniform, half in 8 Gaussian clusters), FP32; forward + adjoint per step."""
+    from paper_1810_09891_gb300.nfft import Plan
+    wl = workload("clusters", 4, np.float32)
+    wl["fhat_r"] = wl["fhat"].astype(np.complex64).astype(np.complex128)
+    wl["f_r"] = wl["f"].astype(np.complex64).astype(np.complex128)
+    M = wl["x"].shape[0]
+    plan = Plan(wl["N"], M, n=wl["n"], m=4, dtype=torch.float32, device=dev)
+    x = torch.tensor(wl["x"], device=dev)
+    fh = torch.tensor(wl["fhat"].astype(np.complex64), device=dev)
+    f = torch.tensor(wl["f"].astype(np.complex64), device=dev)
+    plan.set_nodes(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.set_nodes(x)
+    e1.record()
+    torch.cuda.synchronize()
+    set_nodes_ms = e0.elapsed_time(e1)
+    steps = max(5, min(args.steps, 20))
+    fwd, adj, (y, h), clk = timed_steps(plan, fh, f, steps, args.warmup, flush, uuid, torch)
+    if plan.status() != 0:
+        raise RuntimeError("device status after the clustered workload")
+    stages = profile_stages(plan, fh, f, 5, flush, torch)
+    roof = roofline_of(stages, wl, M, 4, hbm_peak, peak_kind, wl["name"])
+    total = sum(fwd) + sum(adj)
+    rec = {"workload": wl["name"], "N": list(wl["N"]), "n": list(wl["n"]), "m": 4, "M": M,
+           "dtype": "f32", "steps": steps, "ms_per_step": total / steps,
+           "value": M * steps / (total * 1e-3), "unit": UNIT,
+           "fwd_nodes_per_s": M * steps / (sum(fwd) * 1e-3),
+           "adj_nodes_per_s": M * steps / (sum(adj) * 1e-3), "set_nodes_ms": set_nodes_ms,
+           "roofline": roof, "stages_us": {k: 1e3 * v["ms_per_launch"] for k, v in stages.items()},
+           "clocks": clk,
+           "l2": "inputs larger than L2 (grid 134 MB, nodes 84 MB); flushed between steps too"}
+    if not args.no_parity:
+        rec["errors"] = parity(wl, y.cpu().numpy(), h.cpu().numpy(), 4, plan.n,
+                               full_adjoint=False)
+    plan.close()
+    return rec
 
 
 def ours(args):
@@ -502,33 +600,10 @@ def ours(args):
         raise RuntimeError(f"device status {st} after the timed region")
 
     # per-stage times (library events on the plan's stream) over a second pass of K steps
-    L = _lib.lib()
-    import ctypes
-    L.nfft_profile(plan._h, 1)
-    run_variant(plan, fh, f, args.steps, flush, torch)
-    ms = (ctypes.c_double * 7)()
-    cnt = (ctypes.c_int64 * 7)()
-    L.nfft_profile_read(plan._h, ms, cnt, 7)
-    L.nfft_profile(plan._h, 0)
-    stages = {}
-    for i, name in enumerate(_lib.STAGES):
-        if cnt[i]:
-            stages[name] = {"ms_per_launch": ms[i] / cnt[i], "launches": int(cnt[i])}
-    kernel_stages = {k: v for k, v in stages.items() if k in ("fft_forward", "interp", "spread",
-                                                              "fft_adjoint")}
-    step_ms = sum(v["ms_per_launch"] for v in kernel_stages.values())
-    dom = max(kernel_stages, key=lambda k: kernel_stages[k]["ms_per_launch"])
-    alg = algorithmic_bytes(dom, d, wl["N"], wl["n"], M, 4)
-    achieved = alg / (kernel_stages[dom]["ms_per_launch"] * 1e-3) / 1e9
-    for k, v in stages.items():
-        b = algorithmic_bytes(k, d, wl["N"], wl["n"], M, 4)
-        v["algorithmic_bytes"] = b
-        v["GBps"] = b / (v["ms_per_launch"] * 1e-3) / 1e9 if b else None
-        v["share"] = v["ms_per_launch"] / step_ms if k in kernel_stages else None
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak,
-                "traffic": profiled_traffic(dom, wl["name"]),
-                "peak_kind": peak_kind}
+    stages = profile_stages(plan, fh, f, args.steps, flush, torch)
+    kernel_stages = {k: v for k, v in stages.items() if k in KERNEL_STAGES}
+    roofline = roofline_of(stages, wl, M, 4, hbm_peak, peak_kind, wl["name"])
+    dom = roofline["kernel"]
 
     # the two further roofline views of the spreading kernel and of the window arithmetic
     onchip = onchip_roofline(dom, wl, M, args.m, kernel_stages[dom]["ms_per_launch"], clk)
@@ -573,6 +648,14 @@ def ours(args):
         plan.trafo_host(pin_fh, out_f)
         plan.adjoint_host(pin_f, out_h)
     serial_s = time.perf_counter() - t0
+    flushed_s = 0.0
+    for _ in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        plan.trafo_host(pin_fh, out_f)
+        plan.adjoint_host(pin_f, out_h)
+        flushed_s += time.perf_counter() - t1
     plan.set_nodes(x)
     e2e_pipelined(plan, pin_fh, pin_f, out_f, out_h, 3, torch)
     e2e_s = e2e_pipelined(plan, pin_fh, pin_f, out_f, out_h, e2e_steps, torch)
@@ -588,8 +671,10 @@ def ours(args):
                    "copies per step (about 120 us at the ~170 GB/s of pinned copies on this "
                    "machine) hide behind the kernels of the neighbouring step",
            "host_calls_value": world * M * e2e_steps / serial_s,
+           "host_calls_l2_flushed_value": world * M * e2e_steps / flushed_s,
            "host_calls": "nfft_trafo_host + nfft_adjoint_host per step (copies, kernels and a "
-                         "wait in sequence)"}
+                         "wait in sequence, through the C ABI); _l2_flushed: a 256 MiB write "
+                         "before every step, outside the host timer"}
 
     line = None
     if rank == 0:
@@ -609,20 +694,15 @@ def ours(args):
                 ent = {"dtype": "f64" if dt_t == torch.float64 else "f32", "m": mm,
                        "nodes_per_s": M * kv / ((sum(fw) + sum(ad)) * 1e-3),
                        "fwd_nodes_per_s": M * kv / (sum(fw) * 1e-3),
-                       "adj_nodes_per_s": M * kv / (sum(ad) * 1e-3)}
+                       "adj_nodes_per_s": M * kv / (sum(ad) * 1e-3),
+                       "ms_per_step": (sum(fw) + sum(ad)) / kv}
+                stv = profile_stages(pv, fhv, fv, 10, flush, torch)
+                pbytes = 8 if dt_t == torch.float64 else 4
+                ent["roofline"] = roofline_of(stv, wv, M, pbytes, hbm_peak, peak_kind)
+                ent["stages_us"] = {k: 1e3 * v["ms_per_launch"] for k, v in stv.items()}
                 if dt_t == torch.float64 and mm == args.m:
-                    # FP64 window and tap arithmetic against the FP64 FMA rate
-                    pv.set_nodes(xv)
-                    Lv = _lib.lib()
-                    Lv.nfft_profile(pv._h, 1)
-                    run_variant(pv, fhv, fv, 5, flush, torch)
-                    msv = (ctypes.c_double * 7)()
-                    cv = (ctypes.c_int64 * 7)()
-                    Lv.nfft_profile_read(pv._h, msv, cv, 7)
-                    Lv.nfft_profile(pv._h, 0)
-                    st64 = {nm: {"ms_per_launch": msv[i] / cv[i]}
-                            for i, nm in enumerate(_lib.STAGES) if cv[i]}
-                    alu["f64"] = alu_roofline(d, mm, True, M, st64, clk)
+                    # FP64 window and tap arithmetic against the nominal FP64 FMA rate
+                    alu["f64"] = alu_roofline(d, mm, True, M, stv, clk)
                 if not args.no_parity:
                     ent.update(parity(wv, yv.cpu().numpy(), hv.cpu().numpy(), mm, pv.n))
                 variants.append(ent)
@@ -635,6 +715,10 @@ def ours(args):
             cpu = {"value": v, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
                    "sample": f"the full workload ({M} nodes) x {reps} forward+adjoint, "
                              f"{el:.1f} s"}
+        sub = {}
+        if not args.no_subrecords:
+            sub["clusters"] = clusters_record(args, flush, dev, hbm_peak, peak_kind, uuid, torch)
+            sub["batched"] = batched_record(args, dev, uuid, flush, torch)
         launches_per_step = 2 * d + 2
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -657,6 +741,7 @@ def ours(args):
             "stages": stages,
             "variants": variants,
             "cpu_baseline": cpu,
+            "subrecords": sub or None,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
@@ -737,17 +822,13 @@ def e2e_pipelined(plan, pin_fh, pin_f, out_f, out_h, steps, torch):
     return time.perf_counter() - t0
 
 
-def batched(args):
+def batched_record(args, dev, uuid, flush, torch):
     """64 independent 2-D problems (N_i per axis from {64, ..., 512}, M_i log-uniform in
     [1e4, 1e6], uniform nodes, FP32, m = 4): forward + adjoint of the whole batch captured in one
     CUDA graph; value = sum of M_i per step / step time. ``with_backward`` times a second graph
     that also holds the backward of the forward transform."""
-    import torch
-
     from paper_1810_09891_gb300 import workloads as W
     from paper_1810_09891_gb300.batch import PlanBatch, batched_specs
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     specs = batched_specs()
     b = PlanBatch(specs, dtype=torch.float32, device=dev)
     xs = [torch.tensor(W.round_nodes(W.uniform_nodes(s["M"], 2, seed_offset=1000 + i),
@@ -759,44 +840,89 @@ def batched(args):
     gs = [torch.tensor(W.gaussian_values(s["M"], 4000 + i).astype(np.complex64), device=dev)
           for i, s in enumerate(specs)]
     b.set_nodes(xs)
-    tuned = b.tune(fhs, fs) if args.tune else None
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    tuned = b.tune(fhs, fs) if getattr(args, "tune", False) else None
+    steps = max(5, min(args.steps, 50))
 
-    def timed_replays():
+    def timed_replays(sample_clocks=False):
         for _ in range(max(3, args.warmup)):
             b.replay()
         torch.cuda.synchronize()
+        clocks = ClockSampler(uuid) if sample_clocks else None
+        if clocks:
+            clocks.start()
+            for _ in range(20):
+                b.replay()
+            torch.cuda.synchronize()
+        t0 = time.time()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+              for _ in range(steps)]
         for a, c in ev:
             flush.zero_()
             a.record()
             b.replay()
             c.record()
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(c) for a, c in ev)
+        t1 = time.time()
+        clk = clocks.stop(t0, t1) if clocks else None
+        return sum(a.elapsed_time(c) for a, c in ev), clk
 
     b.capture(fhs, fs)
-    total_ms = timed_replays()
+    total_ms, clk = timed_replays(True)
     # the same step plus the backward of the forward transform (grad fhat and grad x for an
     # output gradient per problem) in one graph
     b.capture(fhs, fs, grad_fs=gs)
-    bwd_ms = timed_replays()
+    bwd_ms, _ = timed_replays()
     nodes = sum(s["M"] for s in specs)
-    line = {"metric": METRIC, "value": nodes * args.steps / (total_ms * 1e-3), "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batched_64x2d_uneven", "problems": len(specs),
-                       "nodes_per_step": nodes, "m": 4, "graph": "one CUDA graph per step",
-                       "tuned": bool(args.tune),
-                       "l2": "flushed (256 MiB write) between timed steps"},
-            "with_backward": {"ms_per_step": bwd_ms / args.steps,
-                              "nodes_per_s": nodes * args.steps / (bwd_ms * 1e-3),
-                              "step": "forward + adjoint + backward of the forward "
-                                      "(adjoint for grad fhat, node-gradient kernel for grad x)"},
-            "tuning": [{"N": list(s["N"]), "M": s["M"], "spread": t["spread_method"],
-                        "bins": t["bins"]} for s, t in zip(specs, tuned)] if tuned else None}
+    # whole-step HBM view: the algorithmic bytes of every plan's four kernel stages over the
+    # step time
+    alg = 0.0
+    for s in specs:
+        n = tuple(2 * v for v in s["N"])
+        for st in KERNEL_STAGES:
+            alg += algorithmic_bytes(st, 2, s["N"], n, s["M"], 4)
+    hbm_peak, peak_kind = load_peaks()
+    step_s = total_ms / steps * 1e-3
+    rec = {"workload": "batched_64x2d_uneven", "problems": len(specs), "nodes_per_step": nodes,
+           "m": 4, "dtype": "f32", "steps": steps, "ms_per_step": total_ms / steps,
+           "value": nodes * steps / (total_ms * 1e-3), "unit": UNIT,
+           "graph": "one CUDA graph per step",
+           "roofline": {"bound": "hbm", "kernel": "whole step (all plans, all stages)",
+                        "achieved": alg / step_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": alg / step_s / 1e9 / hbm_peak, "traffic": None,
+                        "peak_kind": peak_kind},
+           "clocks": clk, "tuned": bool(tuned),
+           "l2": "flushed (256 MiB write) between timed steps",
+           "with_backward": {"ms_per_step": bwd_ms / steps,
+                             "nodes_per_s": nodes * steps / (bwd_ms * 1e-3),
+                             "step": "forward + adjoint + backward of the forward "
+                                     "(adjoint for grad fhat, node-gradient kernel for grad x)"},
+           "tuning": [{"N": list(s["N"]), "M": s["M"], "spread": t["spread_method"],
+                       "bins": t["bins"]} for s, t in zip(specs, tuned)] if tuned else None}
+    b.close()
+    return rec
+
+
+def batched(args):
+    """--workload batched: the batched record alone, as a bench line."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    r = batched_record(args, dev, uuid, flush, torch)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": r["steps"], "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": r["workload"], "problems": r["problems"],
+                       "nodes_per_step": r["nodes_per_step"], "m": 4, "graph": r["graph"],
+                       "tuned": r["tuned"], "l2": r["l2"]},
+            "roofline": r["roofline"], "clocks": r["clocks"],
+            "with_backward": r["with_backward"], "tuning": r["tuning"]}
     print(json.dumps(line))
     return 0
 

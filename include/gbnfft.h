@@ -224,9 +224,14 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           4 (d = 2) eight lanes per node, a private tile per eight lanes,
  *                           5 (d = 2) sixteen lanes per node, a private tile per half-warp,
  *                           6 (d = 3) one tile per CTA, its planes along axis 0 owned by the
- *                           CTA's warps (no atomics, no private copies).
+ *                           CTA's warps (no atomics, no private copies),
+ *                           7 (d = 2) one tile per CTA over a super-bin of stripes of whole bins
+ *                           along the last axis (each at least 2m cells wide); the CTA's
+ *                           half-warps spread the even stripes together, then the odd ones (no
+ *                           atomics, no private copies). Needs a last-axis bin of at most
+ *                           2m rounded up to a power of two and n_(d-1) >= 16 such stripes + 2m.
  *                           A form whose tile does not fit or whose d does not match runs as
- *                           the nearest form that fits (6 -> 2 -> 1, 4/5 -> 3 -> 2 -> 1).
+ *                           the nearest form that fits (6 -> 2 -> 1, 7 -> 5, 4/5 -> 3 -> 2 -> 1).
  *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node (gathers from the grid),
  *                           2 one warp per node, 3 one thread per node gathering from a
  *                           shared-memory tile of the node's bin, 4 (d = 2, 3 and m <= 4;
@@ -249,9 +254,12 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           window changes; waits for the device to go idle.
  *   NFFT_OPT_SUBPROBLEM     nodes per spreading work item (a power of two in 32..1024, 0 = the
  *                           default: 128 for 2-D FP32, else 1024): the sorted nodes of a bin are
- *                           cut into items of at
- *                           most this many nodes. Like a bin size, it discards the node
- *                           precomputation and may change nfft_workspace_size. */
+ *                           cut into items of at most this many nodes. Like a bin size, it
+ *                           discards the node precomputation and may change nfft_workspace_size.
+ *   NFFT_OPT_STRIPE_ITEM    nodes per stripe in one work item of spreading form 7 (a power of
+ *                           two in 8..65536, 0 = the default 64): a super-bin whose heaviest
+ *                           stripe holds more nodes is cut into parts, each taking a share of
+ *                           every stripe. Discards the node precomputation like a bin size. */
 enum nfft_option {
     NFFT_OPT_SPREAD_METHOD = 1,
     NFFT_OPT_BIN_0 = 2,
@@ -260,7 +268,8 @@ enum nfft_option {
     NFFT_OPT_INTERP_METHOD = 5,
     NFFT_OPT_WINDOW = 6,
     NFFT_OPT_SUBPROBLEM = 7,
-    NFFT_OPT_WINDOW_TABLE = 8
+    NFFT_OPT_WINDOW_TABLE = 8,
+    NFFT_OPT_STRIPE_ITEM = 9
 };
 int nfft_set_option(nfft_plan plan, int key, int64_t value);
 

@@ -89,10 +89,11 @@ OPT_INTERP_METHOD = 5
 OPT_WINDOW = 6
 OPT_SUBPROBLEM = 7
 OPT_WINDOW_TABLE = 8
+OPT_STRIPE_ITEM = 9
 WINDOWS = {"kaiser_bessel": 0, "gaussian": 1, "bspline": 2, "sinc": 3}
 INTERP_METHODS = {"auto": 0, "thread": 1, "warp": 2, "tile": 3, "octet": 4}
 SPREAD_METHODS = {"auto": 0, "thread": 1, "warp_atomic": 2, "warp_private": 3, "octet": 4,
-                  "half": 5, "plane": 6}
+                  "half": 5, "plane": 6, "stripe": 7}
 
 STAGES = ["set_nodes", "fft_forward", "interp", "zero_grid", "spread", "fft_adjoint", "grad"]
 

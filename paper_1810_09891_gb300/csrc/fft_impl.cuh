@@ -466,19 +466,21 @@ __device__ __forceinline__ void r8_stage(const typename Cplx<T>::type *src,
     }
 }
 
+// One CTA's lines of a pass: P lines of L = 2^LOGL points (P * L / 8 threads, `block` the
+// CTA's index within the pass, S its shared memory: P line buffers of LS cells).
 template <typename T, int LOGL, bool INV>
-__global__ void __launch_bounds__(FftMaxThreads<T>::value)
-    fftr_axis_kernel(const typename Cplx<T>::type *__restrict__ in,
-                     typename Cplx<T>::type *__restrict__ out, long long outer, long long inner,
-                     int Nt, int P, int LS, int pad_mode,
-                     const typename Cplx<T>::type *__restrict__ tw, const T *__restrict__ deconv)
+__device__ __forceinline__ void fftr_block(const typename Cplx<T>::type *__restrict__ in,
+                                           typename Cplx<T>::type *__restrict__ out,
+                                           long long outer, long long inner, int Nt, int P,
+                                           int LS, int pad_mode,
+                                           const typename Cplx<T>::type *__restrict__ tw,
+                                           const T *__restrict__ deconv, long long block,
+                                           typename Cplx<T>::type *S)
 {
     using C = typename Cplx<T>::type;
     constexpr int L = 1 << LOGL;
     constexpr int TL = L / kFftR;
     constexpr int BUF = L + L / 16;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C *S = reinterpret_cast<C *>(smem_raw);
     const int tid = threadIdx.x;
     const int Lin = pad_mode == 1 ? Nt : L;
     const int Lout = pad_mode == 0 ? Nt : L;
@@ -488,15 +490,15 @@ __global__ void __launch_bounds__(FftMaxThreads<T>::value)
     if (inner == 1) {
         c = tid / TL;
         j = tid - c * TL;
-        o0 = (long long)blockIdx.x * P;
+        o0 = block * P;
         i0 = 0;
         lines = (int)min((long long)P, outer - o0);
     } else {
         c = tid % P;
         j = tid / P;
         const long long tiles = (inner + P - 1) / P;
-        o0 = blockIdx.x / tiles;
-        i0 = (blockIdx.x - o0 * tiles) * P;
+        o0 = block / tiles;
+        i0 = (block - o0 * tiles) * P;
         lines = (int)min((long long)P, inner - i0);
     }
     const bool live = c < lines;
@@ -518,6 +520,19 @@ __global__ void __launch_bounds__(FftMaxThreads<T>::value)
     C *b0 = S + (size_t)c * LS;
     C *b1 = b0 + BUF;
     r8_stage<T, LOGL, 0, INV>(src, dst, io, deconv, live, j, b1, b0, tw);
+}
+
+template <typename T, int LOGL, bool INV>
+__global__ void __launch_bounds__(FftMaxThreads<T>::value)
+    fftr_axis_kernel(const typename Cplx<T>::type *__restrict__ in,
+                     typename Cplx<T>::type *__restrict__ out, long long outer, long long inner,
+                     int Nt, int P, int LS, int pad_mode,
+                     const typename Cplx<T>::type *__restrict__ tw, const T *__restrict__ deconv)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fftr_block<T, LOGL, INV>(in, out, outer, inner, Nt, P, LS, pad_mode, tw, deconv,
+                             (long long)blockIdx.x, reinterpret_cast<C *>(smem_raw));
 }
 
 template <typename T, int LOGL>

@@ -46,6 +46,40 @@ __host__ __device__ constexpr int poly_axis_stride(bool fp64, int m)
     return (poly_degree(fp64, m) + 1) * kPolyTaps;
 }
 
+// A spreading subproblem: up to kMaxSub consecutive sorted nodes of one bin.
+struct SubProb {
+    int bin;
+    int start;
+    int count;
+    int pad;
+};
+
+// Stripe form of B^H (d = 2, see spread_impl.cuh): a super-bin is kStripeS stripes side by side
+// along the last axis, a stripe being stripe_width(m) >= 2m cells (a whole number of sort bins)
+// wide and one sort bin high. Stripes j and j + 2 of a super-bin never share a tile cell, so the
+// kStripeHalves half-warps of a CTA spread the even stripes together, then the odd ones, into
+// one tile.
+constexpr int kStripeWarps = 4;
+constexpr int kStripeHalves = 2 * kStripeWarps;
+constexpr int kStripeS = 2 * kStripeHalves;
+constexpr int kStripeItemDefault = 64;  // nodes per stripe per work item (super-bins are cut into
+                                        // parts so that no stripe's part exceeds it)
+__host__ __device__ constexpr int stripe_width(int m)
+{
+    return 2 * m <= 2 ? 2 : 2 * m <= 4 ? 4 : 2 * m <= 8 ? 8 : 16;
+}
+
+// Work of the stripe form, built by set_nodes from the sort bins.
+struct StripeWork {
+    const int *bin_start;   // per sort bin: position of its first node in sorted order
+    const int *bin_count;   // per sort bin: number of nodes
+    const SubProb *items;   // work items {bin = super-bin, start = part p, count = parts P}
+    int *work;              // [0] items, [1] next unclaimed item, [2] CTAs finished
+    int max_items;          // bound on the number of items
+    int R;                  // sort bins per stripe along the last axis (0: no stripe work)
+    int nsb1;               // super-bins along the last axis
+};
+
 // Spreading methods (see spread_impl.cuh); kSpreadAuto picks by tile size.
 constexpr int kSpreadAuto = 0;
 constexpr int kSpreadThread = 1;
@@ -54,6 +88,7 @@ constexpr int kSpreadWarpPrivate = 3;
 constexpr int kSpreadOctet = 4;
 constexpr int kSpreadHalf = 5;
 constexpr int kSpreadPlane = 6;
+constexpr int kSpreadStripe = 7;
 
 // Interpolation methods (see interp_impl.cuh).
 constexpr int kInterpAuto = 0;
@@ -80,6 +115,7 @@ struct Geom {
     const void *poly_host; // host copy of the same table (source of WinCoef kernel arguments)
     const void *lin;       // lookup tables of the window (PRE_LIN_PSI), d axes, or null
     int lin_k;             // samples per unit of t of those tables; 0 = polynomial window
+    StripeWork sw;         // stripe-form spreading work (set before each spreading launch)
 };
 
 // The window polynomial table as a kernel argument (same layout as the device table). Kernels
@@ -115,14 +151,6 @@ __host__ __device__ __forceinline__ int modn(int x, int n)
     return x < 0 ? x + n : x;
 }
 
-// A spreading subproblem: up to kMaxSub consecutive sorted nodes of one bin.
-struct SubProb {
-    int bin;
-    int start;
-    int count;
-    int pad;
-};
-
 // Node record in sorted order. FP32: {cell bits, frac0, frac1, frac2}; FP64: cell in the
 // first 8 bytes, then frac0..2. cell is the row-major index of (base_t mod n_t).
 struct alignas(16) RecF {
@@ -149,18 +177,32 @@ constexpr int kStatusOk = 0;
 // Launchers (each enqueues on `stream`, returns cudaError_t of the launch)
 // ------------------------------------------------------------------------------------------
 
-// set_nodes: cell / bin / rank per node, then counting sort into bins, then subproblems.
+// set_nodes: cell / row sub-bin / rank per node (a sub-bin is one grid row along axis 0 of a bin:
+// index bin * bs0 + row), then the bin totals, the scan over bins, the sub-bin starts, the
+// counting sort (scatter), then subproblems.
 template <typename T>
-cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *bin_count, int2 *bin_rank,
+cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *sub_count, int2 *sub_rank,
                             int *status, cudaStream_t stream);
+cudaError_t launch_bin_totals(const int *sub_count, int S0, int nbins, int *bin_count,
+                              cudaStream_t stream);
+cudaError_t launch_sub_starts(const int *sub_count, const int *bin_start, int S0, int nbins,
+                              int *sub_start, cudaStream_t stream);
 cudaError_t launch_bin_scan(const int *bin_count, int *bin_start, int *sub_start, int *nsub_total,
                             int nbins, int sub_max, cudaStream_t stream);
 template <typename T>
-cudaError_t launch_node_scatter(const Geom &g, const T *x, int64_t M, const int2 *bin_rank,
-                                const int *bin_start, typename RecOf<T>::type *rec, int *perm,
+cudaError_t launch_node_scatter(const Geom &g, const T *x, int64_t M, const int2 *sub_rank,
+                                const int *sub_start, typename RecOf<T>::type *rec, int *perm,
                                 cudaStream_t stream);
 cudaError_t launch_fill_subprobs(const int *bin_count, const int *bin_start, const int *sub_start,
                                  SubProb *subs, int nbins, int sub_max, cudaStream_t stream);
+
+// Work items of the stripe form (d = 2): per super-bin (kStripeS stripes of R sort bins in one
+// sort-bin row) the node count of its heaviest stripe, the exclusive scan of the part counts
+// P = ceil(count / item), and the item list {super-bin, part p, parts P}; sb_count, sb_start
+// and sb_sub hold nsb values, work the item count (then zeroed work counters).
+cudaError_t launch_stripe_items(const int *bin_count, int nb0, int nb1, int R, int nsb1,
+                                int *sb_count, int *sb_start, int *sb_sub, int *work,
+                                SubProb *items, int item, cudaStream_t stream);
 
 // One axis pass of the pruned d-variate FFT.
 //   in  : [outer][Lin][inner]   out : [outer][Lout][inner]

@@ -1,5 +1,6 @@
 // Node precomputation (set_nodes): grid cell and offset of every node, then a counting sort of
-// the nodes into bins (tiles of the oversampled grid), then the list of spreading subproblems.
+// the nodes into bins (tiles of the oversampled grid; inside a bin by grid row along axis 0),
+// then the list of spreading subproblems.
 // This is the GPU form of the paper's node sorting (Section 3.1, Table tab:nfftflags,
 // NFFT_SORT_NODES): nodes that share a tile are processed together by the interpolation and
 // spreading kernels.
@@ -48,13 +49,16 @@ __device__ __forceinline__ bool node_pos(T xt, int n, long long &base, double &f
     return true;
 }
 
+// Sort key of a node: its bin, and inside the bin its row along axis 0 (a sub-bin of one grid
+// row): nodes of a bin end up ordered by that row, so that neighbouring threads of the
+// interpolation read the same grid rows.
 template <typename T>
-__global__ void node_bin_kernel(Geom g, const T *__restrict__ x, int M, int *__restrict__ bin_count,
-                                int2 *__restrict__ bin_rank, int *__restrict__ status)
+__global__ void node_bin_kernel(Geom g, const T *__restrict__ x, int M, int *__restrict__ sub_count,
+                                int2 *__restrict__ sub_rank, int *__restrict__ status)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
-    int bin = 0;
+    int bin = 0, row = 0;
     bool ok = true;
     for (int t = 0; t < g.d; t++) {
         long long base;
@@ -63,20 +67,65 @@ __global__ void node_bin_kernel(Geom g, const T *__restrict__ x, int M, int *__r
         long long b = base % g.n[t];  // base mod n
         if (b < 0) b += g.n[t];
         bin = bin * g.nb[t] + ((int)b >> g.bslog[t]);
+        if (t == 0) row = (int)b & (g.bs[0] - 1);
     }
     if (!ok) atomicCAS(status, kStatusOk, (int)NFFT_EBADNODE);
-    const int rank = atomicAdd(&bin_count[bin], 1);
-    bin_rank[j] = make_int2(bin, rank);
+    const int sub = bin * g.bs[0] + row;
+    const int rank = atomicAdd(&sub_count[sub], 1);
+    sub_rank[j] = make_int2(sub, rank);
 }
 
 template <typename T>
-cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *bin_count, int2 *bin_rank,
+cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *sub_count, int2 *sub_rank,
                             int *status, cudaStream_t stream)
 {
     if (M == 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (int)((M + threads - 1) / threads);
-    node_bin_kernel<T><<<blocks, threads, 0, stream>>>(g, x, (int)M, bin_count, bin_rank, status);
+    node_bin_kernel<T><<<blocks, threads, 0, stream>>>(g, x, (int)M, sub_count, sub_rank, status);
+    return cudaGetLastError();
+}
+
+// Per bin: its node count, the sum over its bs0 row sub-bins.
+__global__ void bin_totals_kernel(const int *__restrict__ sub_count, int S0, int nbins,
+                                  int *__restrict__ bin_count)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    int sum = 0;
+    for (int r = 0; r < S0; r++) sum += sub_count[b * S0 + r];
+    bin_count[b] = sum;
+}
+
+// Per row sub-bin: its first position in sorted order (the bin's start plus the rows before).
+__global__ void sub_starts_kernel(const int *__restrict__ sub_count,
+                                  const int *__restrict__ bin_start, int S0, int nbins,
+                                  int *__restrict__ sub_start)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    int run = bin_start[b];
+    for (int r = 0; r < S0; r++) {
+        sub_start[b * S0 + r] = run;
+        run += sub_count[b * S0 + r];
+    }
+}
+
+cudaError_t launch_bin_totals(const int *sub_count, int S0, int nbins, int *bin_count,
+                              cudaStream_t stream)
+{
+    const int threads = 256;
+    bin_totals_kernel<<<(nbins + threads - 1) / threads, threads, 0, stream>>>(sub_count, S0,
+                                                                              nbins, bin_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub_starts(const int *sub_count, const int *bin_start, int S0, int nbins,
+                              int *sub_start, cudaStream_t stream)
+{
+    const int threads = 256;
+    sub_starts_kernel<<<(nbins + threads - 1) / threads, threads, 0, stream>>>(
+        sub_count, bin_start, S0, nbins, sub_start);
     return cudaGetLastError();
 }
 
@@ -135,8 +184,8 @@ cudaError_t launch_bin_scan(const int *bin_count, int *bin_start, int *sub_start
 
 template <typename T>
 __global__ void node_scatter_kernel(Geom g, const T *__restrict__ x, int M,
-                                    const int2 *__restrict__ bin_rank,
-                                    const int *__restrict__ bin_start,
+                                    const int2 *__restrict__ sub_rank,
+                                    const int *__restrict__ sub_start,
                                     typename RecOf<T>::type *__restrict__ rec, int *__restrict__ perm)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,21 +202,21 @@ __global__ void node_scatter_kernel(Geom g, const T *__restrict__ x, int M,
         r.cell = (r.cell << g.cbits[t]) | (int)b;
         r.fr[t] = (T)frac;
     }
-    const int2 br = bin_rank[j];
-    const int pos = bin_start[br.x] + br.y;
+    const int2 br = sub_rank[j];
+    const int pos = sub_start[br.x] + br.y;
     rec[pos] = r;
     perm[pos] = j;
 }
 
 template <typename T>
-cudaError_t launch_node_scatter(const Geom &g, const T *x, int64_t M, const int2 *bin_rank,
-                                const int *bin_start, typename RecOf<T>::type *rec, int *perm,
+cudaError_t launch_node_scatter(const Geom &g, const T *x, int64_t M, const int2 *sub_rank,
+                                const int *sub_start, typename RecOf<T>::type *rec, int *perm,
                                 cudaStream_t stream)
 {
     if (M == 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (int)((M + threads - 1) / threads);
-    node_scatter_kernel<T><<<blocks, threads, 0, stream>>>(g, x, (int)M, bin_rank, bin_start, rec,
+    node_scatter_kernel<T><<<blocks, threads, 0, stream>>>(g, x, (int)M, sub_rank, sub_start, rec,
                                                            perm);
     return cudaGetLastError();
 }
@@ -196,6 +245,60 @@ cudaError_t launch_fill_subprobs(const int *bin_count, const int *bin_start, con
     const int threads = 256;
     fill_subprobs_kernel<<<(nbins + threads - 1) / threads, threads, 0, stream>>>(
         bin_count, bin_start, sub_start, subs, nbins, sub_max);
+    return cudaGetLastError();
+}
+
+// Node count of the heaviest stripe of every super-bin (a stripe is R sort bins): a work item
+// takes one part of every stripe, and a stripe's part is walked by one half-warp, so the parts
+// are sized by the heaviest stripe.
+__global__ void superbin_count_kernel(const int *__restrict__ count, int nb0, int nb1, int R,
+                                      int nsb1, int *__restrict__ sb_count)
+{
+    const int sb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sb >= nb0 * nsb1) return;
+    const int b0 = sb / nsb1, c0 = (sb - b0 * nsb1) * kStripeS * R;
+    const int c1 = min(c0 + kStripeS * R, nb1);
+    int most = 0;
+    for (int s = c0; s < c1; s += R) {
+        int sum = 0;
+        for (int c = s; c < min(s + R, c1); c++) sum += count[b0 * nb1 + c];
+        most = max(most, sum);
+    }
+    sb_count[sb] = most;
+}
+
+__global__ void fill_stripe_items_kernel(const int *__restrict__ sb_count,
+                                         const int *__restrict__ sb_sub, SubProb *__restrict__ items,
+                                         int nsb, int item)
+{
+    const int sb = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sb >= nsb) return;
+    const int c = sb_count[sb];
+    const int parts = (c + item - 1) / item;
+    for (int k = 0; k < parts; k++) {
+        SubProb p;
+        p.bin = sb;
+        p.start = k;
+        p.count = parts;
+        p.pad = 0;
+        items[sb_sub[sb] + k] = p;
+    }
+}
+
+cudaError_t launch_stripe_items(const int *bin_count, int nb0, int nb1, int R, int nsb1,
+                                int *sb_count, int *sb_start, int *sb_sub, int *work,
+                                SubProb *items, int item, cudaStream_t stream)
+{
+    const int nsb = nb0 * nsb1;
+    const int threads = 256;
+    superbin_count_kernel<<<(nsb + threads - 1) / threads, threads, 0, stream>>>(
+        bin_count, nb0, nb1, R, nsb1, sb_count);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_bin_scan(sb_count, sb_start, sb_sub, work, nsb, item, stream);
+    if (e != cudaSuccess) return e;
+    fill_stripe_items_kernel<<<(nsb + threads - 1) / threads, threads, 0, stream>>>(
+        sb_count, sb_sub, items, nsb, item);
     return cudaGetLastError();
 }
 

@@ -261,6 +261,11 @@ struct gbnfft_plan {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     Region gA, gB, rec, perm, binrank, bincount, binstart, substart, nsub, subs, blu;
+    Region rowcount, rowstart;  // row sub-bins (bs0 per bin): node counts and first positions
+    // stripe-form spreading work (d = 2): super-bin counts, scans and items
+    Region sbcount, sbstart, sbsub, sbn, sitems;
+    int stripe_R = 0, stripe_nsb1 = 0, stripe_nsb = 0, stripe_max_items = 0;
+    int64_t stripe_item_req = 0;  // requested nodes per stripe work item (0 = default)
     size_t ws_need = 0;
     bool nodes_ready = false;
     // host-call staging (plan-owned)
@@ -310,14 +315,21 @@ void layout_workspace(gbnfft_plan *p)
     put(p->bincount, size_t(p->nbins) * sizeof(int));
     put(p->binstart, size_t(p->nbins) * sizeof(int));
     put(p->substart, size_t(p->nbins) * sizeof(int));
+    put(p->rowcount, size_t(p->nbins) * p->geom.bs[0] * sizeof(int));
+    put(p->rowstart, size_t(p->nbins) * p->geom.bs[0] * sizeof(int));
     put(p->nsub, 16);
     put(p->subs, size_t(p->max_subs) * sizeof(SubProb));
     put(p->blu, 2 * p->blu_elems * p->csize);
+    put(p->sbcount, size_t(p->stripe_nsb) * sizeof(int));
+    put(p->sbstart, size_t(p->stripe_nsb) * sizeof(int));
+    put(p->sbsub, size_t(p->stripe_nsb) * sizeof(int));
+    put(p->sbn, 16);
+    put(p->sitems, size_t(p->stripe_max_items) * sizeof(SubProb));
     p->ws_need = align_up(off, 256);
 }
 
-// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 4 x 16 in FP32
-// and 8 x 16 in FP64, 3-D 8 x 8 x 16), clipped to n_t; nodes per spreading work item: the requested number, else 128
+// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 8 x 16,
+// 3-D 8 x 8 x 16), clipped to n_t; nodes per spreading work item: the requested number, else 128
 // for 2-D FP32 and 1024 otherwise (the fastest choices measured with the default spreading forms
 // on a radial trajectory, whose bins hold very different node counts). Recomputes the bin
 // counts and the workspace layout.
@@ -334,7 +346,6 @@ void setup_bins(gbnfft_plan *p)
             continue;
         }
         int64_t bs = p->bin_req[t] > 0 ? p->bin_req[t] : bin_default[p->d - 1][t];
-        if (p->bin_req[t] <= 0 && p->d == 2 && p->dtype == NFFT_FP32 && t == 0) bs = 4;
         if (is_pow2(p->n[t])) {
             if (bs > p->n[t]) bs = p->n[t];  // one bin covers the axis
         } else {
@@ -367,6 +378,21 @@ void setup_bins(gbnfft_plan *p)
     p->sub_max = p->sub_req > 0 ? (int)p->sub_req
                                 : (p->d == 2 && p->dtype == NFFT_FP32 ? 128 : kMaxSub);
     p->max_subs = (int)(nbins + (p->M + p->sub_max - 1) / p->sub_max + 1);
+    // stripe-form work (d = 2): stripes of stripe_width(m) >= 2m cells made of whole sort bins,
+    // kStripeS stripes per super-bin; the super-bin tile must not wrap onto itself
+    p->stripe_R = p->stripe_nsb1 = p->stripe_nsb = p->stripe_max_items = 0;
+    if (p->d == 2) {
+        const int W = stripe_width(p->m);
+        const int span = kStripeS * W;
+        if (g.bs[1] <= W && span + 2 * p->m <= p->n[1]) {
+            p->stripe_R = W / g.bs[1];
+            const int bins_per_sb = kStripeS * p->stripe_R;
+            p->stripe_nsb1 = (g.nb[1] + bins_per_sb - 1) / bins_per_sb;
+            p->stripe_nsb = g.nb[0] * p->stripe_nsb1;
+            const int64_t item = p->stripe_item_req > 0 ? p->stripe_item_req : kStripeItemDefault;
+            p->stripe_max_items = (int)(p->stripe_nsb + (p->M + item - 1) / item + 1);
+        }
+    }
     layout_workspace(p);
 }
 
@@ -504,17 +530,46 @@ template <typename T> int do_set_nodes(gbnfft_plan *p, const void *x)
     ProfScope ps(p, NFFT_STAGE_SET_NODES);
     cudaStream_t s = p->stream;
     int *count = at<int>(p, p->bincount);
-    GB_CHECK(cudaMemsetAsync(count, 0, size_t(p->nbins) * sizeof(int), s));
-    GB_CHECK(launch_node_bin<T>(p->geom, static_cast<const T *>(x), p->M, count,
+    int *rows = at<int>(p, p->rowcount);
+    const int S0 = p->geom.bs[0];
+    GB_CHECK(cudaMemsetAsync(rows, 0, size_t(p->nbins) * S0 * sizeof(int), s));
+    GB_CHECK(launch_node_bin<T>(p->geom, static_cast<const T *>(x), p->M, rows,
                                 at<int2>(p, p->binrank), p->d_status, s));
+    GB_CHECK(launch_bin_totals(rows, S0, p->nbins, count, s));
     GB_CHECK(launch_bin_scan(count, at<int>(p, p->binstart), at<int>(p, p->substart),
                              at<int>(p, p->nsub), p->nbins, p->sub_max, s));
+    GB_CHECK(launch_sub_starts(rows, at<int>(p, p->binstart), S0, p->nbins,
+                               at<int>(p, p->rowstart), s));
     GB_CHECK(launch_node_scatter<T>(p->geom, static_cast<const T *>(x), p->M,
-                                    at<int2>(p, p->binrank), at<int>(p, p->binstart),
+                                    at<int2>(p, p->binrank), at<int>(p, p->rowstart),
                                     at<Rec>(p, p->rec), at<int>(p, p->perm), s));
     GB_CHECK(launch_fill_subprobs(count, at<int>(p, p->binstart), at<int>(p, p->substart),
                                   at<SubProb>(p, p->subs), p->nbins, p->sub_max, s));
+    if (p->stripe_R > 0) {
+        const int item = p->stripe_item_req > 0 ? (int)p->stripe_item_req : kStripeItemDefault;
+        GB_CHECK(launch_stripe_items(count, p->geom.nb[0], p->geom.nb[1], p->stripe_R,
+                                     p->stripe_nsb1, at<int>(p, p->sbcount),
+                                     at<int>(p, p->sbstart), at<int>(p, p->sbsub),
+                                     at<int>(p, p->sbn), at<SubProb>(p, p->sitems), item, s));
+    }
     return NFFT_OK;
+}
+
+// The plan's geometry with the stripe-form work of the current node set attached.
+Geom spread_geom(gbnfft_plan *p)
+{
+    Geom g = p->geom;
+    g.sw = StripeWork{};
+    if (p->stripe_R > 0) {
+        g.sw.bin_start = at<int>(p, p->binstart);
+        g.sw.bin_count = at<int>(p, p->bincount);
+        g.sw.items = at<SubProb>(p, p->sitems);
+        g.sw.work = at<int>(p, p->sbn);
+        g.sw.max_items = p->stripe_max_items;
+        g.sw.R = p->stripe_R;
+        g.sw.nsb1 = p->stripe_nsb1;
+    }
+    return g;
 }
 
 template <typename T> int do_trafo(gbnfft_plan *p, const void *fhat, void *f)
@@ -544,7 +599,7 @@ template <typename T> int do_adjoint(gbnfft_plan *p, const void *f, void *fhat)
     }
     {
         ProfScope ps(p, NFFT_STAGE_SPREAD);
-        GB_CHECK(launch_spread<T>(p->geom, static_cast<const C *>(f), at<Rec>(p, p->rec),
+        GB_CHECK(launch_spread<T>(spread_geom(p), static_cast<const C *>(f), at<Rec>(p, p->rec),
                                   at<int>(p, p->perm), at<SubProb>(p, p->subs),
                                   at<int>(p, p->nsub), p->max_subs, at<C>(p, p->gA), p->stream));
     }
@@ -1114,7 +1169,7 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
     if (!p) return NFFT_EINVAL;
     switch (key) {
     case NFFT_OPT_SPREAD_METHOD:
-        if (value < kSpreadAuto || value > kSpreadPlane) return NFFT_EINVAL;
+        if (value < kSpreadAuto || value > kSpreadStripe) return NFFT_EINVAL;
         p->geom.spread_method = (int)value;
         return NFFT_OK;
     case NFFT_OPT_INTERP_METHOD:
@@ -1138,6 +1193,23 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
             build_lin_tables(p);
         }
         return rc;
+    }
+    case NFFT_OPT_STRIPE_ITEM: {
+        if (value < 0 || value > 65536 || (value > 0 && (value < 8 || !is_pow2(value))))
+            return NFFT_EINVAL;
+        p->stripe_item_req = value;
+        const size_t old_need = p->ws_need;
+        setup_bins(p);
+        p->nodes_ready = false;  // the item list is built by set_nodes
+        if (p->ws_owned && p->ws && p->ws_need > old_need) {
+            set_device(p);
+            if (p->stream) cudaStreamSynchronize(p->stream);
+            cudaFree(p->ws);
+            p->ws = nullptr;
+            p->ws_bytes = 0;
+            p->ws_owned = false;
+        }
+        return NFFT_OK;
     }
     case NFFT_OPT_SUBPROBLEM: {
         if (value < 0 || value > kMaxSub || (value > 0 && (value < 32 || !is_pow2(value))))

@@ -778,10 +778,20 @@ template <typename T, int MM> __host__ __device__ inline int half_pitch(int td1)
     return td1 + ((cw - td1 % mod) + mod) % mod;
 }
 
+// Staged per node (half-warp form): tile offset of the node's first tap inside the subproblem's
+// tile (bit 31 set: the node is on a grid point and the low bits give the offset of tap slot
+// 0), its sorted index, and the window arguments (z = 2 frac - 1, or frac for the lookup-table
+// window).
+template <typename T> struct alignas(16) HalfStage {
+    int off;
+    int s;
+    T u0, u1;
+};
+
 template <typename T>
 __host__ __device__ constexpr size_t half_stage_bytes()
 {
-    return kHalfChunk * (sizeof(typename RecOf<T>::type) + sizeof(typename Cplx<T>::type));
+    return kHalfChunk * (sizeof(HalfStage<T>) + sizeof(typename Cplx<T>::type));
 }
 
 template <typename T, int MM, bool LIN>
@@ -809,8 +819,9 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
     const int tcells = td0 * pitch;
     C *tiles = reinterpret_cast<C *>(smem_raw);
     C *mine = tiles + (size_t)half * tcells;
-    Rec *st_rec = reinterpret_cast<Rec *>(smem_raw + (size_t)kHalfTiles * tcells * sizeof(C));
-    C *st_val = reinterpret_cast<C *>(st_rec + kHalfChunk);
+    HalfStage<T> *st_node =
+        reinterpret_cast<HalfStage<T> *>(smem_raw + (size_t)kHalfTiles * tcells * sizeof(C));
+    C *st_val = reinterpret_cast<C *>(st_node + kHalfChunk);
     // column tap c + 1 of axis 1 and row tap h + 1 of axis 0 (coefficient k of tap i at
     // [k * kPolyTaps + i - 1]); lanes past the 2m taps hold zeros
     T cc[DEG + 1], cr[DEG + 1];
@@ -826,6 +837,7 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
         z.y = (T)0;
         for (int e = tid; e < kHalfTiles * tcells; e += 32 * kHalfWarps) tiles[e] = z;
     }
+    C *const lane_col = mine + rg * pitch + c;
     const int nsub = nsub_total[0];
     __shared__ int s_sp;
     for (int sp = next_subproblem(nsub_total, &s_sp); sp < nsub;
@@ -841,8 +853,18 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
         }
         for (int c0 = 0; c0 < P.count; c0 += kHalfChunk) {
             const int cnt = min(kHalfChunk, P.count - c0);
-            if (tid < cnt) {
-                st_rec[tid] = r_next;
+            if (tid < cnt) {  // stage this thread's node: tile offset and window arguments
+                const int loc1 = (r_next.cell & g.cmask[1]) - org1;
+                const int loc0 = ((r_next.cell >> g.cbits[1]) & g.cmask[0]) - org0;
+                const T fr0 = r_next.fr[0], fr1 = r_next.fr[1];
+                HalfStage<T> st;
+                st.off = (fr0 == (T)0 || fr1 == (T)0)
+                             ? (int)(0x80000000u | (unsigned)(loc0 * pitch + loc1))
+                             : (loc0 + 1) * pitch + loc1 + 1;
+                st.s = P.start + c0 + tid;
+                st.u0 = LIN ? fr0 : (T)2 * fr0 - (T)1;
+                st.u1 = LIN ? fr1 : (T)2 * fr1 - (T)1;
+                st_node[tid] = st;
                 st_val[tid] = v_next;
             }
             __syncthreads();  // (also orders the previous flush's zeroing before these adds)
@@ -854,43 +876,43 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
                 }
             }
             for (int k = half; k < cnt; k += kHalfTiles) {
-                const Rec r = st_rec[k];
+                const HalfStage<T> st = st_node[k];
                 const C v = st_val[k];
-                const int loc1 = (r.cell & g.cmask[1]) - org1;
-                const int loc0 = ((r.cell >> g.cbits[1]) & g.cmask[0]) - org0;
-                const T fr0 = r.fr[0], fr1 = r.fr[1];
-                if (fr0 != (T)0 && fr1 != (T)0) {  // uniform inside the half (one node)
+                if (st.off >= 0) {  // uniform inside the half (one node)
                     T w1, w0h;
                     if constexpr (LIN) {  // lookup-table window
                         w1 = c < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 1), g.lin_k,
-                                                      c + 1, fr1, e1)
+                                                      c + 1, st.u1, e1)
                                      : (T)0;
                         w0h = h < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 0),
-                                                       g.lin_k, h + 1, fr0, e0)
+                                                       g.lin_k, h + 1, st.u0, e0)
                                       : (T)0;
                     } else {
-                        w1 = poly_horner<T, DEG>(cc, (T)2 * fr1 - (T)1);
-                        w0h = poly_horner<T, DEG>(cr, (T)2 * fr0 - (T)1);
+                        w1 = poly_horner<T, DEG>(cc, st.u1);
+                        w0h = poly_horner<T, DEG>(cr, st.u0);
                     }
                     const T ar = w1 * v.x, ai = w1 * v.y;
-                    C *col = mine + (loc0 + 1) * pitch + loc1 + 1 + c;
+                    C *col = lane_col + st.off;
 #pragma unroll
                     for (int j = 0; j < ROWS; j++) {
                         const int rr = rg + j * RG;
                         const T w0 = __shfl_sync(mask, w0h, rr, 16);
                         if (c < PER && rr < PER) {
-                            C a = col[rr * pitch];
+                            C a = col[j * RG * pitch];
                             a.x += w0 * ar;
                             a.y += w0 * ai;
-                            col[rr * pitch] = a;
+                            col[j * RG * pitch] = a;
                         }
                     }
-                } else {
+                } else {  // on a grid point: 2m + 1 taps on some axis
+                    const Rec r = rec[st.s];
+                    const T fr0 = r.fr[0], fr1 = r.fr[1];
+                    C *base = mine + (st.off & 0x7fffffff);
                     for (int q = h; q < NT * NT; q += 16) {
                         const int a0 = q / NT, a1 = q - a0 * NT;
                         const T w = eval_tap<T, MM, LIN ? 2 : 1>(g, tab, 0, a0, fr0) *
                                     eval_tap<T, MM, LIN ? 2 : 1>(g, tab + AS, 1, a1, fr1);
-                        C *p = mine + (loc0 + a0) * pitch + loc1 + a1;
+                        C *p = base + a0 * pitch + a1;
                         C a = *p;
                         a.x += w * v.x;
                         a.y += w * v.y;
@@ -1150,6 +1172,241 @@ __global__ void __launch_bounds__(32 * kPlaneWarps)
     finish_subproblems(nsub_total);
 }
 
+// ---------------------------------------------------------------------------- stripe form (d = 2)
+// One shared tile per CTA and no private copies. The tile covers a super-bin: kStripeS stripes
+// side by side along the last axis, each stripe_width(m) = W >= 2m cells wide (a whole number of
+// sort bins) and one sort bin high, plus the halo of m cells. A node of stripe j adds into tile
+// columns W j + 1 ... W j + W - 1 + 2m (W j ... on a grid point), so stripes j and j + 2 never
+// touch a common cell: the CTA's kStripeHalves half-warps take the even stripes together, then,
+// after a barrier, the odd ones. A half-warp walks the sorted nodes of its stripe sixteen at a
+// time: lane h stages node h (its tile offset, z = 2 frac - 1 per axis, its value), then the
+// sixteen lanes add every staged node with the lane layout of the half-warp form (lane (rg, c):
+// tap column c, tap rows rg, rg + RG, ...; row weights by shuffles). A work item is
+// (super-bin, part p of P): part p takes the p-th P-th of every stripe's node range, P sized so
+// that no stripe's part exceeds the item size (a half-warp walks its part node after node, so the
+// heaviest stripe sets an item's duration). The flush adds the tile into the grid (one vector
+// atomic per nonzero cell) and zeroes it; the tile is cleared once at kernel start.
+template <int MM> struct StripeShape {
+    static constexpr int W = stripe_width(MM);
+    static constexpr int TD1 = kStripeS * W + 2 * MM;
+};
+
+// Row pitch (cells) of the stripe tile: the half-warp's RG rows of CW cells fall side by side in
+// the banks (as half_pitch).
+template <typename T, int MM> __host__ __device__ constexpr int stripe_pitch()
+{
+    constexpr int td1 = StripeShape<MM>::TD1;
+    constexpr int cw = HalfShape<MM>::CW;
+    constexpr int mod = 128 / (2 * (int)sizeof(T));
+    return (HalfShape<MM>::RG == 1 || cw * 2 * (int)sizeof(T) >= 128)
+               ? td1
+               : td1 + ((cw - td1 % mod) + mod) % mod;
+}
+
+// Staged per node: tile offset of the first tap (bit 31 set: the node is on a grid point; the
+// low bits then give the offset of tap slot 0), its sorted index, and the window arguments
+// (z = 2 frac - 1, or frac itself for the lookup-table window).
+template <typename T> struct alignas(16) StripeStage {
+    int off;
+    int s;
+    T u0, u1;
+};
+
+template <typename T, int MM>
+__host__ __device__ constexpr size_t stripe_smem_bytes(int td0)
+{
+    return (size_t)td0 * stripe_pitch<T, MM>() * sizeof(typename Cplx<T>::type) +
+           (size_t)kStripeHalves * 16 * (sizeof(StripeStage<T>) + sizeof(typename Cplx<T>::type));
+}
+
+// Window values of the stripe form: with 2 * 2m <= 16 (m <= 4) every lane of a half-warp holds
+// the polynomial of one tap (lanes h < 2m: tap h + 1 of the last axis, the next 2m lanes: tap
+// h - 2m + 1 of the first axis), evaluates it once per node and the lanes exchange the values by
+// shuffles; for larger m each lane evaluates its column tap and one row tap.
+template <int MM> struct StripeWin {
+    static constexpr bool ONE = 4 * MM <= 16;
+};
+
+template <typename T, int MM, bool LIN>
+__global__ void __launch_bounds__(32 * kStripeWarps, (StripeWin<MM>::ONE && MM > 1) ? 10 : 8)
+    spread_stripe_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
+                         const typename RecOf<T>::type *__restrict__ rec,
+                         const int *__restrict__ perm, typename Cplx<T>::type *__restrict__ grid)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    using Sh = HalfShape<MM>;
+    constexpr int PER = Sh::PER, CW = Sh::CW, RG = Sh::RG, ROWS = Sh::ROWS;
+    constexpr int NT = 2 * MM + 1;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    constexpr int TD1 = StripeShape<MM>::TD1;
+    constexpr int SW = StripeShape<MM>::W;
+    constexpr int PITCH = stripe_pitch<T, MM>();
+    constexpr bool ONE = StripeWin<MM>::ONE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int2 s_rng[kStripeS];
+    __shared__ int s_sp;
+    const T *tab = static_cast<const T *>(g.poly);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int h = lane & 15, half = tid >> 4;
+    const unsigned mask = 0xffffu << (lane & 16);
+    const int c = h & (CW - 1), rg = h / CW;
+    const int td0 = g.bs[0] + 2 * MM;
+    const int cells = td0 * TD1;
+    C *tile = reinterpret_cast<C *>(smem_raw);
+    StripeStage<T> *stage = reinterpret_cast<StripeStage<T> *>(
+        smem_raw + (size_t)td0 * PITCH * sizeof(C)) + half * 16;
+    C *sval = reinterpret_cast<C *>(smem_raw + (size_t)td0 * PITCH * sizeof(C) +
+                                    (size_t)kStripeHalves * 16 * sizeof(StripeStage<T>)) +
+              half * 16;
+    // polynomial coefficients in registers (zeros for lanes without a tap)
+    constexpr int NC = ONE ? 1 : 2;
+    T cf[NC][DEG + 1];
+#pragma unroll
+    for (int k = 0; k <= DEG; k++) {
+        if constexpr (ONE) {
+            const bool col = h < PER, row = h >= PER && h < 2 * PER;
+            cf[0][k] = col ? tab[AS + k * kPolyTaps + h]
+                           : (row ? tab[k * kPolyTaps + h - PER] : (T)0);
+        } else {
+            cf[0][k] = c < PER ? tab[AS + k * kPolyTaps + c] : (T)0;
+            cf[NC - 1][k] = h < PER ? tab[k * kPolyTaps + h] : (T)0;
+        }
+    }
+    const bool lane_col_axis = h < PER;  // ONE: this lane's polynomial is a column tap
+    const T e0 = (T)g.win[0].edge_w, e1 = (T)g.win[1].edge_w;
+    {
+        C z;
+        z.x = (T)0;
+        z.y = (T)0;
+        for (int e = tid; e < td0 * PITCH; e += 32 * kStripeWarps) tile[e] = z;
+    }
+    const StripeWork &sw = g.sw;
+    const int nitems = sw.work[0];
+    C *const lane_col = tile + rg * PITCH + c;
+    for (int sp = next_subproblem(sw.work, &s_sp); sp < nitems;
+         sp = next_subproblem(sw.work, &s_sp)) {
+        const SubProb it = sw.items[sp];
+        const int sb0 = it.bin / sw.nsb1, sb1 = it.bin - sb0 * sw.nsb1;
+        const int org0 = sb0 * g.bs[0], org1 = sb1 * (kStripeS * SW);
+        if (tid < kStripeS) {  // node range of this item's part of stripe tid
+            const int fb1 = (sb1 * kStripeS + tid) * sw.R;
+            int2 rg2 = make_int2(0, 0);
+            if (fb1 < g.nb[1]) {
+                const int fbrow = sb0 * g.nb[1];
+                const int last = min(fb1 + sw.R, g.nb[1]) - 1;
+                const int s0 = sw.bin_start[fbrow + fb1];
+                const int s1 = sw.bin_start[fbrow + last] + sw.bin_count[fbrow + last];
+                const long long len = s1 - s0;
+                rg2.x = s0 + (int)(len * it.start / it.count);
+                rg2.y = s0 + (int)(len * (it.start + 1) / it.count);
+            }
+            s_rng[tid] = rg2;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int ph = 0; ph < 2; ph++) {
+            const int2 ab = s_rng[ph + 2 * half];
+            const int a = ab.x, b = ab.y;
+            Rec r_next;
+            C v_next;
+            if (a + h < b) {
+                r_next = rec[a + h];
+                v_next = f[perm[a + h]];
+            }
+            for (int k0 = a; k0 < b; k0 += 16) {
+                const int nk = min(16, b - k0);
+                if (h < nk) {
+                    const int loc1 = (r_next.cell & g.cmask[1]) - org1;
+                    const int loc0 = ((r_next.cell >> g.cbits[1]) & g.cmask[0]) - org0;
+                    const T fr0 = r_next.fr[0], fr1 = r_next.fr[1];
+                    StripeStage<T> st;
+                    st.off = (fr0 == (T)0 || fr1 == (T)0)
+                                 ? (int)(0x80000000u | (unsigned)(loc0 * PITCH + loc1))
+                                 : (loc0 + 1) * PITCH + loc1 + 1;
+                    st.s = k0 + h;
+                    st.u0 = LIN ? fr0 : (T)2 * fr0 - (T)1;
+                    st.u1 = LIN ? fr1 : (T)2 * fr1 - (T)1;
+                    stage[h] = st;
+                    sval[h] = v_next;
+                }
+                __syncwarp(mask);
+                if (k0 + 16 + h < b) {  // the next chunk is in flight while this one is added
+                    r_next = rec[k0 + 16 + h];
+                    v_next = f[perm[k0 + 16 + h]];
+                }
+                for (int k = 0; k < nk; k++) {
+                    const StripeStage<T> st = stage[k];
+                    const C v = sval[k];
+                    if (st.off >= 0) {  // uniform inside the half (one node)
+                        T w1, w0h;
+                        if constexpr (LIN) {
+                            w1 = c < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 1),
+                                                          g.lin_k, c + 1, st.u1, e1)
+                                         : (T)0;
+                            w0h = h < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 0),
+                                                           g.lin_k, h + 1, st.u0, e0)
+                                          : (T)0;
+                        } else if constexpr (ONE) {
+                            const T wl = poly_horner<T, DEG>(cf[0], lane_col_axis ? st.u1 : st.u0);
+                            w1 = __shfl_sync(mask, wl, c, 16);
+                            w0h = wl;  // row tap rr lives in lane PER + rr
+                        } else {
+                            w1 = poly_horner<T, DEG>(cf[0], st.u1);
+                            w0h = poly_horner<T, DEG>(cf[NC - 1], st.u0);
+                        }
+                        const T ar = w1 * v.x, ai = w1 * v.y;
+                        C *col = lane_col + st.off;
+#pragma unroll
+                        for (int j = 0; j < ROWS; j++) {
+                            const int rr = rg + j * RG;
+                            const T w0 = __shfl_sync(mask, w0h, (ONE && !LIN) ? PER + rr : rr, 16);
+                            if (c < PER && rr < PER) {
+                                C q = col[j * RG * PITCH];
+                                q.x += w0 * ar;
+                                q.y += w0 * ai;
+                                col[j * RG * PITCH] = q;
+                            }
+                        }
+                    } else {  // on a grid point: 2m + 1 taps on some axis
+                        const Rec r = rec[st.s];
+                        const T fr0 = r.fr[0], fr1 = r.fr[1];
+                        C *base = tile + (st.off & 0x7fffffff);
+                        for (int q = h; q < NT * NT; q += 16) {
+                            const int a0 = q / NT, a1 = q - a0 * NT;
+                            const T w = eval_tap<T, MM, LIN ? 2 : 1>(g, tab, 0, a0, fr0) *
+                                        eval_tap<T, MM, LIN ? 2 : 1>(g, tab + AS, 1, a1, fr1);
+                            C *pc = base + a0 * PITCH + a1;
+                            C t = *pc;
+                            t.x += w * v.x;
+                            t.y += w * v.y;
+                            *pc = t;
+                        }
+                    }
+                    __syncwarp(mask);
+                }
+            }
+            __syncthreads();  // the other colour class touches the same cells
+        }
+        // flush: cell (a0, a1) is grid point ((org0 - m + a0) mod n0, (org1 - m + a1) mod n1)
+        C z;
+        z.x = (T)0;
+        z.y = (T)0;
+        for (int idx = tid; idx < cells; idx += 32 * kStripeWarps) {
+            const int a0 = idx / TD1, a1 = idx - a0 * TD1;
+            C *pc = tile + a0 * PITCH + a1;
+            const C cv = *pc;
+            if (cv.x == (T)0 && cv.y == (T)0) continue;
+            *pc = z;
+            const size_t gi = (size_t)wrapn(org0 - MM + a0, g.n[0]) * g.n[1] +
+                              (size_t)wrapn(org1 - MM + a1, g.n[1]);
+            global_add(grid + gi, cv.x, cv.y);
+        }
+    }
+    finish_subproblems(sw.work);
+}
+
 // Shared memory left for the dynamic part once the static window tables are placed.
 template <typename T, int MM> constexpr size_t spread_dyn_limit()
 {
@@ -1183,7 +1440,8 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
     int method = g.spread_method;
     if (method == kSpreadAuto) {
         method = tile * kSpreadWarps <= 64 * 1024 ? kSpreadWarpPrivate : kSpreadWarpAtomic;
-        // measured fastest for 2-D: sixteen lanes per node in FP32, eight in FP64
+        // measured fastest for 2-D: sixteen lanes per node in FP32, eight in FP64 (both with
+        // private tiles)
         if (D == 2) method = sizeof(T) == 8 ? kSpreadOctet : kSpreadHalf;
         if (D == 3) method = kSpreadPlane;
     }
@@ -1197,6 +1455,9 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
     if (method == kSpreadOctet &&
         (D != 2 || 2 * MM + 1 > 16 || octet_tiles + spread_stage_bytes<T>() > limit))
         method = kSpreadWarpPrivate;
+    if (method == kSpreadStripe &&
+        (D != 2 || g.sw.R <= 0 || stripe_smem_bytes<T, MM>(g.bs[0] + 2 * MM) > limit))
+        method = kSpreadHalf;
     if (method == kSpreadHalf && (D != 2 || half_tiles + half_stage_bytes<T>() > 227 * 1024))
         method = kSpreadWarpPrivate;
     const size_t plane_tile = D == 3 ? ((size_t)(g.bs[0] + 2 * MM) * (size_t)(g.bs[1] + 2 * MM) *
@@ -1248,6 +1509,23 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
                 if (e != cudaSuccess) return e;
                 spread_half_kernel<T, MM, false><<<blocks, 32 * kHalfWarps, smem, stream>>>(
                     g, f, rec, perm, subs, nsub_total, grid);
+            }
+        }
+    } else if (method == kSpreadStripe) {
+        if constexpr (D == 2) {
+            const size_t smem = stripe_smem_bytes<T, MM>(g.bs[0] + 2 * MM);
+            if (g.lin_k) {
+                e = launch_persistent(spread_stripe_kernel<T, MM, true>, smem, 32 * kStripeWarps,
+                                      g.sw.max_items, blocks);
+                if (e != cudaSuccess) return e;
+                spread_stripe_kernel<T, MM, true><<<blocks, 32 * kStripeWarps, smem, stream>>>(
+                    g, f, rec, perm, grid);
+            } else {
+                e = launch_persistent(spread_stripe_kernel<T, MM, false>, smem, 32 * kStripeWarps,
+                                      g.sw.max_items, blocks);
+                if (e != cudaSuccess) return e;
+                spread_stripe_kernel<T, MM, false><<<blocks, 32 * kStripeWarps, smem, stream>>>(
+                    g, f, rec, perm, grid);
             }
         }
     } else if (method == kSpreadPlane) {

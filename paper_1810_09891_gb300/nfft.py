@@ -117,10 +117,12 @@ class Plan:
         """``window`` in {kaiser_bessel, gaussian, bspline, sinc} and ``window_table`` (K > 0:
         the window from a K-point-per-cell lookup table, PRE_LIN_PSI; 0: polynomials) change the
         approximation (they wait for the device to go idle); tuning: ``spread_method`` in {auto, thread,
-        warp_atomic, warp_private, octet, half}, ``interp_method`` in {auto, thread, warp, tile}, or
-        ``bin0`` / ``bin1`` / ``bin2`` (power-of-two bin sizes), ``subproblem`` (nodes per
-        spreading work item, a power of two in 32..1024). Changing a bin or subproblem size
-        discards the node precomputation; set the nodes again afterwards."""
+        warp_atomic, warp_private, octet, half, plane, stripe}, ``interp_method`` in {auto, thread,
+        warp, tile, octet}, or ``bin0`` / ``bin1`` / ``bin2`` (power-of-two bin sizes),
+        ``subproblem`` (nodes per spreading work item, a power of two in 32..1024),
+        ``stripe_item`` (nodes per work item of the stripe form, a power of two in 64..65536).
+        Changing a bin, subproblem or item size discards the node precomputation; set the nodes
+        again afterwards."""
         L = _lib.lib()
         if key == "window_table":
             check(L.nfft_set_option(self._h, _lib.OPT_WINDOW_TABLE, int(value)),
@@ -141,8 +143,9 @@ class Plan:
             check(L.nfft_set_option(self._h, _lib.OPT_INTERP_METHOD,
                                     _lib.INTERP_METHODS[value]), "nfft_set_option")
             return
-        if key in ("bin0", "bin1", "bin2", "subproblem"):
-            opt = _lib.OPT_SUBPROBLEM if key == "subproblem" else _lib.OPT_BIN[int(key[-1])]
+        if key in ("bin0", "bin1", "bin2", "subproblem", "stripe_item"):
+            opt = {"subproblem": _lib.OPT_SUBPROBLEM, "stripe_item": _lib.OPT_STRIPE_ITEM}.get(
+                key) or _lib.OPT_BIN[int(key[-1])]
             check(L.nfft_set_option(self._h, opt, int(value)), "nfft_set_option")
             info = _lib.NfftInfo()
             check(L.nfft_get_info(self._h, ctypes.byref(info)), "nfft_get_info")

@@ -115,16 +115,26 @@ def test_general_n_limits():
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_fft_length_errors.json")
 
 
-def _deconv_range(N, n, m):
-    """kappa = prod_t max|phihat_t| / min|phihat_t| over I_N: the spread of the deconvolution
-    factors 1 / phihat, by which rounding in the FFT is amplified relative to the result (it
-    grows like I0(m b) as sigma = n/N -> 1)."""
+def _deconv_range(N, n, m, band=None):
+    """kappa = prod_t max|phihat_t| / min|phihat_t| over I_N (or over |k_t| <= band_t): the
+    spread of the deconvolution factors 1 / phihat, by which rounding in the FFT is amplified
+    relative to the result (over I_N it grows like I0(m b) as sigma = n/N -> 1)."""
     k = 1.0
-    for Nt, nt in zip(N, n):
+    for t, (Nt, nt) in enumerate(zip(N, n)):
         b = oracle.kb_b(nt, Nt)
-        ph = [oracle.kb_phihat(j, nt, m, b) for j in range(-Nt // 2, Nt // 2)]
+        lim = Nt // 2 if band is None else band[t]
+        ph = [oracle.kb_phihat(j, nt, m, b) for j in range(-Nt // 2, Nt // 2) if abs(j) <= lim]
         k *= max(ph) / min(ph)
     return k
+
+
+def _low_band(N):
+    """Mask of the coefficients with |k_t| <= N_t / 4 on every axis (row-major, centred)."""
+    axes = [np.abs(np.arange(Nt) - Nt // 2) <= Nt // 4 for Nt in N]
+    mask = axes[0]
+    for a in axes[1:]:
+        mask = np.logical_and.outer(mask, a)
+    return mask
 
 
 @pytest.mark.parametrize("d", [1, 2, 3])
@@ -134,7 +144,9 @@ def test_paper_fft_length_sweep_on_gpu(d):
     deconvolution factors, 1.6 at sigma = 4, 1e9 and more as sigma -> 1, where the problem
     itself loses digits), and where that amplification is small against the printed errors,
     its errors E_2, E_inf against the NDFT track them (factor 1/4..5 above 1e-12, at most 5x or
-    2e-14 at the rounding floor)."""
+    2e-14 at the rounding floor). Coefficients supported away from the band edge
+    (|k_t| <= N_t/4, spread of 1/phihat there at most ~1e4) give a check within
+    max(1e-12, 50 eps kappa_low) <= 1e-9 at every printed n, forward and adjoint."""
     with open(GOLDEN) as fh:
         gold = json.load(fh)
     wl = gold["workloads"][str(d)]
@@ -147,13 +159,30 @@ def test_paper_fft_length_sweep_on_gpu(d):
     exact = oracle.ndft(x, fhat)
     xt = to_dev(x, torch.float64)
     ft = to_dev(fhat, torch.float64)
+    # a check whose rounding amplification stays small at every n: coefficients supported on
+    # |k_t| <= N_t / 4, away from the band edge where 1/phihat is largest; the adjoint is
+    # compared on the same coefficients
+    low = _low_band(N)
+    f_low = np.where(low, fhat, 0.0)
+    fl_t = to_dev(f_low, torch.float64)
+    w = W.gaussian_values(x.shape[0], 90 + d)
+    w_t = to_dev(w, torch.float64)
+    band = [Nt // 4 for Nt in N]
     for (n, e2_ref), (_, einf_ref) in zip(gold["E2"][str(d)], gold["Einf"][str(d)]):
         plan = Plan(N, x.shape[0], n=(n,) * d, m=m, dtype=torch.float64, device=DEV)
         plan.set_nodes(xt)
         y = plan.trafo(ft).cpu().numpy()
+        y_low = plan.trafo(fl_t).cpu().numpy()
+        h = plan.adjoint(w_t).cpu().numpy()
         plan.close()
         amp = 50 * np.finfo(np.float64).eps * _deconv_range(N, (n,) * d, m)
         assert rel_l2(y, oracle.nfft(x, fhat, n=(n,) * d, m=m)) <= max(1e-12, amp), n
+        amp_low = 50 * np.finfo(np.float64).eps * _deconv_range(N, (n,) * d, m, band)
+        assert amp_low <= 1e-9, (n, amp_low)  # a real check at every sweep length
+        tol_low = max(1e-12, amp_low)
+        assert rel_l2(y_low, oracle.nfft(x, f_low, n=(n,) * d, m=m)) <= tol_low, n
+        h_ref = oracle.nfft_adjoint(x, w, N, n=(n,) * d, m=m)
+        assert rel_l2(h[low], h_ref[low]) <= tol_low, n
         for e, ref in ((oracle.error_E2(exact, y), e2_ref),
                        (oracle.error_Einf(exact, y, fhat), einf_ref)):
             if ref >= 1e-12 and amp > ref / 10:
