@@ -866,12 +866,24 @@ def batched_record(args, dev, uuid, flush, torch):
         clk = clocks.stop(t0, t1) if clocks else None
         return sum(a.elapsed_time(c) for a, c in ev), clk
 
+    fused = b.fused
     b.capture(fhs, fs)
     total_ms, clk = timed_replays(True)
     # the same step plus the backward of the forward transform (grad fhat and grad x for an
     # output gradient per problem) in one graph
     b.capture(fhs, fs, grad_fs=gs)
     bwd_ms, _ = timed_replays()
+    # the same batch plan by plan (per-plan launches on eight side streams, parallel branches of
+    # the graph), for comparison
+    plan_by_plan = None
+    if fused:
+        b.set_fused(False)
+        b.capture(fhs, fs)
+        pbp_ms, _ = timed_replays()
+        plan_by_plan = {"ms_per_step": pbp_ms / steps,
+                        "nodes_per_s": sum(s["M"] for s in specs) * steps / (pbp_ms * 1e-3),
+                        "how": "per-plan launches on 8 side streams, one CUDA graph"}
+        b.set_fused(True)
     nodes = sum(s["M"] for s in specs)
     # whole-step HBM view: the algorithmic bytes of every plan's four kernel stages over the
     # step time
@@ -886,6 +898,7 @@ def batched_record(args, dev, uuid, flush, torch):
            "m": 4, "dtype": "f32", "steps": steps, "ms_per_step": total_ms / steps,
            "value": nodes * steps / (total_ms * 1e-3), "unit": UNIT,
            "graph": "one CUDA graph per step",
+           "fused": fused, "plan_by_plan": plan_by_plan,
            "roofline": {"bound": "hbm", "kernel": "whole step (all plans, all stages)",
                         "achieved": alg / step_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                         "frac": alg / step_s / 1e9 / hbm_peak, "traffic": None,
@@ -920,7 +933,8 @@ def batched(args):
             "data": "synthetic",
             "config": {"workload": r["workload"], "problems": r["problems"],
                        "nodes_per_step": r["nodes_per_step"], "m": 4, "graph": r["graph"],
-                       "tuned": r["tuned"], "l2": r["l2"]},
+                       "fused": r["fused"], "tuned": r["tuned"], "l2": r["l2"]},
+            "plan_by_plan": r["plan_by_plan"],
             "roofline": r["roofline"], "clocks": r["clocks"],
             "with_backward": r["with_backward"], "tuning": r["tuning"]}
     print(json.dumps(line))

@@ -38,7 +38,8 @@
  * makes the library refuse its own device allocations on the host, as if the device were out of
  * memory (NFFT_ENOMEM): it names the allocation sites to refuse, comma-separated ("tables" in
  * nfft_plan_create, "workspace" in nfft_set_nodes, "stage" in the _host calls, "lin" in
- * NFFT_OPT_WINDOW_TABLE), or "all". It is read at every allocation.
+ * NFFT_OPT_WINDOW_TABLE, "batch" in the first fused batch call), or "all". It is read at every
+ * allocation.
  *
  * Tracing: every stage of every call is wrapped in an NVTX range named "gbnfft <stage>" (see
  * enum nfft_stage), visible in any profiler that records NVTX.
@@ -168,6 +169,26 @@ int nfft_batch_adjoint(nfft_batch batch, const void *const *f, void *const *fhat
 /* Node gradient of every plan: gx[i] = nfft_grad_x(plan i, coef[i], w[i]). */
 int nfft_batch_grad_x(nfft_batch batch, const void *const *coef, const void *const *w,
                       void *const *gx);
+
+/* Fused execution of a batch. When the plans qualify - at most 128 plans, all d = 2 and
+ * NFFT_FP32, one m and one window kind, power-of-two n_t in 16..4096, the polynomial window
+ * (NFFT_OPT_WINDOW_TABLE 0), automatic or half-warp
+ * spreading (NFFT_OPT_SPREAD_METHOD 0 or 5) and automatic or thread interpolation - every batch
+ * call runs each stage for all plans in one launch on the batch's stream: the FFT passes over a
+ * work list of (plan, lines) blocks, the interpolation and node gradient over (plan, 128 nodes)
+ * blocks, and the spreading over the plans' subproblem lists concatenated and claimed by
+ * persistent CTAs. The first fused call allocates the per-plan tables (device memory and pinned
+ * host memory), uploads them on the batch's stream and waits for the upload; a call after a
+ * plan's workspace or tuning changed rebuilds them the same way. Make such a call before
+ * capturing the batch's calls into a CUDA graph (allocation and waiting are not allowed during
+ * capture). A batch whose plans no longer qualify runs plan by plan on the side streams. Results equal
+ * those of the plans' own calls up to the order of floating-point additions in the spreading.
+ * nfft_batch_set_fused(batch, 0) turns fused execution off (plan by plan on side streams, the
+ * default when the plans do not qualify); enable = 1 turns it on (the default) and returns
+ * NFFT_EUNSUPPORTED if the plans do not qualify. nfft_batch_get_fused reports whether the next
+ * call runs fused. */
+int nfft_batch_set_fused(nfft_batch batch, int enable);
+int nfft_batch_get_fused(nfft_batch batch, int *fused);
 
 /* Plan parameters after defaults: d, N[3], n[3], M, m, dtype, the tile (bin) size used to
  * sort the nodes, the workspace size and the window (NFFT_OPT_WINDOW). Unused trailing entries

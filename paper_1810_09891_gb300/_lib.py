@@ -81,6 +81,8 @@ SIGNATURES = {
     "nfft_batch_trafo": ([_P, _P, _P], _I),
     "nfft_batch_adjoint": ([_P, _P, _P], _I),
     "nfft_batch_grad_x": ([_P, _P, _P, _P], _I),
+    "nfft_batch_set_fused": ([_P, _I], _I),
+    "nfft_batch_get_fused": ([_P, ctypes.POINTER(_I)], _I),
 }
 
 OPT_SPREAD_METHOD = 1
@@ -93,7 +95,7 @@ OPT_STRIPE_ITEM = 9
 WINDOWS = {"kaiser_bessel": 0, "gaussian": 1, "bspline": 2, "sinc": 3}
 INTERP_METHODS = {"auto": 0, "thread": 1, "warp": 2, "tile": 3, "octet": 4}
 SPREAD_METHODS = {"auto": 0, "thread": 1, "warp_atomic": 2, "warp_private": 3, "octet": 4,
-                  "half": 5, "plane": 6, "stripe": 7}
+                  "half": 5, "plane": 6, "stripe": 7, "rows": 8}
 
 STAGES = ["set_nodes", "fft_forward", "interp", "zero_grid", "spread", "fft_adjoint", "grad"]
 

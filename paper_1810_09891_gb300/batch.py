@@ -1,5 +1,6 @@
-"""Many NFFTs of uneven size at once: a batch of plans, captured in one CUDA graph, with
-per-plan tuning by measurement.
+"""Many NFFTs of uneven size at once: a batch of plans, run fused (one launch per stage over all
+plans) or plan by plan on side streams, captured in one CUDA graph, with per-plan tuning by
+measurement.
 
 ``PlanBatch`` owns one ``Plan`` per problem (its own N, M, n, m, precision) and one library
 batch over them (``nfft_batch_*`` of the C ABI: the plans run concurrently on side streams
@@ -150,6 +151,19 @@ class PlanBatch:
         check(L.nfft_batch_size(self._b, ctypes.byref(cnt), ctypes.byref(ns)), "nfft_batch_size")
         self.n_streams = ns.value
         self.lane = [L.nfft_batch_lane(self._b, i) for i in range(k)]
+
+    @property
+    def fused(self) -> bool:
+        """Whether the next call runs every stage of all plans in one launch (nfft_batch_*
+        fused execution: 2-D FP32 plans with one m and window; see include/gbnfft.h)."""
+        v = ctypes.c_int()
+        check(_lib.lib().nfft_batch_get_fused(self._b, ctypes.byref(v)), "nfft_batch_get_fused")
+        return bool(v.value)
+
+    def set_fused(self, enable: bool) -> None:
+        """Turn fused execution on (NFFT_EUNSUPPORTED if the plans do not qualify) or off (plan
+        by plan on the side streams)."""
+        check(_lib.lib().nfft_batch_set_fused(self._b, int(bool(enable))), "nfft_batch_set_fused")
 
     def close(self):
         b = getattr(self, "_b", None)

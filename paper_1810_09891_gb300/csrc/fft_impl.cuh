@@ -18,6 +18,8 @@
 // factors are computed in FP64 at plan creation and stored in the plan's precision.
 #pragma once
 
+#include <algorithm>
+
 #include "gbnfft_internal.cuh"
 
 namespace gbnfft {
@@ -362,6 +364,9 @@ template <typename C, int LOGR, bool INV> __device__ __forceinline__ void dft_re
 // per 16, which keeps the stride-8 writes of the first stages free of bank conflicts.
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
+#ifndef GBNFFT_FFT_TWPOW
+#define GBNFFT_FFT_TWPOW 0
+#endif
 constexpr int kFftLogR = 3;  // largest stage radix 2^kFftLogR (radix 4 measured slower)
 constexpr int kFftR = 1 << kFftLogR;
 
@@ -443,12 +448,29 @@ __device__ __forceinline__ void r8_stage(const typename Cplx<T>::type *src,
         }
         const int kk = b & (NS - 1);
         if (LOGNS > 0) {
+#if GBNFFT_FFT_TWPOW
+            // one table read per butterfly; the other twiddles as its powers (depth 3)
+            C w[kFftR];
+            w[1] = tw[kk << (LOGL - LOGNS - LOGRS)];
+            if (INV) w[1].y = -w[1].y;
+            if (RS > 2) w[2] = cmul(w[1], w[1]);
+            if (RS > 3) w[3] = cmul(w[2], w[1]);
+            if (RS > 4) {
+                w[4] = cmul(w[2], w[2]);
+                w[5] = cmul(w[4], w[1]);
+                w[6] = cmul(w[4], w[2]);
+                w[7] = cmul(w[4], w[3]);
+            }
+#pragma unroll
+            for (int r = 1; r < RS; r++) a[r] = cmul(a[r], w[r]);
+#else
 #pragma unroll
             for (int r = 1; r < RS; r++) {
                 C w = tw[(r * kk) << (LOGL - LOGNS - LOGRS)];
                 if (INV) w.y = -w.y;
                 a[r] = cmul(a[r], w);
             }
+#endif
         }
         dft_reg<C, LOGRS, INV>(a);
         const int idx = ((b >> LOGNS) << (LOGNS + LOGRS)) + kk;
@@ -643,6 +665,78 @@ cudaError_t launch_fft_axis(const typename Cplx<T>::type *in, typename Cplx<T>::
     default: return cudaErrorInvalidValue;
     }
 #undef GB_FFT_CASE
+}
+
+// ------------------------------------------------------------------ fused batches
+// One pass of the pruned FFT for every plan of a batch in one launch: the CTAs walk a work list
+// of (plan, block) items, a block being P = kFusedFftThreads * 8 / L lines of the plan's length
+// L, so every item keeps the whole CTA busy whatever L is.
+namespace {
+
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kFusedFftThreads)
+    fft_fused_kernel(const FusedFftPass *__restrict__ passes,
+                     const FusedItem *__restrict__ items, int nitems,
+                     const __grid_constant__ FusedPtrs ptrs)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *S = reinterpret_cast<C *>(smem_raw);
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const FusedItem w = items[it];
+        const FusedFftPass q = passes[w.plan];
+        const C *in = static_cast<const C *>(q.in ? q.in : ptrs.in[w.plan]);
+        C *out = static_cast<C *>(q.out ? q.out : ptrs.out[w.plan]);
+        const C *tw = static_cast<const C *>(q.tw);
+        const T *dc = static_cast<const T *>(q.deconv);
+        switch (q.logl) {
+#define GB_FUSED_FFT(LG)                                                                          \
+    case LG:                                                                                      \
+        fftr_block<T, LG, INV>(in, out, q.outer, q.inner, q.Nt, q.P, q.LS, q.pad_mode, tw, dc,    \
+                               (long long)w.block, S);                                            \
+        break;
+            GB_FUSED_FFT(4)
+            GB_FUSED_FFT(5)
+            GB_FUSED_FFT(6)
+            GB_FUSED_FFT(7)
+            GB_FUSED_FFT(8)
+            GB_FUSED_FFT(9)
+            GB_FUSED_FFT(10)
+            GB_FUSED_FFT(11)
+            GB_FUSED_FFT(12)
+#undef GB_FUSED_FFT
+        default: break;
+        }
+        __syncthreads();  // the next item reuses the line buffers
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fft_fused(const FusedFftPass *passes, const FusedItem *items, int nitems,
+                             int sign, size_t smem, const FusedPtrs &ptrs, cudaStream_t stream)
+{
+    if (nitems <= 0) return cudaSuccess;
+    const void *k = sign > 0 ? reinterpret_cast<const void *>(fft_fused_kernel<T, true>)
+                             : reinterpret_cast<const void *>(fft_fused_kernel<T, false>);
+    cudaError_t e = ensure_dynamic_smem_ptr(k, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = sign > 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       &per_sm, fft_fused_kernel<T, true>, kFusedFftThreads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                       &per_sm, fft_fused_kernel<T, false>, kFusedFftThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidValue;
+    const int blocks = std::min(nitems, per_sm * num_sms());
+    if (sign > 0)
+        fft_fused_kernel<T, true><<<blocks, kFusedFftThreads, smem, stream>>>(passes, items,
+                                                                             nitems, ptrs);
+    else
+        fft_fused_kernel<T, false><<<blocks, kFusedFftThreads, smem, stream>>>(passes, items,
+                                                                              nitems, ptrs);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ any even length: Bluestein

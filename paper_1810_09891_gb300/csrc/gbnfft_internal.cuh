@@ -89,6 +89,7 @@ constexpr int kSpreadOctet = 4;
 constexpr int kSpreadHalf = 5;
 constexpr int kSpreadPlane = 6;
 constexpr int kSpreadStripe = 7;
+constexpr int kSpreadRows = 8;
 
 // Interpolation methods (see interp_impl.cuh).
 constexpr int kInterpAuto = 0;
@@ -177,9 +178,10 @@ constexpr int kStatusOk = 0;
 // Launchers (each enqueues on `stream`, returns cudaError_t of the launch)
 // ------------------------------------------------------------------------------------------
 
-// set_nodes: cell / row sub-bin / rank per node (a sub-bin is one grid row along axis 0 of a bin:
-// index bin * bs0 + row), then the bin totals, the scan over bins, the sub-bin starts, the
-// counting sort (scatter), then subproblems.
+// set_nodes: cell / row sub-bin / rank per node (a sub-bin is one grid row of a bin: the cell
+// along axis 0 in 1-D and 2-D, the (axis 0, axis 1) pair in 3-D; index bin * S0 + row with
+// S0 = bs0, or bs0 * bs1 in 3-D), then the bin totals, the scan over bins, the sub-bin starts,
+// the counting sort (scatter), then subproblems.
 template <typename T>
 cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *sub_count, int2 *sub_rank,
                             int *status, cudaStream_t stream);
@@ -253,6 +255,73 @@ template <typename T>
 cudaError_t launch_grad(const Geom &g, const typename Cplx<T>::type *grid,
                         const typename RecOf<T>::type *rec, const int *perm, int64_t M,
                         const typename Cplx<T>::type *w, T *gx, cudaStream_t stream);
+
+// ------------------------------------------------------------------------------------------
+// Fused batches: one launch per stage over every plan of a batch (see batch_fused.cu)
+// ------------------------------------------------------------------------------------------
+constexpr int kFusedMax = 128;          // plans of a fused batch (per-plan kernel arguments)
+constexpr int kFusedFftThreads = 512;   // threads of a fused FFT CTA: P = 4096 / L lines of L
+
+// Pointers that change from call to call, one per plan, passed to the kernels by value.
+struct FusedPtrs {
+    const void *in[kFusedMax];
+    void *out[kFusedMax];
+};
+
+// First CTA of every plan in the per-node stages (128 sorted nodes per CTA) and in the zeroing
+// of the grids, [kFusedMax + 1] entries each (the last one is the total), passed by value.
+struct FusedOffsets {
+    int node_block0[kFusedMax + 1];
+    int zero_block0[kFusedMax + 1];
+};
+
+// A work item: CTA-sized piece `block` of plan `plan`'s work in one stage.
+struct FusedItem {
+    int plan;
+    int block;
+};
+
+// One pruned-FFT pass of one plan (the arguments of launch_fft_axis, with P and LS fixed so that
+// a block is P lines of L = 2^logl points on kFusedFftThreads threads).
+struct FusedFftPass {
+    const void *in;      // input lines; null: the call's input pointer of the plan
+    void *out;           // output lines; null: the call's output pointer of the plan
+    long long outer, inner;
+    int logl, Nt, P, LS, pad_mode;
+    const void *tw;      // twiddles of the pass' length (plan precision)
+    const void *deconv;  // deconvolution factors of the pass' axis (plan precision)
+};
+
+// The per-node stages of one plan (interpolation, node gradient, spreading) in a fused launch.
+struct FusedNodePlan {
+    Geom g;
+    void *grid;          // the plan's oversampled grid (gA)
+    const void *rec;     // sorted node records
+    const int *perm;     // sorted position -> caller's node index
+    const SubProb *subs; // spreading subproblems of the plan
+    const int *nsub;     // [0]: number of subproblems
+    int M;
+    long long G;         // |I_n|
+};
+
+template <typename T>
+cudaError_t launch_fft_fused(const FusedFftPass *passes, const FusedItem *items, int nitems,
+                             int sign, size_t smem, const FusedPtrs &ptrs, cudaStream_t stream);
+// FP32, d = 2 (batch_fused.cu): zeroing of the plans' grids, interpolation (grad = false: out[p]
+// = f_p) or node gradient (grad = true: in[p] = w_p, out[p] = gx_p), and half-warp spreading
+// (in[p] = f_p) with its item prefix. g0 is any plan's geometry (m is shared); shared_window:
+// every plan has g0's window polynomials.
+int zero_fused_blocks(long long G, size_t csize);
+cudaError_t launch_zero_fused(const FusedNodePlan *plans, int nplans, const FusedOffsets &off,
+                              size_t csize, cudaStream_t stream);
+cudaError_t launch_interp_fused(const FusedNodePlan *plans, int nplans, const FusedOffsets &off,
+                                const Geom &g0, const FusedPtrs &ptrs, bool grad,
+                                bool shared_window, cudaStream_t stream);
+cudaError_t launch_spread_fused(const FusedNodePlan *plans, int nplans, int *item_start,
+                                int *work, int max_items, int tile_cells, const Geom &g0,
+                                const FusedPtrs &ptrs, cudaStream_t stream);
+int half_tile_cells_f32(int m, int bs0, int bs1);  // cells of one half-warp tile (FP32)
+size_t half_smem_bytes_f32(int tile_cells);         // shared memory of the half-warp form
 
 // Dispatch on the window cutoff m (kernels are instantiated for m = 1..kMaxM).
 #define GBNFFT_DISPATCH_M(FN, T, D, ...)                                                          \

@@ -2,7 +2,7 @@
 //   f_j = sum_{l in I_{n,m}(x_j)} g_{l mod n} prod_t psi_t(n_t x_{j,t} - l_t),
 // and the derivative of the same sum with respect to the node coordinates (node gradient).
 //
-// Thread form (default but for 3-D FP32): one thread per node, nodes visited in bin-sorted
+// Thread form (default): one thread per node, nodes visited in bin-sorted
 // order so that the threads of a warp read neighbouring grid cells (L1/L2 reuse of the
 // oversampled grid). The window values of the inner axes are evaluated once per node into
 // registers from the per-tap polynomials (kernel-argument tables, read as warp-wide
@@ -10,8 +10,8 @@
 // node on a grid point) use 2m+1 taps per axis; all other nodes use 2m (the closed support of
 // eq. Inm).
 //
-// Warp form (option): one warp per node, the lanes cover the node's taps. Octet form (default
-// for 3-D FP32 with m <= 4): eight lanes per node along the last axis (see below). Tiled form
+// Warp form (option): one warp per node, the lanes cover the node's taps. Octet form (option,
+// d = 2, 3 with m <= 4): eight lanes per node along the last axis (see below). Tiled form
 // (option): gathers from a shared-memory copy of the bin's tile.
 #pragma once
 
@@ -689,10 +689,10 @@ cudaError_t launch_interp_m(const Geom &g, const typename Cplx<T>::type *grid,
     const size_t tile = cells * sizeof(C);
     constexpr size_t tables = kMaxDim * poly_axis_stride(sizeof(T) == 8, MM) * sizeof(T);
     int method = g.interp_method;
-    // measured fastest on the GB300: the octet form for 3-D FP32 (m <= 4; clustered 3-D
-    // workload 1.53 ms against 1.71 ms), the thread form everywhere else
-    if (method == kInterpAuto)
-        method = (D == 3 && sizeof(T) == 4 && 2 * MM <= 8) ? kInterpOctet : kInterpThread;
+    // measured fastest on the GB300: the thread form everywhere (with the nodes of a bin
+    // ordered by grid row, the clustered 3-D workload takes 1.08 ms against 1.41 ms for the
+    // octet form)
+    if (method == kInterpAuto) method = kInterpThread;
     if (method == kInterpTile && tile + tables > 227 * 1024) method = kInterpThread;
     if (method == kInterpTile) {
         cudaError_t e = ensure_dynamic_smem(interp_tile_kernel<T, D, MM>, tile);

@@ -49,9 +49,14 @@ __device__ __forceinline__ bool node_pos(T xt, int n, long long &base, double &f
     return true;
 }
 
-// Sort key of a node: its bin, and inside the bin its row along axis 0 (a sub-bin of one grid
-// row): nodes of a bin end up ordered by that row, so that neighbouring threads of the
-// interpolation read the same grid rows.
+// Sort key of a node: its bin, and inside the bin its grid row (a sub-bin: the cell along axis 0
+// in 1-D and 2-D, the (axis 0, axis 1) cell pair in 3-D): nodes of a bin end up ordered by row,
+// so that neighbouring threads of the interpolation read the same grid rows.
+__host__ __device__ inline int row_subbins(const Geom &g)
+{
+    return g.d == 3 ? g.bs[0] * g.bs[1] : g.bs[0];
+}
+
 template <typename T>
 __global__ void node_bin_kernel(Geom g, const T *__restrict__ x, int M, int *__restrict__ sub_count,
                                 int2 *__restrict__ sub_rank, int *__restrict__ status)
@@ -68,9 +73,10 @@ __global__ void node_bin_kernel(Geom g, const T *__restrict__ x, int M, int *__r
         if (b < 0) b += g.n[t];
         bin = bin * g.nb[t] + ((int)b >> g.bslog[t]);
         if (t == 0) row = (int)b & (g.bs[0] - 1);
+        if (t == 1 && g.d == 3) row = row * g.bs[1] + ((int)b & (g.bs[1] - 1));
     }
     if (!ok) atomicCAS(status, kStatusOk, (int)NFFT_EBADNODE);
-    const int sub = bin * g.bs[0] + row;
+    const int sub = bin * row_subbins(g) + row;
     const int rank = atomicAdd(&sub_count[sub], 1);
     sub_rank[j] = make_int2(sub, rank);
 }
@@ -86,7 +92,7 @@ cudaError_t launch_node_bin(const Geom &g, const T *x, int64_t M, int *sub_count
     return cudaGetLastError();
 }
 
-// Per bin: its node count, the sum over its bs0 row sub-bins.
+// Per bin: its node count, the sum over its S0 row sub-bins.
 __global__ void bin_totals_kernel(const int *__restrict__ sub_count, int S0, int nbins,
                                   int *__restrict__ bin_count)
 {

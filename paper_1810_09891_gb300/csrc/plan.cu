@@ -261,7 +261,7 @@ struct gbnfft_plan {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     Region gA, gB, rec, perm, binrank, bincount, binstart, substart, nsub, subs, blu;
-    Region rowcount, rowstart;  // row sub-bins (bs0 per bin): node counts and first positions
+    Region rowcount, rowstart;  // row sub-bins of the bins: node counts and first positions
     // stripe-form spreading work (d = 2): super-bin counts, scans and items
     Region sbcount, sbstart, sbsub, sbn, sitems;
     int stripe_R = 0, stripe_nsb1 = 0, stripe_nsb = 0, stripe_max_items = 0;
@@ -315,8 +315,9 @@ void layout_workspace(gbnfft_plan *p)
     put(p->bincount, size_t(p->nbins) * sizeof(int));
     put(p->binstart, size_t(p->nbins) * sizeof(int));
     put(p->substart, size_t(p->nbins) * sizeof(int));
-    put(p->rowcount, size_t(p->nbins) * p->geom.bs[0] * sizeof(int));
-    put(p->rowstart, size_t(p->nbins) * p->geom.bs[0] * sizeof(int));
+    const size_t S0 = size_t(p->geom.bs[0]) * (p->d == 3 ? p->geom.bs[1] : 1);
+    put(p->rowcount, size_t(p->nbins) * S0 * sizeof(int));
+    put(p->rowstart, size_t(p->nbins) * S0 * sizeof(int));
     put(p->nsub, 16);
     put(p->subs, size_t(p->max_subs) * sizeof(SubProb));
     put(p->blu, 2 * p->blu_elems * p->csize);
@@ -531,7 +532,7 @@ template <typename T> int do_set_nodes(gbnfft_plan *p, const void *x)
     cudaStream_t s = p->stream;
     int *count = at<int>(p, p->bincount);
     int *rows = at<int>(p, p->rowcount);
-    const int S0 = p->geom.bs[0];
+    const int S0 = p->geom.bs[0] * (p->d == 3 ? p->geom.bs[1] : 1);  // row sub-bins per bin
     GB_CHECK(cudaMemsetAsync(rows, 0, size_t(p->nbins) * S0 * sizeof(int), s));
     GB_CHECK(launch_node_bin<T>(p->geom, static_cast<const T *>(x), p->M, rows,
                                 at<int2>(p, p->binrank), p->d_status, s));
@@ -1169,7 +1170,7 @@ int nfft_set_option(nfft_plan p, int key, int64_t value)
     if (!p) return NFFT_EINVAL;
     switch (key) {
     case NFFT_OPT_SPREAD_METHOD:
-        if (value < kSpreadAuto || value > kSpreadStripe) return NFFT_EINVAL;
+        if (value < kSpreadAuto || value > kSpreadRows) return NFFT_EINVAL;
         p->geom.spread_method = (int)value;
         return NFFT_OK;
     case NFFT_OPT_INTERP_METHOD:
@@ -1395,6 +1396,24 @@ int nfft_adjoint_host(nfft_plan p, const void *f_host, void *fhat_host)
 // (the plan's own stream is swapped for the duration of the call), and joins the side streams
 // back with one event each. Plans go to lanes largest first, each to the lane with the least
 // work so far (work ~ M + |I_n|). The pattern records into a CUDA graph as parallel branches.
+//
+// A batch whose plans qualify is run fused instead (see batch_fused.cu): one launch per stage
+// over all plans, in the batch's stream, from per-plan tables and work lists kept in one device
+// block (uploaded from pinned host memory, waited for once). The tables are rebuilt when a
+// plan's workspace or tuning changed since they were built.
+enum FusedPass { kFwdRows = 0, kFwdCols = 1, kAdjCols = 2, kAdjRows = 3, kFusedPasses = 4 };
+
+struct FusedSig {  // the plan state the fused tables depend on
+    const void *ws;
+    int bs[3], spread, interp, lin_k, window;
+    bool operator==(const FusedSig &o) const
+    {
+        return ws == o.ws && bs[0] == o.bs[0] && bs[1] == o.bs[1] && bs[2] == o.bs[2] &&
+               spread == o.spread && interp == o.interp && lin_k == o.lin_k &&
+               window == o.window;
+    }
+};
+
 struct gbnfft_batch {
     std::vector<gbnfft_plan *> plans;
     std::vector<int> lane;
@@ -1403,6 +1422,20 @@ struct gbnfft_batch {
     cudaEvent_t fork = nullptr;
     cudaStream_t stream = nullptr;
     int device = 0;
+    // fused execution
+    bool fused = false;           // run fused (requested and the plans qualify)
+    bool fused_wanted = true;
+    std::vector<FusedSig> sig;    // per plan, when the tables were built
+    char *fdev = nullptr;         // device block: node plans, passes, items, prefix, counters
+    char *fhost = nullptr;        // pinned host image of the same block
+    size_t fbytes = 0;
+    size_t off_nodes = 0, off_pass[kFusedPasses] = {}, off_items[kFusedPasses] = {};
+    size_t off_istart = 0, off_work = 0;
+    int nitems[kFusedPasses] = {};
+    size_t fft_smem[kFusedPasses] = {};
+    int node_blocks = 0, zero_blocks = 0, max_items = 0, tile_cells = 0;
+    bool shared_window = false;  // every plan has the same window polynomials
+    FusedOffsets offsets{};      // per-plan first blocks of the per-node and zeroing stages
 };
 
 namespace {
@@ -1414,7 +1447,263 @@ void batch_free(gbnfft_batch *b)
     for (cudaEvent_t e : b->join)
         if (e) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->fdev) cudaFree(b->fdev);
+    if (b->fhost) cudaFreeHost(b->fhost);
     delete b;
+}
+
+FusedSig fused_sig(const gbnfft_plan *p)
+{
+    FusedSig s{};
+    s.ws = p->ws;
+    for (int t = 0; t < 3; t++) s.bs[t] = p->geom.bs[t];
+    s.spread = p->geom.spread_method;
+    s.interp = p->geom.interp_method;
+    s.lin_k = p->lin_k;
+    s.window = p->window;
+    return s;
+}
+
+// Whether the plans can run fused: 2-D FP32, one m and window, the half-warp spreading form and
+// the thread interpolation form (automatic or chosen), polynomial window, power-of-two FFT
+// lengths 16..4096.
+bool fusable(const gbnfft_batch *b)
+{
+    const auto &ps = b->plans;
+    if (ps.empty() || ps.size() > size_t(kFusedMax)) return false;
+    const gbnfft_plan *p0 = ps[0];
+    size_t cells = 0;
+    for (const gbnfft_plan *p : ps) {
+        if (p->d != 2 || p->dtype != NFFT_FP32 || p->m != p0->m || p->window != p0->window ||
+            p->lin_k != 0)
+            return false;
+        if (p->geom.spread_method != kSpreadAuto && p->geom.spread_method != kSpreadHalf)
+            return false;
+        if (p->geom.interp_method != kInterpAuto && p->geom.interp_method != kInterpThread)
+            return false;
+        for (int t = 0; t < 2; t++)
+            if (!is_pow2(p->n[t]) || p->n[t] < 16 || p->n[t] > 4096 || p->blu_M[t]) return false;
+        cells = std::max(cells, size_t(half_tile_cells_f32(p->m, p->geom.bs[0], p->geom.bs[1])));
+    }
+    // private tiles and staging of the half-warp form in shared memory, beside static data
+    return half_smem_bytes_f32((int)cells) <= 200 * 1024;
+}
+
+// Row stride (cells) of a line buffer of the radix-8 FFT for P lines of L (as launch_fftr).
+int fused_ls(int L, int P, bool strided)
+{
+    int LS = 2 * (L + L / 16);
+    if (strided && P > 1) {
+        const int cells = 128 / (int)sizeof(float2);
+        const int want = (cells / P) % cells;
+        LS += ((want - LS % cells) + cells) % cells;
+    }
+    return LS;
+}
+
+// (Re)build the fused tables from the plans' current state and enqueue their upload.
+int fused_build(gbnfft_batch *b)
+{
+    const int n = (int)b->plans.size();
+    std::vector<FusedNodePlan> nodes(n);
+    std::vector<FusedFftPass> pass[kFusedPasses];
+    std::vector<FusedItem> items[kFusedPasses];
+    int node_blocks = 0, zero_blocks = 0, max_items = 0, cells = 0;
+    for (int i = 0; i < n; i++) {
+        gbnfft_plan *p = b->plans[i];
+        FusedNodePlan &q = nodes[i];
+        std::memset(&q, 0, sizeof(q));
+        q.g = p->geom;
+        q.g.sw = StripeWork{};
+        q.grid = at<float2>(p, p->gA);
+        q.rec = at<RecF>(p, p->rec);
+        q.perm = at<int>(p, p->perm);
+        q.subs = at<SubProb>(p, p->subs);
+        q.nsub = at<int>(p, p->nsub);
+        q.M = (int)p->M;
+        q.G = p->G;
+        b->offsets.node_block0[i] = node_blocks;
+        b->offsets.zero_block0[i] = zero_blocks;
+        node_blocks += (int)((p->M + 127) / 128);
+        zero_blocks += zero_fused_blocks(p->G, sizeof(float2));
+        max_items += p->max_subs;
+        cells = std::max(cells, half_tile_cells_f32(p->m, p->geom.bs[0], p->geom.bs[1]));
+        // the four pruned passes of Algorithm "NFFT" (rows then columns, D fused) and of
+        // Algorithm "adjoint NFFT" (columns then rows, D^H fused)
+        float2 *A = at<float2>(p, p->gA), *B = at<float2>(p, p->gB);
+        const int n0 = (int)p->n[0], n1 = (int)p->n[1], N0 = (int)p->N[0], N1 = (int)p->N[1];
+        const int Pr = kFusedFftThreads * 8 / n1, Pc = kFusedFftThreads * 8 / n0;
+        const FusedFftPass q4[kFusedPasses] = {
+            {nullptr, B, N0, 1, ilog2(n1), N1, Pr, fused_ls(n1, Pr, false), 1, p->tw[1],
+             p->deconv[1]},
+            {B, A, 1, n1, ilog2(n0), N0, Pc, fused_ls(n0, Pc, true), 1, p->tw[0], p->deconv[0]},
+            {A, B, 1, n1, ilog2(n0), N0, Pc, fused_ls(n0, Pc, true), 0, p->tw[0], p->deconv[0]},
+            {B, nullptr, N0, 1, ilog2(n1), N1, Pr, fused_ls(n1, Pr, false), 0, p->tw[1],
+             p->deconv[1]}};
+        for (int k = 0; k < kFusedPasses; k++) {
+            const FusedFftPass &f = q4[k];
+            pass[k].push_back(f);
+            const long long blocks = f.inner == 1 ? (f.outer + f.P - 1) / f.P
+                                                  : f.outer * ((f.inner + f.P - 1) / f.P);
+            for (long long blk = 0; blk < blocks; blk++) items[k].push_back({i, (int)blk});
+            b->fft_smem[k] = std::max(b->fft_smem[k], size_t(f.P) * f.LS * sizeof(float2));
+        }
+    }
+    // one block: node plans, passes and items of the four passes, item prefix, counters
+    size_t off = 0;
+    auto put = [&](size_t bytes) {
+        off = align_up(off, 256);
+        const size_t at0 = off;
+        off += bytes;
+        return at0;
+    };
+    b->off_nodes = put(n * sizeof(FusedNodePlan));
+    for (int k = 0; k < kFusedPasses; k++) {
+        b->off_pass[k] = put(n * sizeof(FusedFftPass));
+        b->off_items[k] = put(items[k].size() * sizeof(FusedItem));
+        b->nitems[k] = (int)items[k].size();
+    }
+    b->off_istart = put((n + 1) * sizeof(int));
+    b->off_work = put(4 * sizeof(int));
+    const size_t need = align_up(off, 256);
+    if (need > b->fbytes) {
+        if (b->fdev) {
+            cudaStreamSynchronize(b->stream);
+            cudaFree(b->fdev);
+            cudaFreeHost(b->fhost);
+            b->fdev = nullptr;
+            b->fhost = nullptr;
+            b->fbytes = 0;
+        }
+        void *d = nullptr, *h = nullptr;
+        if (dev_alloc(&d, need, "batch") != cudaSuccess) {
+            cudaGetLastError();
+            return NFFT_ENOMEM;
+        }
+        if (cudaMallocHost(&h, need) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(d);
+            return NFFT_ENOMEM;
+        }
+        b->fdev = static_cast<char *>(d);
+        b->fhost = static_cast<char *>(h);
+        b->fbytes = need;
+    } else {
+        // the pinned image may still be read by an upload in flight
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) return NFFT_ECUDA;
+    }
+    std::memset(b->fhost, 0, need);
+    std::memcpy(b->fhost + b->off_nodes, nodes.data(), n * sizeof(FusedNodePlan));
+    for (int k = 0; k < kFusedPasses; k++) {
+        std::memcpy(b->fhost + b->off_pass[k], pass[k].data(), n * sizeof(FusedFftPass));
+        std::memcpy(b->fhost + b->off_items[k], items[k].data(),
+                    items[k].size() * sizeof(FusedItem));
+    }
+    // complete before any stream uses the tables (later calls may come on another stream)
+    GB_CHECK(cudaMemcpyAsync(b->fdev, b->fhost, need, cudaMemcpyHostToDevice, b->stream));
+    GB_CHECK(cudaStreamSynchronize(b->stream));
+    b->offsets.node_block0[n] = node_blocks;
+    b->offsets.zero_block0[n] = zero_blocks;
+    b->shared_window = true;
+    for (int i = 1; i < n; i++)
+        b->shared_window &= b->plans[i]->poly_host == b->plans[0]->poly_host;
+    b->node_blocks = node_blocks;
+    b->zero_blocks = zero_blocks;
+    b->max_items = max_items;
+    b->tile_cells = cells;
+    b->sig.resize(n);
+    for (int i = 0; i < n; i++) b->sig[i] = fused_sig(b->plans[i]);
+    return NFFT_OK;
+}
+
+// Tables current for the plans' state (rebuilt if a plan changed); false if the plans no
+// longer qualify (the call then runs plan by plan).
+int fused_ready(gbnfft_batch *b, bool &use)
+{
+    use = false;
+    if (!b->fused_wanted) return NFFT_OK;
+    bool same = b->fdev && b->sig.size() == b->plans.size();
+    for (size_t i = 0; same && i < b->plans.size(); i++)
+        same = b->sig[i] == fused_sig(b->plans[i]);
+    if (!same) {
+        if (!fusable(b)) return NFFT_OK;
+        const int rc = fused_build(b);
+        if (rc) return rc;
+    }
+    use = true;
+    return NFFT_OK;
+}
+
+template <typename P> P *fused_at(gbnfft_batch *b, size_t off)
+{
+    return reinterpret_cast<P *>(b->fdev + off);
+}
+
+int fused_fft(gbnfft_batch *b, int k, int sign, const FusedPtrs &ptrs)
+{
+    GB_CHECK(launch_fft_fused<float>(fused_at<FusedFftPass>(b, b->off_pass[k]),
+                                     fused_at<FusedItem>(b, b->off_items[k]), b->nitems[k], sign,
+                                     b->fft_smem[k], ptrs, b->stream));
+    return NFFT_OK;
+}
+
+int fused_trafo(gbnfft_batch *b, const void *const *fhat, void *const *f)
+{
+    FusedPtrs ptrs{};
+    for (size_t i = 0; i < b->plans.size(); i++) {
+        ptrs.in[i] = fhat[i];
+        ptrs.out[i] = f[i];
+    }
+    int rc = fused_fft(b, kFwdRows, -1, ptrs);
+    if (!rc) rc = fused_fft(b, kFwdCols, -1, ptrs);
+    if (rc) return rc;
+    GB_CHECK(launch_interp_fused(fused_at<FusedNodePlan>(b, b->off_nodes), (int)b->plans.size(),
+                                 b->offsets, b->plans[0]->geom, ptrs, false,
+                                 b->shared_window, b->stream));
+    return NFFT_OK;
+}
+
+int fused_adjoint(gbnfft_batch *b, const void *const *f, void *const *fhat)
+{
+    FusedPtrs ptrs{};
+    for (size_t i = 0; i < b->plans.size(); i++) {
+        ptrs.in[i] = f[i];
+        ptrs.out[i] = fhat[i];
+    }
+    const int n = (int)b->plans.size();
+    FusedNodePlan *nodes = fused_at<FusedNodePlan>(b, b->off_nodes);
+    GB_CHECK(launch_zero_fused(nodes, n, b->offsets, sizeof(float2), b->stream));
+    GB_CHECK(launch_spread_fused(nodes, n, fused_at<int>(b, b->off_istart),
+                                 fused_at<int>(b, b->off_work), b->max_items, b->tile_cells,
+                                 b->plans[0]->geom, ptrs, b->stream));
+    int rc = fused_fft(b, kAdjCols, +1, ptrs);
+    if (!rc) rc = fused_fft(b, kAdjRows, +1, ptrs);
+    return rc;
+}
+
+int fused_grad(gbnfft_batch *b, const void *const *coef, const void *const *w, void *const *gx)
+{
+    FusedPtrs ptrs{};
+    for (size_t i = 0; i < b->plans.size(); i++) ptrs.in[i] = coef[i];
+    int rc = fused_fft(b, kFwdRows, -1, ptrs);
+    if (!rc) rc = fused_fft(b, kFwdCols, -1, ptrs);
+    if (rc) return rc;
+    for (size_t i = 0; i < b->plans.size(); i++) {
+        ptrs.in[i] = w[i];
+        ptrs.out[i] = gx[i];
+    }
+    GB_CHECK(launch_interp_fused(fused_at<FusedNodePlan>(b, b->off_nodes), (int)b->plans.size(),
+                                 b->offsets, b->plans[0]->geom, ptrs, true,
+                                 b->shared_window, b->stream));
+    return NFFT_OK;
+}
+
+int batch_device(gbnfft_batch *b)
+{
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return NFFT_ECUDA;
+    if (cur != b->device && cudaSetDevice(b->device) != cudaSuccess) return NFFT_ECUDA;
+    return NFFT_OK;
 }
 
 // fn(plan, i) for every plan of the batch on its lane; the batch stream waits for all of them.
@@ -1545,6 +1834,13 @@ int nfft_batch_trafo(nfft_batch b, const void *const *fhat, void *const *f)
         if (!p->nodes_ready) return NFFT_ENOTREADY;
         if (check_dev_ptr(p, fhat[i], p->NN) || check_dev_ptr(p, f[i], p->M)) return NFFT_EINVAL;
     }
+    bool use = false;
+    int rc = fused_ready(b, use);
+    if (rc) return rc;
+    if (use) {
+        if (batch_device(b)) return NFFT_ECUDA;
+        return fused_trafo(b, fhat, f);
+    }
     return batch_run(b, [&](gbnfft_plan *p, size_t i) { return nfft_trafo(p, fhat[i], f[i]); });
 }
 
@@ -1555,6 +1851,13 @@ int nfft_batch_adjoint(nfft_batch b, const void *const *f, void *const *fhat)
         const gbnfft_plan *p = b->plans[i];
         if (!p->nodes_ready) return NFFT_ENOTREADY;
         if (check_dev_ptr(p, f[i], p->M) || check_dev_ptr(p, fhat[i], p->NN)) return NFFT_EINVAL;
+    }
+    bool use = false;
+    int rc = fused_ready(b, use);
+    if (rc) return rc;
+    if (use) {
+        if (batch_device(b)) return NFFT_ECUDA;
+        return fused_adjoint(b, f, fhat);
     }
     return batch_run(b, [&](gbnfft_plan *p, size_t i) { return nfft_adjoint(p, f[i], fhat[i]); });
 }
@@ -1569,9 +1872,35 @@ int nfft_batch_grad_x(nfft_batch b, const void *const *coef, const void *const *
         if (check_dev_ptr(p, coef[i], p->NN) || check_dev_ptr(p, w[i], p->M)) return NFFT_EINVAL;
         if (p->M > 0 && (!gx[i] || !aligned(gx[i], p->rsize))) return NFFT_EINVAL;
     }
+    bool use = false;
+    int rc = fused_ready(b, use);
+    if (rc) return rc;
+    if (use) {
+        if (batch_device(b)) return NFFT_ECUDA;
+        return fused_grad(b, coef, w, gx);
+    }
     return batch_run(b, [&](gbnfft_plan *p, size_t i) {
         return nfft_grad_x(p, coef[i], w[i], gx[i]);
     });
+}
+
+int nfft_batch_set_fused(nfft_batch b, int enable)
+{
+    if (!b) return NFFT_EINVAL;
+    if (!enable) {
+        b->fused_wanted = false;
+        return NFFT_OK;
+    }
+    if (!fusable(b)) return NFFT_EUNSUPPORTED;
+    b->fused_wanted = true;
+    return NFFT_OK;
+}
+
+int nfft_batch_get_fused(nfft_batch b, int *fused)
+{
+    if (!b || !fused) return NFFT_EINVAL;
+    *fused = (b->fused_wanted && fusable(b)) ? 1 : 0;
+    return NFFT_OK;
 }
 
 }  // extern "C"

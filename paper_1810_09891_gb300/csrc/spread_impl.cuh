@@ -794,12 +794,39 @@ __host__ __device__ constexpr size_t half_stage_bytes()
     return kHalfChunk * (sizeof(HalfStage<T>) + sizeof(typename Cplx<T>::type));
 }
 
+// Shared memory of the half-warp form: the staged chunk of nodes first, then the kHalfTiles
+// private tiles (td0 rows of `pitch` cells each).
+template <typename T>
+__device__ __forceinline__ typename Cplx<T>::type *half_tiles(unsigned char *smem)
+{
+    return reinterpret_cast<typename Cplx<T>::type *>(smem + half_stage_bytes<T>());
+}
+
+// Window polynomials of the half-warp form in registers: column tap c + 1 of axis 1 and row tap
+// h + 1 of axis 0 (coefficient k of tap i at [k * kPolyTaps + i - 1]); lanes past the 2m taps
+// hold zeros.
+template <typename T, int MM>
+__device__ __forceinline__ void half_coefficients(const T *__restrict__ tab, T *cc, T *cr)
+{
+    using Sh = HalfShape<MM>;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    const int h = threadIdx.x & 15, c = h & (Sh::CW - 1);
+#pragma unroll
+    for (int k = 0; k <= DEG; k++) {
+        cc[k] = c < Sh::PER ? tab[AS + k * kPolyTaps + c] : (T)0;
+        cr[k] = h < Sh::PER ? tab[k * kPolyTaps + h] : (T)0;
+    }
+}
+
+// One subproblem of the half-warp form: the CTA stages its nodes a chunk at a time, every
+// half-warp adds one node after another into its private tile, and the flush adds the CTA's
+// tiles into the grid and zeroes them.
 template <typename T, int MM, bool LIN>
-__global__ void __launch_bounds__(32 * kHalfWarps)
-    spread_half_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
-                       const typename RecOf<T>::type *__restrict__ rec,
-                       const int *__restrict__ perm, const SubProb *__restrict__ subs,
-                       int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
+__device__ __forceinline__ void half_subproblem(
+    const Geom &g, const SubProb &P, const typename Cplx<T>::type *__restrict__ f,
+    const typename RecOf<T>::type *__restrict__ rec, const int *__restrict__ perm,
+    typename Cplx<T>::type *__restrict__ grid, unsigned char *smem, const T *cc, const T *cr)
 {
     using C = typename Cplx<T>::type;
     using Rec = typename RecOf<T>::type;
@@ -808,8 +835,7 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
     constexpr int NT = 2 * MM + 1;
     constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
     constexpr int DEG = PolyDeg<T, MM>::value;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const T *tab = static_cast<const T *>(g.poly);  // read once into registers (and on edges)
+    const T *tab = static_cast<const T *>(g.poly);  // global table (taps of grid-point nodes)
     const int tid = threadIdx.x, lane = tid & 31;
     const int h = lane & 15, half = tid >> 4;
     const unsigned mask = 0xffffu << (lane & 16);
@@ -817,137 +843,283 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
     const int td0 = g.bs[0] + 2 * MM, td1 = g.bs[1] + 2 * MM;
     const int pitch = half_pitch<T, MM>(td1);
     const int tcells = td0 * pitch;
-    C *tiles = reinterpret_cast<C *>(smem_raw);
-    C *mine = tiles + (size_t)half * tcells;
-    HalfStage<T> *st_node =
-        reinterpret_cast<HalfStage<T> *>(smem_raw + (size_t)kHalfTiles * tcells * sizeof(C));
+    HalfStage<T> *st_node = reinterpret_cast<HalfStage<T> *>(smem);
     C *st_val = reinterpret_cast<C *>(st_node + kHalfChunk);
-    // column tap c + 1 of axis 1 and row tap h + 1 of axis 0 (coefficient k of tap i at
-    // [k * kPolyTaps + i - 1]); lanes past the 2m taps hold zeros
-    T cc[DEG + 1], cr[DEG + 1];
-#pragma unroll
-    for (int k = 0; k <= DEG; k++) {
-        cc[k] = c < PER ? tab[AS + k * kPolyTaps + c] : (T)0;
-        cr[k] = h < PER ? tab[k * kPolyTaps + h] : (T)0;
-    }
+    C *tiles = half_tiles<T>(smem);
+    C *mine = tiles + (size_t)half * tcells;
+    C *const lane_col = mine + rg * pitch + c;
     const T e0 = (T)g.win[0].edge_w, e1 = (T)g.win[1].edge_w;
+    const int org1 = (P.bin % g.nb[1]) * g.bs[1];
+    const int org0 = (P.bin / g.nb[1]) * g.bs[0];
+    Rec r_next;
+    C v_next;
+    if (tid < P.count) {
+        r_next = rec[P.start + tid];
+        v_next = f[perm[P.start + tid]];
+    }
+    for (int c0 = 0; c0 < P.count; c0 += kHalfChunk) {
+        const int cnt = min(kHalfChunk, P.count - c0);
+        if (tid < cnt) {  // stage this thread's node: tile offset and window arguments
+            const int loc1 = (r_next.cell & g.cmask[1]) - org1;
+            const int loc0 = ((r_next.cell >> g.cbits[1]) & g.cmask[0]) - org0;
+            const T fr0 = r_next.fr[0], fr1 = r_next.fr[1];
+            HalfStage<T> st;
+            st.off = (fr0 == (T)0 || fr1 == (T)0)
+                         ? (int)(0x80000000u | (unsigned)(loc0 * pitch + loc1))
+                         : (loc0 + 1) * pitch + loc1 + 1;
+            st.s = P.start + c0 + tid;
+            st.u0 = LIN ? fr0 : (T)2 * fr0 - (T)1;
+            st.u1 = LIN ? fr1 : (T)2 * fr1 - (T)1;
+            st_node[tid] = st;
+            st_val[tid] = v_next;
+        }
+        __syncthreads();  // (also orders the previous flush's zeroing before these adds)
+        {
+            const int nx = c0 + kHalfChunk + tid;
+            if (nx < P.count) {
+                r_next = rec[P.start + nx];
+                v_next = f[perm[P.start + nx]];
+            }
+        }
+        for (int k = half; k < cnt; k += kHalfTiles) {
+            const HalfStage<T> st = st_node[k];
+            const C v = st_val[k];
+            if (st.off >= 0) {  // uniform inside the half (one node)
+                T w1, w0h;
+                if constexpr (LIN) {  // lookup-table window
+                    w1 = c < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 1), g.lin_k,
+                                                  c + 1, st.u1, e1)
+                                 : (T)0;
+                    w0h = h < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 0), g.lin_k,
+                                                   h + 1, st.u0, e0)
+                                  : (T)0;
+                } else {
+                    w1 = poly_horner<T, DEG>(cc, st.u1);
+                    w0h = poly_horner<T, DEG>(cr, st.u0);
+                }
+                const T ar = w1 * v.x, ai = w1 * v.y;
+                C *col = lane_col + st.off;
+#pragma unroll
+                for (int j = 0; j < ROWS; j++) {
+                    const int rr = rg + j * RG;
+                    const T w0 = __shfl_sync(mask, w0h, rr, 16);
+                    if (c < PER && rr < PER) {
+                        C a = col[j * RG * pitch];
+                        a.x += w0 * ar;
+                        a.y += w0 * ai;
+                        col[j * RG * pitch] = a;
+                    }
+                }
+            } else {  // on a grid point: 2m + 1 taps on some axis
+                const Rec r = rec[st.s];
+                const T fr0 = r.fr[0], fr1 = r.fr[1];
+                C *base = mine + (st.off & 0x7fffffff);
+                for (int q = h; q < NT * NT; q += 16) {
+                    const int a0 = q / NT, a1 = q - a0 * NT;
+                    const T w = eval_tap<T, MM, LIN ? 2 : 1>(g, tab, 0, a0, fr0) *
+                                eval_tap<T, MM, LIN ? 2 : 1>(g, tab + AS, 1, a1, fr1);
+                    C *p = base + a0 * pitch + a1;
+                    C a = *p;
+                    a.x += w * v.x;
+                    a.y += w * v.y;
+                    *p = a;
+                }
+            }
+            __syncwarp(mask);
+        }
+        __syncthreads();
+    }
+
+    // flush: cell (a0, a1) of the tile is grid point ((org0 - m + a0) mod n0,
+    // (org1 - m + a1) mod n1); consecutive threads take consecutive cells; each cell is read
+    // from every tile and zeroed there
+    C z;
+    z.x = (T)0;
+    z.y = (T)0;
+    for (int idx = tid; idx < td0 * td1; idx += 32 * kHalfWarps) {
+        const int a0 = idx / td1, a1 = idx - a0 * td1;
+        const int e = a0 * pitch + a1;
+        T vr = (T)0, vi = (T)0;
+#pragma unroll
+        for (int o = 0; o < kHalfTiles; o++) {
+            const C cv = tiles[(size_t)o * tcells + e];
+            tiles[(size_t)o * tcells + e] = z;
+            vr += cv.x;
+            vi += cv.y;
+        }
+        if (vr == (T)0 && vi == (T)0) continue;
+        const size_t gi = (size_t)wrapn(org0 - MM + a0, g.n[0]) * g.n[1] +
+                          (size_t)wrapn(org1 - MM + a1, g.n[1]);
+        global_add(grid + gi, vr, vi);
+    }
+}
+
+template <typename T, int MM, bool LIN>
+__global__ void __launch_bounds__(32 * kHalfWarps)
+    spread_half_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
+                       const typename RecOf<T>::type *__restrict__ rec,
+                       const int *__restrict__ perm, const SubProb *__restrict__ subs,
+                       int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
+{
+    using C = typename Cplx<T>::type;
+    constexpr int DEG = PolyDeg<T, MM>::value;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T cc[DEG + 1], cr[DEG + 1];
+    half_coefficients<T, MM>(static_cast<const T *>(g.poly), cc, cr);
     {
+        const int tcells = (g.bs[0] + 2 * MM) * half_pitch<T, MM>(g.bs[1] + 2 * MM);
+        C *tiles = half_tiles<T>(smem_raw);
         C z;
         z.x = (T)0;
         z.y = (T)0;
-        for (int e = tid; e < kHalfTiles * tcells; e += 32 * kHalfWarps) tiles[e] = z;
+        for (int e = threadIdx.x; e < kHalfTiles * tcells; e += 32 * kHalfWarps) tiles[e] = z;
     }
-    C *const lane_col = mine + rg * pitch + c;
     const int nsub = nsub_total[0];
     __shared__ int s_sp;
     for (int sp = next_subproblem(nsub_total, &s_sp); sp < nsub;
-         sp = next_subproblem(nsub_total, &s_sp)) {
+         sp = next_subproblem(nsub_total, &s_sp))
+        half_subproblem<T, MM, LIN>(g, subs[sp], f, rec, perm, grid, smem_raw, cc, cr);
+    finish_subproblems(nsub_total);
+}
+
+// ------------------------------------------------------------------------------ rows form (d = 2)
+// No shared-memory tile at all. Inside a bin the sorted nodes are ordered by their grid row
+// (set_nodes), so a warp walking a subproblem meets the rows in increasing order. Lane c owns
+// column c of the subproblem's tile (bin + halo along the last axis, at most 32 cells) and keeps
+// 2m + 1 consecutive tile rows of that column in registers: a node at row r adds its column
+// weight times its row weights into rows r .. r + 2m. When the next node starts a later row,
+// the rows below it are complete: each is added into the grid once (one vector atomic per
+// nonzero cell) and the register window slides up. Each node's window values are computed once,
+// by the lane that stages it (row weights, and column weights times the node value, tap 0 being
+// nonzero only on a grid point), and read by the warp from shared memory. The warps of a CTA are
+// independent: each claims its own subproblems from the plan's work counter.
+constexpr int kRowsWarps = 4;
+
+template <typename T, int MM> struct RowsShape {
+    static constexpr int NT = 2 * MM + 1;             // taps per axis (register rows)
+    static constexpr int NTP = (NT + 3) & ~3;         // staged row weights per node (16-byte rows)
+    static constexpr size_t per_warp =
+        32 * (sizeof(int2) + NTP * sizeof(T) + NT * sizeof(typename Cplx<T>::type));
+};
+
+template <typename T, int MM, bool LIN>
+__global__ void __launch_bounds__(32 * kRowsWarps)
+    spread_rows_kernel(Geom g, const __grid_constant__ WinCoef<T, MM> wc,
+                       const typename Cplx<T>::type *__restrict__ f,
+                       const typename RecOf<T>::type *__restrict__ rec,
+                       const int *__restrict__ perm, const SubProb *__restrict__ subs,
+                       int *__restrict__ work, typename Cplx<T>::type *__restrict__ grid)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    using Sh = RowsShape<T, MM>;
+    constexpr int NT = Sh::NT, NTP = Sh::NTP;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    constexpr int MODE = LIN ? 2 : 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char *mine = smem_raw + (size_t)warp * Sh::per_warp;
+    T *st_w0 = reinterpret_cast<T *>(mine);                               // [32][NTP]
+    C *st_cv = reinterpret_cast<C *>(mine + 32 * NTP * sizeof(T));        // [32][NT]
+    int2 *st_at = reinterpret_cast<int2 *>(mine + 32 * (NTP * sizeof(T) + NT * sizeof(C)));
+    const int td1 = g.bs[1] + 2 * MM;  // tile columns (<= 32)
+    const bool col_on = lane < td1;
+    const int nsub = work[0];
+    for (;;) {
+        int sp = 0;
+        if (lane == 0) sp = atomicAdd(work + 1, 1);
+        sp = __shfl_sync(0xffffffffu, sp, 0);
+        if (sp >= nsub) break;
         const SubProb P = subs[sp];
         const int org1 = (P.bin % g.nb[1]) * g.bs[1];
         const int org0 = (P.bin / g.nb[1]) * g.bs[0];
-        Rec r_next;
-        C v_next;
-        if (tid < P.count) {
-            r_next = rec[P.start + tid];
-            v_next = f[perm[P.start + tid]];
-        }
-        for (int c0 = 0; c0 < P.count; c0 += kHalfChunk) {
-            const int cnt = min(kHalfChunk, P.count - c0);
-            if (tid < cnt) {  // stage this thread's node: tile offset and window arguments
-                const int loc1 = (r_next.cell & g.cmask[1]) - org1;
-                const int loc0 = ((r_next.cell >> g.cbits[1]) & g.cmask[0]) - org0;
-                const T fr0 = r_next.fr[0], fr1 = r_next.fr[1];
-                HalfStage<T> st;
-                st.off = (fr0 == (T)0 || fr1 == (T)0)
-                             ? (int)(0x80000000u | (unsigned)(loc0 * pitch + loc1))
-                             : (loc0 + 1) * pitch + loc1 + 1;
-                st.s = P.start + c0 + tid;
-                st.u0 = LIN ? fr0 : (T)2 * fr0 - (T)1;
-                st.u1 = LIN ? fr1 : (T)2 * fr1 - (T)1;
-                st_node[tid] = st;
-                st_val[tid] = v_next;
-            }
-            __syncthreads();  // (also orders the previous flush's zeroing before these adds)
-            {
-                const int nx = c0 + kHalfChunk + tid;
-                if (nx < P.count) {
-                    r_next = rec[P.start + nx];
-                    v_next = f[perm[P.start + nx]];
-                }
-            }
-            for (int k = half; k < cnt; k += kHalfTiles) {
-                const HalfStage<T> st = st_node[k];
-                const C v = st_val[k];
-                if (st.off >= 0) {  // uniform inside the half (one node)
-                    T w1, w0h;
-                    if constexpr (LIN) {  // lookup-table window
-                        w1 = c < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 1), g.lin_k,
-                                                      c + 1, st.u1, e1)
-                                     : (T)0;
-                        w0h = h < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 0),
-                                                       g.lin_k, h + 1, st.u0, e0)
-                                      : (T)0;
-                    } else {
-                        w1 = poly_horner<T, DEG>(cc, st.u1);
-                        w0h = poly_horner<T, DEG>(cr, st.u0);
-                    }
-                    const T ar = w1 * v.x, ai = w1 * v.y;
-                    C *col = lane_col + st.off;
+        const size_t gcol = (size_t)wrapn(org1 - MM + lane, g.n[1]);
+        C acc[NT];
 #pragma unroll
-                    for (int j = 0; j < ROWS; j++) {
-                        const int rr = rg + j * RG;
-                        const T w0 = __shfl_sync(mask, w0h, rr, 16);
-                        if (c < PER && rr < PER) {
-                            C a = col[j * RG * pitch];
-                            a.x += w0 * ar;
-                            a.y += w0 * ai;
-                            col[j * RG * pitch] = a;
+        for (int r = 0; r < NT; r++) {
+            acc[r].x = (T)0;
+            acc[r].y = (T)0;
+        }
+        int cur = -1;  // tile row of acc[0]
+        // add register row r (tile row cur + r) into the grid
+        auto flush_row = [&](int r) {
+            if (col_on && (acc[r].x != (T)0 || acc[r].y != (T)0))
+                global_add(grid + (size_t)wrapn(org0 - MM + cur + r, g.n[0]) * g.n[1] + gcol,
+                           acc[r].x, acc[r].y);
+        };
+        for (int k0 = 0; k0 < P.count; k0 += 32) {
+            const int cnt = min(32, P.count - k0);
+            if (lane < cnt) {  // stage this lane's node: its rows' and columns' window values
+                const int s = P.start + k0 + lane;
+                const Rec r = rec[s];
+                const C v = f[perm[s]];
+                const int loc1 = (r.cell & g.cmask[1]) - org1;
+                const int loc0 = ((r.cell >> g.cbits[1]) & g.cmask[0]) - org0;
+                T w0[NT], w1[NT];
+                eval_taps<T, MM, 0, MODE>(g, wc.c, 0, r.fr[0], w0);
+                eval_taps<T, MM, 0, MODE>(g, wc.c + AS, 1, r.fr[1], w1);
+#pragma unroll
+                for (int t = 0; t < NT; t++) {
+                    st_w0[lane * NTP + t] = w0[t];
+                    C q;
+                    q.x = w1[t] * v.x;
+                    q.y = w1[t] * v.y;
+                    st_cv[lane * NT + t] = q;
+                }
+                st_at[lane] = make_int2(loc0, loc1);
+            }
+            __syncwarp();
+            for (int k = 0; k < cnt; k++) {
+                const int2 at = st_at[k];
+                if (at.x != cur) {  // uniform: a later row; the rows below it are complete
+                    if (cur >= 0) {
+                        const int dr = at.x - cur;
+                        if (dr >= NT) {
+#pragma unroll
+                            for (int r = 0; r < NT; r++) {
+                                flush_row(r);
+                                acc[r].x = (T)0;
+                                acc[r].y = (T)0;
+                            }
+                        } else {
+                            for (int i = 0; i < dr; i++) {
+                                flush_row(0);
+                                cur++;
+#pragma unroll
+                                for (int r = 0; r + 1 < NT; r++) acc[r] = acc[r + 1];
+                                acc[NT - 1].x = (T)0;
+                                acc[NT - 1].y = (T)0;
+                            }
                         }
                     }
-                } else {  // on a grid point: 2m + 1 taps on some axis
-                    const Rec r = rec[st.s];
-                    const T fr0 = r.fr[0], fr1 = r.fr[1];
-                    C *base = mine + (st.off & 0x7fffffff);
-                    for (int q = h; q < NT * NT; q += 16) {
-                        const int a0 = q / NT, a1 = q - a0 * NT;
-                        const T w = eval_tap<T, MM, LIN ? 2 : 1>(g, tab, 0, a0, fr0) *
-                                    eval_tap<T, MM, LIN ? 2 : 1>(g, tab + AS, 1, a1, fr1);
-                        C *p = base + a0 * pitch + a1;
-                        C a = *p;
-                        a.x += w * v.x;
-                        a.y += w * v.y;
-                        *p = a;
-                    }
+                    cur = at.x;
                 }
-                __syncwarp(mask);
-            }
-            __syncthreads();
-        }
-
-        // flush: cell (a0, a1) of the tile is grid point ((org0 - m + a0) mod n0,
-        // (org1 - m + a1) mod n1); consecutive threads take consecutive cells; each cell is read
-        // from every tile and zeroed there
-        C z;
-        z.x = (T)0;
-        z.y = (T)0;
-        for (int idx = tid; idx < td0 * td1; idx += 32 * kHalfWarps) {
-            const int a0 = idx / td1, a1 = idx - a0 * td1;
-            const int e = a0 * pitch + a1;
-            T vr = (T)0, vi = (T)0;
+                const int t = lane - at.y;  // this column's tap of the node
+                const bool in = t >= 0 && t < NT;
+                const C cv = st_cv[k * NT + (in ? t : 0)];
+                const T cr = in ? cv.x : (T)0, ci = in ? cv.y : (T)0;
+                const T *w0 = st_w0 + k * NTP;
 #pragma unroll
-            for (int o = 0; o < kHalfTiles; o++) {
-                const C cv = tiles[(size_t)o * tcells + e];
-                tiles[(size_t)o * tcells + e] = z;
-                vr += cv.x;
-                vi += cv.y;
+                for (int r = 0; r < NT; r++) {
+                    const T w = w0[r];
+                    acc[r].x += w * cr;
+                    acc[r].y += w * ci;
+                }
             }
-            if (vr == (T)0 && vi == (T)0) continue;
-            const size_t gi = (size_t)wrapn(org0 - MM + a0, g.n[0]) * g.n[1] +
-                              (size_t)wrapn(org1 - MM + a1, g.n[1]);
-            global_add(grid + gi, vr, vi);
+            __syncwarp();
+        }
+        if (cur >= 0) {
+#pragma unroll
+            for (int r = 0; r < NT; r++) flush_row(r);
         }
     }
-    finish_subproblems(nsub_total);
+    if (lane == 0) {  // the last warp to finish resets the counters for the next launch
+        __threadfence();
+        if (atomicAdd(work + 2, 1) == (int)(gridDim.x * kRowsWarps) - 1) {
+            work[1] = 0;
+            work[2] = 0;
+        }
+    }
 }
 
 // ----------------------------------------------------------------------------- plane form (d = 3)
@@ -1455,6 +1627,8 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
     if (method == kSpreadOctet &&
         (D != 2 || 2 * MM + 1 > 16 || octet_tiles + spread_stage_bytes<T>() > limit))
         method = kSpreadWarpPrivate;
+    if (method == kSpreadRows && (D != 2 || g.bs[D - 1] + 2 * MM > 32))
+        method = kSpreadHalf;
     if (method == kSpreadStripe &&
         (D != 2 || g.sw.R <= 0 || stripe_smem_bytes<T, MM>(g.bs[0] + 2 * MM) > limit))
         method = kSpreadHalf;
@@ -1509,6 +1683,24 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
                 if (e != cudaSuccess) return e;
                 spread_half_kernel<T, MM, false><<<blocks, 32 * kHalfWarps, smem, stream>>>(
                     g, f, rec, perm, subs, nsub_total, grid);
+            }
+        }
+    } else if (method == kSpreadRows) {
+        if constexpr (D == 2) {
+            const size_t smem = RowsShape<T, MM>::per_warp * kRowsWarps;
+            const int warps_cap = (max_subs + kRowsWarps - 1) / kRowsWarps;
+            if (g.lin_k) {
+                e = launch_persistent(spread_rows_kernel<T, MM, true>, smem, 32 * kRowsWarps,
+                                      warps_cap, blocks);
+                if (e != cudaSuccess) return e;
+                spread_rows_kernel<T, MM, true><<<blocks, 32 * kRowsWarps, smem, stream>>>(
+                    g, make_wincoef<T, MM>(g), f, rec, perm, subs, nsub_total, grid);
+            } else {
+                e = launch_persistent(spread_rows_kernel<T, MM, false>, smem, 32 * kRowsWarps,
+                                      warps_cap, blocks);
+                if (e != cudaSuccess) return e;
+                spread_rows_kernel<T, MM, false><<<blocks, 32 * kRowsWarps, smem, stream>>>(
+                    g, make_wincoef<T, MM>(g), f, rec, perm, subs, nsub_total, grid);
             }
         }
     } else if (method == kSpreadStripe) {

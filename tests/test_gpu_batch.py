@@ -258,3 +258,131 @@ def test_library_batch_checks_every_plan_before_enqueuing():
         assert rel_l2(o.cpu().numpy(), p.trafo(fh).cpu().numpy()) <= 1e-14
         assert p.status() == 0
     assert L.nfft_batch_destroy(b) == 0
+
+
+# ------------------------------------------------------------------ fused execution
+
+def _check_batch(b, xs, fhs, fs, gs, dtype=torch.float32, tol_x=1e-5):
+    fh_t = [to_dev(v, dtype) for v in fhs]
+    f_t = [to_dev(v, dtype) for v in fs]
+    g_t = [to_dev(v, dtype) for v in gs]
+    outs_f = [o.cpu().numpy() for o in b.trafo(fh_t)]
+    outs_h = [o.cpu().numpy() for o in b.adjoint(f_t)]
+    _, g_x = b.backward(g_t, fh_t, want_fhat=False)
+    g_x = [t.cpu().numpy() for t in g_x]
+    for i, p in enumerate(b.plans):
+        xr, fhr, fr, gr = (rounded(xs[i], dtype), rounded(fhs[i], dtype), rounded(fs[i], dtype),
+                           rounded(gs[i], dtype))
+        assert rel_l2(outs_f[i], oracle.nfft(xr, fhr, n=p.n, m=p.m)) <= TOL[dtype], i
+        assert rel_l2(outs_h[i], oracle.nfft_adjoint(xr, fr, p.N, n=p.n, m=p.m)) <= TOL[dtype], i
+        if p.M:
+            assert rel_l2(g_x[i], oracle.nfft_grad_x(xr, fhr, gr, n=p.n, m=p.m)) <= tol_x, i
+    return outs_f, outs_h, g_x
+
+
+def test_fused_batch_matches_oracle_and_plan_by_plan():
+    """2-D FP32 plans with one m run fused (one launch per stage over all plans): forward,
+    adjoint and node gradient of every plan against the oracle, and against the same batch run
+    plan by plan on side streams."""
+    specs = SPECS + [{"N": (256, 16), "M": 0}, {"N": (2048, 32), "M": 4000}]
+    b = PlanBatch(specs, dtype=torch.float32, device=DEV)
+    assert b.fused
+    xs, fhs, fs = _inputs(specs, torch.float32, 1500)
+    _, _, gs = _inputs(specs, torch.float32, 1600)
+    b.set_nodes([to_dev(x, torch.float32) for x in xs])
+    ff, fh, fx = _check_batch(b, xs, fhs, fs, gs)
+    b.set_fused(False)
+    assert not b.fused
+    sf, sh, sx = _check_batch(b, xs, fhs, fs, gs)
+    for i in range(len(specs)):
+        assert rel_l2(ff[i], sf[i]) <= 1e-6
+        assert rel_l2(fh[i], sh[i]) <= 1e-6
+        if specs[i]["M"]:
+            assert rel_l2(fx[i], sx[i]) <= 1e-6
+    b.set_fused(True)
+    assert b.fused
+    b.close()
+
+
+def test_fused_batch_follows_plan_changes_and_graph_replay():
+    """A plan retuned after the fused tables were built (new bins, nodes set again) is picked
+    up by the next call; a captured graph of the fused batch replays with new inputs."""
+    b = PlanBatch(SPECS, dtype=torch.float32, device=DEV)
+    xs, fhs, fs = _inputs(SPECS, torch.float32, 1700)
+    _, _, gs = _inputs(SPECS, torch.float32, 1750)
+    b.set_nodes([to_dev(x, torch.float32) for x in xs])
+    _check_batch(b, xs, fhs, fs, gs)
+    b.plans[3].set_option("bin0", 16)
+    b.plans[3].set_option("bin1", 32)
+    b.set_nodes([to_dev(x, torch.float32) for x in xs])
+    assert b.fused
+    _check_batch(b, xs, fhs, fs, gs)
+    fh_t = [to_dev(v, torch.float32) for v in fhs]
+    f_t = [to_dev(v, torch.float32) for v in fs]
+    b.capture(fh_t, f_t)
+    _, fhs2, fs2 = _inputs(SPECS, torch.float32, 1800)
+    for i in range(len(SPECS)):
+        b.in_fhat[i].copy_(to_dev(fhs2[i], torch.float32))
+        b.in_f[i].copy_(to_dev(fs2[i], torch.float32))
+    gf, gh = b.replay()
+    torch.cuda.synchronize()
+    for i, p in enumerate(b.plans):
+        xr = rounded(xs[i], torch.float32)
+        assert rel_l2(gf[i].cpu().numpy(), oracle.nfft(
+            xr, rounded(fhs2[i], torch.float32), n=p.n, m=4)) <= TOL[torch.float32]
+        assert rel_l2(gh[i].cpu().numpy(), oracle.nfft_adjoint(
+            xr, rounded(fs2[i], torch.float32), p.N, n=p.n, m=4)) <= TOL[torch.float32]
+    b.close()
+
+
+def test_batches_that_do_not_qualify_run_plan_by_plan():
+    from paper_1810_09891_gb300._lib import NfftError
+    mixed = [dict(SPECS[0]), dict(SPECS[1], m=3)]  # two window cutoffs
+    b = PlanBatch(mixed, dtype=torch.float32, device=DEV)
+    assert not b.fused
+    with pytest.raises(NfftError, match="NFFT_EUNSUPPORTED"):
+        b.set_fused(True)
+    xs, fhs, fs = _inputs(mixed, torch.float32, 1900)
+    _, _, gs = _inputs(mixed, torch.float32, 1950)
+    b.set_nodes([to_dev(x, torch.float32) for x in xs])
+    _check_batch(b, xs, fhs, fs, gs)
+    b.close()
+    b64 = PlanBatch(SPECS, dtype=torch.float64, device=DEV)
+    assert not b64.fused  # FP64 batches run plan by plan
+    b64.close()
+    odd = PlanBatch([{"N": (60, 60), "M": 100, "n": (130, 128)}], dtype=torch.float32,
+                    device=DEV)
+    assert not odd.fused  # a length that is not a power of two
+    odd.close()
+    spread = PlanBatch(SPECS[:2], dtype=torch.float32, device=DEV)
+    spread.plans[0].set_option("spread_method", "octet")
+    assert not spread.fused  # the fused spreading is the half-warp form
+    spread.close()
+
+
+def test_fused_batched_workload_full_size():
+    """The 64-problem batched workload (N_i per axis in {64, ..., 512}, M_i up to 1e6), fused:
+    the forward on 2048 sampled nodes and the adjoint of every coefficient against the oracle
+    for the largest problem and three others."""
+    specs = batched_specs()
+    b = PlanBatch(specs, dtype=torch.float32, device=DEV)
+    assert b.fused
+    xs = [W.round_nodes(W.uniform_nodes(s["M"], 2, seed_offset=1000 + i), np.float32)
+          for i, s in enumerate(specs)]
+    fhs = [W.gaussian_fhat(s["N"], 2000 + i) for i, s in enumerate(specs)]
+    fs = [W.gaussian_values(s["M"], 3000 + i) for i, s in enumerate(specs)]
+    b.set_nodes([to_dev(x, torch.float32) for x in xs])
+    yf = b.trafo([to_dev(v, torch.float32) for v in fhs])
+    yh = b.adjoint([to_dev(v, torch.float32) for v in fs])
+    torch.cuda.synchronize()
+    big = int(np.argmax([s["M"] for s in specs]))
+    for i in (big, 0, 17, 63):
+        p = b.plans[i]
+        xr, fhr, fr = (rounded(xs[i], torch.float32), rounded(fhs[i], torch.float32),
+                       rounded(fs[i], torch.float32))
+        idx = np.sort(np.random.default_rng(i).choice(p.M, min(2048, p.M), replace=False))
+        assert rel_l2(yf[i].cpu().numpy()[idx], oracle.nfft(xr[idx], fhr, n=p.n, m=4)) <= \
+            TOL[torch.float32], i
+        assert rel_l2(yh[i].cpu().numpy(), oracle.nfft_adjoint(xr, fr, p.N, n=p.n, m=4)) <= \
+            TOL[torch.float32], i
+    b.close()

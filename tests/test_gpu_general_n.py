@@ -55,7 +55,8 @@ def test_general_n_parity(N, n, m, M, dtype):
     assert rel_l2(yh, rh) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("spread", ["thread", "warp_atomic", "warp_private", "octet", "half", "plane"])
+@pytest.mark.parametrize("spread", ["thread", "warp_atomic", "warp_private", "octet", "half", "plane",
+                                    "rows"])
 @pytest.mark.parametrize("interp", ["thread", "warp", "tile", "octet"])
 def test_general_n_every_form(spread, interp):
     """Radial nodes (dense centre) on a 2-D grid whose last bins are partial."""

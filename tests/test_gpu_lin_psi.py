@@ -47,7 +47,8 @@ def test_table_window_parity(N, n, m, M, K, dtype):
     assert rel_l2(yh, rh) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("spread", ["thread", "warp_atomic", "warp_private", "octet", "half", "plane"])
+@pytest.mark.parametrize("spread", ["thread", "warp_atomic", "warp_private", "octet", "half", "plane",
+                                    "rows"])
 @pytest.mark.parametrize("window", ["kaiser_bessel", "gaussian", "bspline", "sinc"])
 def test_table_window_every_form(spread, window):
     N, n, m, K = (48, 40), (96, 80), 4, 128

@@ -84,7 +84,7 @@ def test_uniform_nodes(N, n, m, M, dtype):
 @pytest.mark.parametrize("forms", [("thread", "thread"), ("warp", "warp_atomic"),
                                    ("tile", "warp_private"), ("thread", "octet"),
                                    ("thread", "half"), ("thread", "plane"),
-                                   ("octet", "half"), ("octet", "plane")])
+                                   ("octet", "half"), ("octet", "plane"), ("thread", "rows")])
 def test_every_window_cutoff(d, m, dtype, forms):
     N = {1: (40,), 2: (20, 24), 3: (12, 8, 10)}[d]
     n = {1: (128,), 2: (64, 64), 3: (32, 32, 32)}[d]
@@ -103,7 +103,7 @@ def test_every_window_cutoff(d, m, dtype, forms):
 @pytest.mark.parametrize("forms", [("thread", "thread"), ("warp", "warp_atomic"),
                                    ("tile", "warp_private"), ("thread", "octet"),
                                    ("thread", "half"), ("thread", "plane"),
-                                   ("octet", "half"), ("octet", "plane")])
+                                   ("octet", "half"), ("octet", "plane"), ("thread", "rows")])
 def test_nodes_on_grid_points_and_edges(d, dtype, forms):
     """Nodes exactly on grid points (2m+1 taps), at -1/2, coincident nodes, and nodes outside
     the torus (any real is taken modulo 1)."""

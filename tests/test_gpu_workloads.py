@@ -14,7 +14,7 @@ from gpu_helpers import DEV, TOL, rel_l2, rounded, to_dev
 pytestmark = pytest.mark.gpu
 
 METHODS = ["thread", "warp_atomic", "warp_private"]
-METHODS_2D = METHODS + ["octet", "half"]  # the group forms exist for d = 2 only
+METHODS_2D = METHODS + ["octet", "half", "rows"]  # the group forms exist for d = 2 only
 METHODS_3D = METHODS + ["plane"]  # the plane form exists for d = 3 only
 INTERP = ["thread", "warp", "tile", "octet"]
 
@@ -195,21 +195,21 @@ def test_subproblem_sizes(dtype):
 
 
 def test_method_option_ranges():
-    """NFFT_OPT_SPREAD_METHOD takes 0..7 and NFFT_OPT_INTERP_METHOD 0..4; other values are
+    """NFFT_OPT_SPREAD_METHOD takes 0..8 and NFFT_OPT_INTERP_METHOD 0..4; other values are
     rejected with NFFT_EINVAL and leave the plan usable."""
     from paper_1810_09891_gb300 import _lib
 
     L = _lib.lib()
     plan = Plan((16, 16, 16), 100, m=4, dtype=torch.float32, device=DEV)
-    for v in range(0, 8):
+    for v in range(0, 9):
         assert L.nfft_set_option(plan._h, _lib.OPT_SPREAD_METHOD, v) == 0
     for v in range(0, 5):
         assert L.nfft_set_option(plan._h, _lib.OPT_INTERP_METHOD, v) == 0
-    einval = L.nfft_set_option(plan._h, _lib.OPT_SPREAD_METHOD, 8)
+    einval = L.nfft_set_option(plan._h, _lib.OPT_SPREAD_METHOD, 9)
     assert einval != 0
     assert L.nfft_set_option(plan._h, _lib.OPT_SPREAD_METHOD, -1) == einval
     assert L.nfft_set_option(plan._h, _lib.OPT_INTERP_METHOD, 5) == einval
-    assert _lib.SPREAD_METHODS["stripe"] == 7 and _lib.INTERP_METHODS["octet"] == 4
+    assert _lib.SPREAD_METHODS["rows"] == 8 and _lib.INTERP_METHODS["octet"] == 4
     x = W.uniform_nodes(100, 3, seed_offset=609)
     fh = W.gaussian_fhat((16, 16, 16), 610)
     plan.set_nodes(to_dev(x, torch.float32))
