@@ -250,9 +250,14 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           along the last axis (each at least 2m cells wide); the CTA's
  *                           half-warps spread the even stripes together, then the odd ones (no
  *                           atomics, no private copies). Needs a last-axis bin of at most
- *                           2m rounded up to a power of two and n_(d-1) >= 16 such stripes + 2m.
+ *                           2m rounded up to a power of two and n_(d-1) >= 16 such stripes + 2m,
+ *                           8 (d = 2) no tile: a warp walks the row-ordered nodes of a
+ *                           subproblem with lane c keeping 2m + 1 rows of tile column c in
+ *                           registers, adding each completed row into the grid (needs a
+ *                           last-axis bin + 2m <= 32).
  *                           A form whose tile does not fit or whose d does not match runs as
- *                           the nearest form that fits (6 -> 2 -> 1, 7 -> 5, 4/5 -> 3 -> 2 -> 1).
+ *                           the nearest form that fits (6 -> 2 -> 1, 7 -> 5, 8 -> 5,
+ *                           4/5 -> 3 -> 2 -> 1).
  *   NFFT_OPT_INTERP_METHOD  0 automatic, 1 one thread per node (gathers from the grid),
  *                           2 one warp per node, 3 one thread per node gathering from a
  *                           shared-memory tile of the node's bin, 4 (d = 2, 3 and m <= 4;

@@ -364,9 +364,6 @@ template <typename C, int LOGR, bool INV> __device__ __forceinline__ void dft_re
 // per 16, which keeps the stride-8 writes of the first stages free of bank conflicts.
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
-#ifndef GBNFFT_FFT_TWPOW
-#define GBNFFT_FFT_TWPOW 0
-#endif
 constexpr int kFftLogR = 3;  // largest stage radix 2^kFftLogR (radix 4 measured slower)
 constexpr int kFftR = 1 << kFftLogR;
 
@@ -448,29 +445,12 @@ __device__ __forceinline__ void r8_stage(const typename Cplx<T>::type *src,
         }
         const int kk = b & (NS - 1);
         if (LOGNS > 0) {
-#if GBNFFT_FFT_TWPOW
-            // one table read per butterfly; the other twiddles as its powers (depth 3)
-            C w[kFftR];
-            w[1] = tw[kk << (LOGL - LOGNS - LOGRS)];
-            if (INV) w[1].y = -w[1].y;
-            if (RS > 2) w[2] = cmul(w[1], w[1]);
-            if (RS > 3) w[3] = cmul(w[2], w[1]);
-            if (RS > 4) {
-                w[4] = cmul(w[2], w[2]);
-                w[5] = cmul(w[4], w[1]);
-                w[6] = cmul(w[4], w[2]);
-                w[7] = cmul(w[4], w[3]);
-            }
-#pragma unroll
-            for (int r = 1; r < RS; r++) a[r] = cmul(a[r], w[r]);
-#else
 #pragma unroll
             for (int r = 1; r < RS; r++) {
                 C w = tw[(r * kk) << (LOGL - LOGNS - LOGRS)];
                 if (INV) w.y = -w.y;
                 a[r] = cmul(a[r], w);
             }
-#endif
         }
         dft_reg<C, LOGRS, INV>(a);
         const int idx = ((b >> LOGNS) << (LOGNS + LOGRS)) + kk;
