@@ -162,22 +162,23 @@ __global__ void __launch_bounds__(kInterpThreads)
 
 // B^H of every plan: the CTAs claim subproblems of the concatenated lists through the batch's
 // work counter; the private tiles start clean and every flush leaves the cells it covered clean
-// again, so consecutive subproblems of different plans (different bin shapes) share them.
-template <typename T, int MM>
+// again, so consecutive subproblems of different plans (different bin shapes) share them. With
+// SHARED every plan has the window polynomials of `wc` (kernel parameter space); otherwise each
+// plan's own table is read from global memory.
+template <typename T, int MM, bool SHARED>
 __global__ void __launch_bounds__(32 * kHalfWarps)
     spread_fused_kernel(const FusedNodePlan *__restrict__ plans, int nplans,
                         const int *__restrict__ item_start, int *__restrict__ work,
-                        int tile_cells, const __grid_constant__ FusedPtrs ptrs)
+                        int tile_cells, const __grid_constant__ WinCoef<T, MM> wc,
+                        const __grid_constant__ FusedPtrs ptrs)
 {
     using C = typename Cplx<T>::type;
     using Rec = typename RecOf<T>::type;
-    constexpr int DEG = PolyDeg<T, MM>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Geom sg;
     __shared__ int s_sp;
-    T cc[DEG + 1], cr[DEG + 1];  // the window polynomials of the current item's plan
     {
-        C *tiles = half_tiles<T>(smem_raw);
+        C *tiles = half_tiles<T, MM>(smem_raw);
         C z;
         z.x = (T)0;
         z.y = (T)0;
@@ -186,19 +187,19 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
     __shared__ int s_start[kFusedMax + 1];
     for (int q = threadIdx.x; q <= nplans; q += blockDim.x) s_start[q] = item_start[q];
     const int nitems = work[0];
-    int cur = -1;  // the plan whose geometry and window polynomials are loaded
+    int cur = -1;  // the plan whose geometry is loaded
     for (int sp = next_subproblem(work, &s_sp); sp < nitems; sp = next_subproblem(work, &s_sp)) {
         const int p = find_plan(nplans, sp, [&](int q) { return s_start[q]; });
         if (p != cur) {  // uniform in the CTA
             load_geom(plans, p, &sg);
-            half_coefficients<T, MM>(static_cast<const T *>(plans[p].g.poly), cc, cr);
             __syncthreads();
             cur = p;
         }
         const SubProb P = plans[p].subs[sp - s_start[p]];
+        const T *coef = SHARED ? wc.c : static_cast<const T *>(plans[p].g.poly);
         half_subproblem<T, MM, false>(sg, P, static_cast<const C *>(ptrs.in[p]),
                                       static_cast<const Rec *>(plans[p].rec), plans[p].perm,
-                                      static_cast<C *>(plans[p].grid), smem_raw, cc, cr);
+                                      static_cast<C *>(plans[p].grid), smem_raw, coef);
     }
     finish_subproblems(work);
 }
@@ -241,21 +242,33 @@ cudaError_t interp_fused_m(const FusedNodePlan *plans, int nplans, const FusedOf
                   : interp_fused_ms<T, MM, false>(plans, nplans, off, wc, ptrs, grad, stream);
 }
 
-template <typename T, int MM>
-cudaError_t spread_fused_m(const FusedNodePlan *plans, int nplans, const int *item_start,
-                           int *work, int max_items, int tile_cells, const FusedPtrs &ptrs,
-                           cudaStream_t stream)
+template <typename T, int MM, bool SHARED>
+cudaError_t spread_fused_ms(const FusedNodePlan *plans, int nplans, const int *item_start,
+                            int *work, int max_items, int tile_cells, const WinCoef<T, MM> &wc,
+                            const FusedPtrs &ptrs, cudaStream_t stream)
 {
-    const size_t smem = half_stage_bytes<T>() +
+    const size_t smem = half_stage_bytes<T, MM>() +
                         (size_t)kHalfTiles * tile_cells * sizeof(typename Cplx<T>::type);
-    cudaError_t e = ensure_dynamic_smem(spread_fused_kernel<T, MM>, smem);
+    cudaError_t e = ensure_dynamic_smem(spread_fused_kernel<T, MM, SHARED>, smem);
     if (e != cudaSuccess) return e;
     const int blocks =
-        persistent_blocks(spread_fused_kernel<T, MM>, 32 * kHalfWarps, smem, max_items);
+        persistent_blocks(spread_fused_kernel<T, MM, SHARED>, 32 * kHalfWarps, smem, max_items);
     if (!blocks) return cudaErrorInvalidValue;
-    spread_fused_kernel<T, MM><<<blocks, 32 * kHalfWarps, smem, stream>>>(
-        plans, nplans, item_start, work, tile_cells, ptrs);
+    spread_fused_kernel<T, MM, SHARED><<<blocks, 32 * kHalfWarps, smem, stream>>>(
+        plans, nplans, item_start, work, tile_cells, wc, ptrs);
     return cudaGetLastError();
+}
+
+template <typename T, int MM>
+cudaError_t spread_fused_m(const FusedNodePlan *plans, int nplans, const int *item_start,
+                           int *work, int max_items, int tile_cells, const Geom &g0,
+                           const FusedPtrs &ptrs, bool shared, cudaStream_t stream)
+{
+    const WinCoef<T, MM> wc = make_wincoef<T, MM>(g0);
+    return shared ? spread_fused_ms<T, MM, true>(plans, nplans, item_start, work, max_items,
+                                                 tile_cells, wc, ptrs, stream)
+                  : spread_fused_ms<T, MM, false>(plans, nplans, item_start, work, max_items,
+                                                  tile_cells, wc, ptrs, stream);
 }
 
 }  // namespace
@@ -298,7 +311,7 @@ cudaError_t launch_interp_fused(const FusedNodePlan *plans, int nplans, const Fu
 
 cudaError_t launch_spread_fused(const FusedNodePlan *plans, int nplans, int *item_start,
                                 int *work, int max_items, int tile_cells, const Geom &g0,
-                                const FusedPtrs &ptrs, cudaStream_t stream)
+                                const FusedPtrs &ptrs, bool shared_window, cudaStream_t stream)
 {
     detail::fused_items_kernel<<<1, kFusedMax, 0, stream>>>(plans, nplans, item_start, work);
     cudaError_t e = cudaGetLastError();
@@ -308,7 +321,7 @@ cudaError_t launch_spread_fused(const FusedNodePlan *plans, int nplans, int *ite
 #define GB_CASE(MM)                                                                               \
     case MM:                                                                                      \
         return detail::spread_fused_m<float, MM>(plans, nplans, item_start, work, max_items,      \
-                                                 tile_cells, ptrs, stream);
+                                                 tile_cells, g0, ptrs, shared_window, stream);
         GB_CASE(1) GB_CASE(2) GB_CASE(3) GB_CASE(4) GB_CASE(5) GB_CASE(6) GB_CASE(7) GB_CASE(8)
 #undef GB_CASE
     default: return cudaErrorInvalidValue;
@@ -333,10 +346,17 @@ int half_tile_cells_f32(int m, int bs0, int bs1)
     return (bs0 + 2 * m) * pitch;
 }
 
-size_t half_smem_bytes_f32(int tile_cells)
+size_t half_smem_bytes_f32(int m, int tile_cells)
 {
-    return detail::half_stage_bytes<float>() +
-           (size_t)detail::kHalfTiles * tile_cells * sizeof(float2);
+    size_t stage = 0;
+    switch (m) {
+#define GB_CASE(MM)                                                                               \
+    case MM: stage = detail::half_stage_bytes<float, MM>(); break;
+        GB_CASE(1) GB_CASE(2) GB_CASE(3) GB_CASE(4) GB_CASE(5) GB_CASE(6) GB_CASE(7) GB_CASE(8)
+#undef GB_CASE
+    default: return ~size_t(0);
+    }
+    return stage + (size_t)detail::kHalfTiles * tile_cells * sizeof(float2);
 }
 
 }  // namespace gbnfft

@@ -1486,7 +1486,7 @@ bool fusable(const gbnfft_batch *b)
         cells = std::max(cells, size_t(half_tile_cells_f32(p->m, p->geom.bs[0], p->geom.bs[1])));
     }
     // private tiles and staging of the half-warp form in shared memory, beside static data
-    return half_smem_bytes_f32((int)cells) <= 200 * 1024;
+    return half_smem_bytes_f32(p0->m, (int)cells) <= 200 * 1024;
 }
 
 // Row stride (cells) of a line buffer of the radix-8 FFT for P lines of L (as launch_fftr).
@@ -1675,7 +1675,7 @@ int fused_adjoint(gbnfft_batch *b, const void *const *f, void *const *fhat)
     GB_CHECK(launch_zero_fused(nodes, n, b->offsets, sizeof(float2), b->stream));
     GB_CHECK(launch_spread_fused(nodes, n, fused_at<int>(b, b->off_istart),
                                  fused_at<int>(b, b->off_work), b->max_items, b->tile_cells,
-                                 b->plans[0]->geom, ptrs, b->stream));
+                                 b->plans[0]->geom, ptrs, b->shared_window, b->stream));
     int rc = fused_fft(b, kAdjCols, +1, ptrs);
     if (!rc) rc = fused_fft(b, kAdjRows, +1, ptrs);
     return rc;

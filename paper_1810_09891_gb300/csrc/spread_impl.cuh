@@ -741,11 +741,13 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
 // ------------------------------------------------------------------------ half-warp form (d = 2)
 // Sixteen lanes per node, two nodes per warp, one private complex tile per half-warp. The lanes
 // of a half form RG row groups x CW columns (CW = the 2m taps per axis rounded up to a power of
-// two); lane (rg, c) owns tap column c and tap rows rg, rg + RG, ... of its node. A lane
-// evaluates the column weight of its column and the row weight of row h (its index in the half)
-// from coefficients held in registers; row weights reach the other lanes by shuffles, and the
-// column weight times the node value is formed once per node. A node on a grid point (2m + 1
-// taps on some axis) takes a plain loop over its taps with weights from the global tables.
+// two); lane (rg, c) owns tap column c and tap rows rg, rg + RG, ... of its node. The window
+// weights are evaluated once per node, by the thread that stages the node (all taps of an axis
+// at once, mirrored pairs sharing one polynomial evaluation): the row weights are staged in the
+// order the row groups read them (one vector load per lane), the column weights already times
+// the node value. A node on a grid point of an axis has 2m + 1 taps on that axis: taps 1 .. 2m
+// as for any node, and tap 0 (weight edge_w) one cell before them; the window stays a product
+// over the axes, so the extra row and column of taps take one more read-modify-write per lane.
 // The tile row pitch is padded so that the row groups of one half fall on distinct banks.
 //
 // The CTAs are small (kHalfWarps warps): the flush reads every private tile of the CTA at every
@@ -757,13 +759,15 @@ __global__ void __launch_bounds__(32 * kSpreadWarps)
 #endif
 constexpr int kHalfWarps = GBNFFT_HALF_WARPS;
 constexpr int kHalfTiles = 2 * kHalfWarps;     // half-warps (and private tiles) per CTA
-constexpr int kHalfChunk = 32 * kHalfWarps;    // nodes staged per round
+constexpr int kHalfChunk = 32 * kHalfWarps;    // nodes staged per round (one per thread)
 
 template <int MM> struct HalfShape {
     static constexpr int PER = 2 * MM;
     static constexpr int CW = PER <= 2 ? 2 : PER <= 4 ? 4 : PER <= 8 ? 8 : 16;
     static constexpr int RG = 16 / CW;
     static constexpr int ROWS = (PER + RG - 1) / RG;
+    static constexpr int RP = ROWS == 1 ? 1 : ((ROWS + 3) & ~3);  // staged row weights per group
+    static constexpr int RW = RG * RP;                             // staged row weights per node
 };
 
 // Row pitch (in cells) of a half-warp tile whose rows hold td1 cells: one half touches RG rows
@@ -778,64 +782,54 @@ template <typename T, int MM> __host__ __device__ inline int half_pitch(int td1)
     return td1 + ((cw - td1 % mod) + mod) % mod;
 }
 
-// Staged per node (half-warp form): tile offset of the node's first tap inside the subproblem's
-// tile (bit 31 set: the node is on a grid point and the low bits give the offset of tap slot
-// 0), its sorted index, and the window arguments (z = 2 frac - 1, or frac for the lookup-table
-// window).
-template <typename T> struct alignas(16) HalfStage {
-    int off;
-    int s;
-    T u0, u1;
+// One staged chunk of the half-warp form, per node k < kHalfChunk:
+//   info[k]  tile offset of the node's tap (1, 1) | grid-point flags << 28 (bit t: frac_t = 0,
+//            so tap 0 of axis t is live)
+//   val[k]   the node value
+//   row[k * RW + g * RP + j]   the weight of tap row g + j * RG + 1 (row group g reads RP in a row)
+//   col[k * CW + (c ^ swz(k))] the weight of tap column c + 1 times the node value; the index is
+//            swizzled (swz(k) = (k / 2) mod CW) so that the stores of one thread per node and
+//            the loads of two nodes per warp both spread over the banks
+template <typename T, int MM> struct HalfStageLayout {
+    using Sh = HalfShape<MM>;
+    static constexpr size_t info = 0;
+    static constexpr size_t val = ((size_t)kHalfChunk * sizeof(int) + 15) / 16 * 16;
+    static constexpr size_t row = val + (size_t)kHalfChunk * 2 * sizeof(T);
+    static constexpr size_t col = row + ((size_t)kHalfChunk * Sh::RW * sizeof(T) + 15) / 16 * 16;
+    static constexpr size_t bytes = col + (size_t)kHalfChunk * Sh::CW * 2 * sizeof(T);
 };
 
-template <typename T>
+template <typename T, int MM>
 __host__ __device__ constexpr size_t half_stage_bytes()
 {
-    return kHalfChunk * (sizeof(HalfStage<T>) + sizeof(typename Cplx<T>::type));
+    return HalfStageLayout<T, MM>::bytes;
 }
 
 // Shared memory of the half-warp form: the staged chunk of nodes first, then the kHalfTiles
 // private tiles (td0 rows of `pitch` cells each).
-template <typename T>
+template <typename T, int MM>
 __device__ __forceinline__ typename Cplx<T>::type *half_tiles(unsigned char *smem)
 {
-    return reinterpret_cast<typename Cplx<T>::type *>(smem + half_stage_bytes<T>());
-}
-
-// Window polynomials of the half-warp form in registers: column tap c + 1 of axis 1 and row tap
-// h + 1 of axis 0 (coefficient k of tap i at [k * kPolyTaps + i - 1]); lanes past the 2m taps
-// hold zeros.
-template <typename T, int MM>
-__device__ __forceinline__ void half_coefficients(const T *__restrict__ tab, T *cc, T *cr)
-{
-    using Sh = HalfShape<MM>;
-    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
-    constexpr int DEG = PolyDeg<T, MM>::value;
-    const int h = threadIdx.x & 15, c = h & (Sh::CW - 1);
-#pragma unroll
-    for (int k = 0; k <= DEG; k++) {
-        cc[k] = c < Sh::PER ? tab[AS + k * kPolyTaps + c] : (T)0;
-        cr[k] = h < Sh::PER ? tab[k * kPolyTaps + h] : (T)0;
-    }
+    return reinterpret_cast<typename Cplx<T>::type *>(smem + half_stage_bytes<T, MM>());
 }
 
 // One subproblem of the half-warp form: the CTA stages its nodes a chunk at a time, every
 // half-warp adds one node after another into its private tile, and the flush adds the CTA's
-// tiles into the grid and zeroes them.
+// tiles into the grid and zeroes them. `coef` is the polynomial window table of axis 0 (axis 1
+// follows it; unused with the lookup-table window).
 template <typename T, int MM, bool LIN>
 __device__ __forceinline__ void half_subproblem(
     const Geom &g, const SubProb &P, const typename Cplx<T>::type *__restrict__ f,
     const typename RecOf<T>::type *__restrict__ rec, const int *__restrict__ perm,
-    typename Cplx<T>::type *__restrict__ grid, unsigned char *smem, const T *cc, const T *cr)
+    typename Cplx<T>::type *__restrict__ grid, unsigned char *smem, const T *__restrict__ coef)
 {
     using C = typename Cplx<T>::type;
     using Rec = typename RecOf<T>::type;
     using Sh = HalfShape<MM>;
+    using Lay = HalfStageLayout<T, MM>;
     constexpr int PER = Sh::PER, CW = Sh::CW, RG = Sh::RG, ROWS = Sh::ROWS;
-    constexpr int NT = 2 * MM + 1;
+    constexpr int RP = Sh::RP, RW = Sh::RW;
     constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
-    constexpr int DEG = PolyDeg<T, MM>::value;
-    const T *tab = static_cast<const T *>(g.poly);  // global table (taps of grid-point nodes)
     const int tid = threadIdx.x, lane = tid & 31;
     const int h = lane & 15, half = tid >> 4;
     const unsigned mask = 0xffffu << (lane & 16);
@@ -843,9 +837,11 @@ __device__ __forceinline__ void half_subproblem(
     const int td0 = g.bs[0] + 2 * MM, td1 = g.bs[1] + 2 * MM;
     const int pitch = half_pitch<T, MM>(td1);
     const int tcells = td0 * pitch;
-    HalfStage<T> *st_node = reinterpret_cast<HalfStage<T> *>(smem);
-    C *st_val = reinterpret_cast<C *>(st_node + kHalfChunk);
-    C *tiles = half_tiles<T>(smem);
+    int *st_info = reinterpret_cast<int *>(smem + Lay::info);
+    C *st_val = reinterpret_cast<C *>(smem + Lay::val);
+    T *st_row = reinterpret_cast<T *>(smem + Lay::row);
+    C *st_col = reinterpret_cast<C *>(smem + Lay::col);
+    C *tiles = half_tiles<T, MM>(smem);
     C *mine = tiles + (size_t)half * tcells;
     C *const lane_col = mine + rg * pitch + c;
     const T e0 = (T)g.win[0].edge_w, e1 = (T)g.win[1].edge_w;
@@ -859,19 +855,36 @@ __device__ __forceinline__ void half_subproblem(
     }
     for (int c0 = 0; c0 < P.count; c0 += kHalfChunk) {
         const int cnt = min(kHalfChunk, P.count - c0);
-        if (tid < cnt) {  // stage this thread's node: tile offset and window arguments
+        if (tid < cnt) {  // stage this thread's node: tile offset, weights, value
             const int loc1 = (r_next.cell & g.cmask[1]) - org1;
             const int loc0 = ((r_next.cell >> g.cbits[1]) & g.cmask[0]) - org0;
             const T fr0 = r_next.fr[0], fr1 = r_next.fr[1];
-            HalfStage<T> st;
-            st.off = (fr0 == (T)0 || fr1 == (T)0)
-                         ? (int)(0x80000000u | (unsigned)(loc0 * pitch + loc1))
-                         : (loc0 + 1) * pitch + loc1 + 1;
-            st.s = P.start + c0 + tid;
-            st.u0 = LIN ? fr0 : (T)2 * fr0 - (T)1;
-            st.u1 = LIN ? fr1 : (T)2 * fr1 - (T)1;
-            st_node[tid] = st;
+            T w0[2 * MM + 1], w1[2 * MM + 1];  // taps 1 .. 2m of each axis
+            if constexpr (LIN) {
+                lin_taps<T, MM, 1>(lin_axis<T, MM>(g.lin, g.lin_k, 0), g.lin_k, fr0, e0, w0);
+                lin_taps<T, MM, 1>(lin_axis<T, MM>(g.lin, g.lin_k, 1), g.lin_k, fr1, e1, w1);
+            } else {
+                window_taps<T, MM, 1>(coef, fr0, e0, w0);
+                window_taps<T, MM, 1>(coef + AS, fr1, e1, w1);
+            }
+            const int gp = (fr0 == (T)0 ? 1 : 0) | (fr1 == (T)0 ? 2 : 0);
+            st_info[tid] = ((loc0 + 1) * pitch + loc1 + 1) | (gp << 28);
             st_val[tid] = v_next;
+            T *rw = st_row + tid * RW;
+#pragma unroll
+            for (int q = 0; q < RW; q++) {
+                const int rr = q / RP + (q % RP) * RG;
+                rw[q] = rr < PER ? w0[rr + 1] : (T)0;
+            }
+            C *cw = st_col + tid * CW;
+            const int sw = (tid >> 1) & (CW - 1);
+#pragma unroll
+            for (int q = 0; q < PER; q++) {
+                C a;
+                a.x = w1[q + 1] * v_next.x;
+                a.y = w1[q + 1] * v_next.y;
+                cw[q ^ sw] = a;
+            }
         }
         __syncthreads();  // (also orders the previous flush's zeroing before these adds)
         {
@@ -882,43 +895,46 @@ __device__ __forceinline__ void half_subproblem(
             }
         }
         for (int k = half; k < cnt; k += kHalfTiles) {
-            const HalfStage<T> st = st_node[k];
-            const C v = st_val[k];
-            if (st.off >= 0) {  // uniform inside the half (one node)
-                T w1, w0h;
-                if constexpr (LIN) {  // lookup-table window
-                    w1 = c < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 1), g.lin_k,
-                                                  c + 1, st.u1, e1)
-                                 : (T)0;
-                    w0h = h < PER ? lin_tap<T, MM>(lin_axis<T, MM>(g.lin, g.lin_k, 0), g.lin_k,
-                                                   h + 1, st.u0, e0)
-                                  : (T)0;
-                } else {
-                    w1 = poly_horner<T, DEG>(cc, st.u1);
-                    w0h = poly_horner<T, DEG>(cr, st.u0);
-                }
-                const T ar = w1 * v.x, ai = w1 * v.y;
-                C *col = lane_col + st.off;
+            const int info = st_info[k];
+            const C cv = st_col[k * CW + (c ^ ((k >> 1) & (CW - 1)))];
+            T w0r[RP];
 #pragma unroll
-                for (int j = 0; j < ROWS; j++) {
-                    const int rr = rg + j * RG;
-                    const T w0 = __shfl_sync(mask, w0h, rr, 16);
-                    if (c < PER && rr < PER) {
-                        C a = col[j * RG * pitch];
-                        a.x += w0 * ar;
-                        a.y += w0 * ai;
-                        col[j * RG * pitch] = a;
-                    }
+            for (int j = 0; j < RP; j++) w0r[j] = st_row[k * RW + rg * RP + j];
+            const int off = info & 0x0fffffff;
+            C *col = lane_col + off;
+#pragma unroll
+            for (int j = 0; j < ROWS; j++) {
+                const int rr = rg + j * RG;
+                if (c < PER && rr < PER) {
+                    C a = col[j * RG * pitch];
+                    a.x += w0r[j] * cv.x;
+                    a.y += w0r[j] * cv.y;
+                    col[j * RG * pitch] = a;
                 }
-            } else {  // on a grid point: 2m + 1 taps on some axis
-                const Rec r = rec[st.s];
-                const T fr0 = r.fr[0], fr1 = r.fr[1];
-                C *base = mine + (st.off & 0x7fffffff);
-                for (int q = h; q < NT * NT; q += 16) {
-                    const int a0 = q / NT, a1 = q - a0 * NT;
-                    const T w = eval_tap<T, MM, LIN ? 2 : 1>(g, tab, 0, a0, fr0) *
-                                eval_tap<T, MM, LIN ? 2 : 1>(g, tab + AS, 1, a1, fr1);
-                    C *p = base + a0 * pitch + a1;
+            }
+            const int gp = info >> 28;
+            if (gp != 0 && h < PER) {  // uniform inside the half: a node on a grid point
+                C *base = mine + off;
+                if (gp & 1) {  // row tap 0 of axis 0 over the column taps 1 .. 2m (c == h)
+                    C *p = base - pitch + h;
+                    C a = *p;
+                    a.x += e0 * cv.x;
+                    a.y += e0 * cv.y;
+                    *p = a;
+                }
+                if (gp & 2) {  // column tap 0 of axis 1 over the row taps 1 .. 2m
+                    const C v = st_val[k];
+                    const T w = st_row[k * RW + (h % RG) * RP + h / RG] * e1;
+                    C *p = base + h * pitch - 1;
+                    C a = *p;
+                    a.x += w * v.x;
+                    a.y += w * v.y;
+                    *p = a;
+                }
+                if (gp == 3 && h == 0) {  // the corner: tap 0 of both axes
+                    const C v = st_val[k];
+                    const T w = e0 * e1;
+                    C *p = base - pitch - 1;
                     C a = *p;
                     a.x += w * v.x;
                     a.y += w * v.y;
@@ -936,8 +952,10 @@ __device__ __forceinline__ void half_subproblem(
     C z;
     z.x = (T)0;
     z.y = (T)0;
-    for (int idx = tid; idx < td0 * td1; idx += 32 * kHalfWarps) {
-        const int a0 = idx / td1, a1 = idx - a0 * td1;
+    constexpr int kStep = 32 * kHalfWarps;
+    const int dq = kStep / td1, dr = kStep - dq * td1;
+    int a0 = tid / td1, a1 = tid - a0 * td1;
+    for (int idx = tid; idx < td0 * td1; idx += kStep) {
         const int e = a0 * pitch + a1;
         T vr = (T)0, vi = (T)0;
 #pragma unroll
@@ -947,28 +965,33 @@ __device__ __forceinline__ void half_subproblem(
             vr += cv.x;
             vi += cv.y;
         }
-        if (vr == (T)0 && vi == (T)0) continue;
-        const size_t gi = (size_t)wrapn(org0 - MM + a0, g.n[0]) * g.n[1] +
-                          (size_t)wrapn(org1 - MM + a1, g.n[1]);
-        global_add(grid + gi, vr, vi);
+        if (vr != (T)0 || vi != (T)0) {
+            const size_t gi = (size_t)wrapn(org0 - MM + a0, g.n[0]) * g.n[1] +
+                              (size_t)wrapn(org1 - MM + a1, g.n[1]);
+            global_add(grid + gi, vr, vi);
+        }
+        a0 += dq;  // (a0, a1) = the cell of idx + kStep
+        a1 += dr;
+        if (a1 >= td1) {
+            a1 -= td1;
+            a0++;
+        }
     }
 }
 
 template <typename T, int MM, bool LIN>
 __global__ void __launch_bounds__(32 * kHalfWarps)
-    spread_half_kernel(Geom g, const typename Cplx<T>::type *__restrict__ f,
+    spread_half_kernel(Geom g, const __grid_constant__ WinCoef<T, MM> wc,
+                       const typename Cplx<T>::type *__restrict__ f,
                        const typename RecOf<T>::type *__restrict__ rec,
                        const int *__restrict__ perm, const SubProb *__restrict__ subs,
                        int *__restrict__ nsub_total, typename Cplx<T>::type *__restrict__ grid)
 {
     using C = typename Cplx<T>::type;
-    constexpr int DEG = PolyDeg<T, MM>::value;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T cc[DEG + 1], cr[DEG + 1];
-    half_coefficients<T, MM>(static_cast<const T *>(g.poly), cc, cr);
     {
         const int tcells = (g.bs[0] + 2 * MM) * half_pitch<T, MM>(g.bs[1] + 2 * MM);
-        C *tiles = half_tiles<T>(smem_raw);
+        C *tiles = half_tiles<T, MM>(smem_raw);
         C z;
         z.x = (T)0;
         z.y = (T)0;
@@ -978,31 +1001,64 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
     __shared__ int s_sp;
     for (int sp = next_subproblem(nsub_total, &s_sp); sp < nsub;
          sp = next_subproblem(nsub_total, &s_sp))
-        half_subproblem<T, MM, LIN>(g, subs[sp], f, rec, perm, grid, smem_raw, cc, cr);
+        half_subproblem<T, MM, LIN>(g, subs[sp], f, rec, perm, grid, smem_raw, wc.c);
     finish_subproblems(nsub_total);
 }
 
 // ------------------------------------------------------------------------------ rows form (d = 2)
-// No shared-memory tile at all. Inside a bin the sorted nodes are ordered by their grid row
-// (set_nodes), so a warp walking a subproblem meets the rows in increasing order. Lane c owns
-// column c of the subproblem's tile (bin + halo along the last axis, at most 32 cells) and keeps
-// 2m + 1 consecutive tile rows of that column in registers: a node at row r adds its column
-// weight times its row weights into rows r .. r + 2m. When the next node starts a later row,
-// the rows below it are complete: each is added into the grid once (one vector atomic per
-// nonzero cell) and the register window slides up. Each node's window values are computed once,
-// by the lane that stages it (row weights, and column weights times the node value, tap 0 being
-// nonzero only on a grid point), and read by the warp from shared memory. The warps of a CTA are
-// independent: each claims its own subproblems from the plan's work counter.
+// No shared-memory tile at all: a group of G lanes (a half-warp when the tile is at most 16
+// cells wide, else the whole warp) keeps one subproblem's whole tile in registers. Lane c of
+// the group owns column c of the tile (bin + 2m halo along the last axis) and all td0 = b0 + 2m
+// tile rows of that column. Each node's window values are computed once, by the lane that
+// stages it: the column weights times the node value, and the row weights already placed at
+// the node's tile rows in a zero-filled column of td0 values. A node then costs every lane of
+// the group one multiply-add per tile row, with no branch on the node's position, and a few
+// shared-memory loads (instead of a read-modify-write per tap, which bounds the tile forms on
+// the shared-memory pipe). Tap 0 of an axis is nonzero only on a grid point. The two
+// half-warps of a warp take consecutive subproblems; at the end of a subproblem every nonzero
+// cell is added into the grid once (one vector atomic). The warps are independent: each claims
+// its own subproblems from the plan's work counter.
 constexpr int kRowsWarps = 4;
 
-template <typename T, int MM> struct RowsShape {
-    static constexpr int NT = 2 * MM + 1;             // taps per axis (register rows)
-    static constexpr int NTP = (NT + 3) & ~3;         // staged row weights per node (16-byte rows)
-    static constexpr size_t per_warp =
-        32 * (sizeof(int2) + NTP * sizeof(T) + NT * sizeof(typename Cplx<T>::type));
+template <typename T, int MM, int BS0, int G> struct RowsShape {
+    static constexpr int NT = 2 * MM + 1;                          // taps per axis
+    static constexpr int TD0 = BS0 + 2 * MM;                       // tile rows (registers)
+    static constexpr int TDP = (TD0 * (int)sizeof(T) + 15) / 16 * 16 / (int)sizeof(T);
+    static constexpr int GROUPS = 32 / G;                          // subproblems per warp
+    // per group: G nodes staged, each TDP row values, NT column values, one column offset;
+    // a group stride that is not a multiple of 128 bytes keeps the two groups' loads of one
+    // instruction on different banks
+    static constexpr size_t raw = (size_t)G * (TDP * sizeof(T) +
+                                              NT * sizeof(typename Cplx<T>::type) + sizeof(int));
+    static constexpr size_t raw16 = (raw + 15) / 16 * 16;
+    static constexpr size_t group = raw16 + (raw16 % 128 == 0 ? 16 : 0);
+    static constexpr size_t per_warp = group * GROUPS;
 };
 
-template <typename T, int MM, bool LIN>
+// n values from 16-byte aligned shared memory (n a multiple of 16 / sizeof(T))
+template <typename T, int N>
+__device__ __forceinline__ void load_aligned16(const T *p, T *w)
+{
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < N; i += 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(p + i);
+            w[i] = v.x;
+            w[i + 1] = v.y;
+            w[i + 2] = v.z;
+            w[i + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; i += 2) {
+            const double2 v = *reinterpret_cast<const double2 *>(p + i);
+            w[i] = v.x;
+            w[i + 1] = v.y;
+        }
+    }
+}
+
+template <typename T, int MM, bool LIN, int BS0, int G>
 __global__ void __launch_bounds__(32 * kRowsWarps)
     spread_rows_kernel(Geom g, const __grid_constant__ WinCoef<T, MM> wc,
                        const typename Cplx<T>::type *__restrict__ f,
@@ -1012,105 +1068,102 @@ __global__ void __launch_bounds__(32 * kRowsWarps)
 {
     using C = typename Cplx<T>::type;
     using Rec = typename RecOf<T>::type;
-    using Sh = RowsShape<T, MM>;
-    constexpr int NT = Sh::NT, NTP = Sh::NTP;
+    using Sh = RowsShape<T, MM, BS0, G>;
+    constexpr int NT = Sh::NT, TD0 = Sh::TD0, TDP = Sh::TDP, GROUPS = Sh::GROUPS;
     constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
     constexpr int MODE = LIN ? 2 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char *mine = smem_raw + (size_t)warp * Sh::per_warp;
-    T *st_w0 = reinterpret_cast<T *>(mine);                               // [32][NTP]
-    C *st_cv = reinterpret_cast<C *>(mine + 32 * NTP * sizeof(T));        // [32][NT]
-    int2 *st_at = reinterpret_cast<int2 *>(mine + 32 * (NTP * sizeof(T) + NT * sizeof(C)));
-    const int td1 = g.bs[1] + 2 * MM;  // tile columns (<= 32)
-    const bool col_on = lane < td1;
+    const int grp = lane / G, gl = lane % G;
+    unsigned char *mine = smem_raw + (size_t)warp * Sh::per_warp + (size_t)grp * Sh::group;
+    T *st_w0 = reinterpret_cast<T *>(mine);                             // [G][TDP]
+    C *st_cv = reinterpret_cast<C *>(mine + G * TDP * sizeof(T));       // [G][NT]
+    int *st_at = reinterpret_cast<int *>(mine + G * (TDP * sizeof(T) + NT * sizeof(C)));
+    const int td1 = g.bs[1] + 2 * MM;  // tile columns (<= G)
     const int nsub = work[0];
     for (;;) {
-        int sp = 0;
-        if (lane == 0) sp = atomicAdd(work + 1, 1);
-        sp = __shfl_sync(0xffffffffu, sp, 0);
-        if (sp >= nsub) break;
-        const SubProb P = subs[sp];
+        int sp0 = 0;
+        if (lane == 0) sp0 = atomicAdd(work + 1, GROUPS);
+        sp0 = __shfl_sync(0xffffffffu, sp0, 0);
+        if (sp0 >= nsub) break;
+        const int sp = sp0 + grp;
+        SubProb P;
+        P.bin = 0;
+        P.start = 0;
+        P.count = 0;
+        if (sp < nsub) P = subs[sp];
         const int org1 = (P.bin % g.nb[1]) * g.bs[1];
         const int org0 = (P.bin / g.nb[1]) * g.bs[0];
-        const size_t gcol = (size_t)wrapn(org1 - MM + lane, g.n[1]);
-        C acc[NT];
+        int most = P.count;  // rounds are run for the larger subproblem of the warp
+        if constexpr (GROUPS == 2) most = max(most, __shfl_xor_sync(0xffffffffu, most, 16));
+        C acc[TD0];
 #pragma unroll
-        for (int r = 0; r < NT; r++) {
-            acc[r].x = (T)0;
-            acc[r].y = (T)0;
+        for (int j = 0; j < TD0; j++) {
+            acc[j].x = (T)0;
+            acc[j].y = (T)0;
         }
-        int cur = -1;  // tile row of acc[0]
-        // add register row r (tile row cur + r) into the grid
-        auto flush_row = [&](int r) {
-            if (col_on && (acc[r].x != (T)0 || acc[r].y != (T)0))
-                global_add(grid + (size_t)wrapn(org0 - MM + cur + r, g.n[0]) * g.n[1] + gcol,
-                           acc[r].x, acc[r].y);
-        };
-        for (int k0 = 0; k0 < P.count; k0 += 32) {
-            const int cnt = min(32, P.count - k0);
-            if (lane < cnt) {  // stage this lane's node: its rows' and columns' window values
-                const int s = P.start + k0 + lane;
-                const Rec r = rec[s];
-                const C v = f[perm[s]];
+        Rec nr;  // this lane's node of the next round, loaded one round ahead
+        C nv;
+        if (gl < P.count) {
+            nr = rec[P.start + gl];
+            nv = f[perm[P.start + gl]];
+        }
+        for (int k0 = 0; k0 < most; k0 += G) {
+            const int cnt = min(G, P.count - k0);  // this group's nodes in this round (may be <= 0)
+            if (gl < cnt) {  // stage this lane's node
+                const Rec r = nr;
+                const C v = nv;
+                if (k0 + G + gl < P.count) {
+                    const int s = P.start + k0 + G + gl;
+                    nr = rec[s];
+                    nv = f[perm[s]];
+                }
                 const int loc1 = (r.cell & g.cmask[1]) - org1;
                 const int loc0 = ((r.cell >> g.cbits[1]) & g.cmask[0]) - org0;
                 T w0[NT], w1[NT];
                 eval_taps<T, MM, 0, MODE>(g, wc.c, 0, r.fr[0], w0);
                 eval_taps<T, MM, 0, MODE>(g, wc.c + AS, 1, r.fr[1], w1);
+                T *wr = st_w0 + gl * TDP;  // tile rows loc0 .. loc0 + 2m, zeros elsewhere
+#pragma unroll
+                for (int j = 0; j < TDP; j++) wr[j] = (T)0;
+#pragma unroll
+                for (int t = 0; t < NT; t++) wr[loc0 + t] = w0[t];
 #pragma unroll
                 for (int t = 0; t < NT; t++) {
-                    st_w0[lane * NTP + t] = w0[t];
                     C q;
                     q.x = w1[t] * v.x;
                     q.y = w1[t] * v.y;
-                    st_cv[lane * NT + t] = q;
+                    st_cv[gl * NT + t] = q;
                 }
-                st_at[lane] = make_int2(loc0, loc1);
+                st_at[gl] = loc1;
             }
             __syncwarp();
-            for (int k = 0; k < cnt; k++) {
-                const int2 at = st_at[k];
-                if (at.x != cur) {  // uniform: a later row; the rows below it are complete
-                    if (cur >= 0) {
-                        const int dr = at.x - cur;
-                        if (dr >= NT) {
+            const int cm = min(G, most - k0);
+            for (int k = 0; k < cm; k++) {
+                if (k < cnt) {  // (the two groups differ only at the end of the smaller one)
+                    const int t = gl - st_at[k];  // this column's tap of the node
+                    const bool in = (unsigned)t < (unsigned)NT;
+                    const C cv = st_cv[k * NT + (in ? t : 0)];
+                    const T cr = in ? cv.x : (T)0, ci = in ? cv.y : (T)0;
+                    T w[TDP];
+                    load_aligned16<T, TDP>(st_w0 + k * TDP, w);
 #pragma unroll
-                            for (int r = 0; r < NT; r++) {
-                                flush_row(r);
-                                acc[r].x = (T)0;
-                                acc[r].y = (T)0;
-                            }
-                        } else {
-                            for (int i = 0; i < dr; i++) {
-                                flush_row(0);
-                                cur++;
-#pragma unroll
-                                for (int r = 0; r + 1 < NT; r++) acc[r] = acc[r + 1];
-                                acc[NT - 1].x = (T)0;
-                                acc[NT - 1].y = (T)0;
-                            }
-                        }
+                    for (int j = 0; j < TD0; j++) {
+                        acc[j].x = fma(w[j], cr, acc[j].x);
+                        acc[j].y = fma(w[j], ci, acc[j].y);
                     }
-                    cur = at.x;
-                }
-                const int t = lane - at.y;  // this column's tap of the node
-                const bool in = t >= 0 && t < NT;
-                const C cv = st_cv[k * NT + (in ? t : 0)];
-                const T cr = in ? cv.x : (T)0, ci = in ? cv.y : (T)0;
-                const T *w0 = st_w0 + k * NTP;
-#pragma unroll
-                for (int r = 0; r < NT; r++) {
-                    const T w = w0[r];
-                    acc[r].x += w * cr;
-                    acc[r].y += w * ci;
                 }
             }
             __syncwarp();
         }
-        if (cur >= 0) {
+        // tile cell (j, gl) is grid point ((org0 - m + j) mod n0, (org1 - m + gl) mod n1)
+        if (P.count > 0 && gl < td1) {
+            const size_t gcol = (size_t)wrapn(org1 - MM + gl, g.n[1]);
 #pragma unroll
-            for (int r = 0; r < NT; r++) flush_row(r);
+            for (int j = 0; j < TD0; j++)
+                if (acc[j].x != (T)0 || acc[j].y != (T)0)
+                    global_add(grid + (size_t)wrapn(org0 - MM + j, g.n[0]) * g.n[1] + gcol,
+                               acc[j].x, acc[j].y);
         }
     }
     if (lane == 0) {  // the last warp to finish resets the counters for the next launch
@@ -1600,6 +1653,31 @@ static cudaError_t launch_persistent(K kernel, size_t smem, int threads, int max
     return cudaSuccess;
 }
 
+template <typename T, int MM, int BS0, int G>
+cudaError_t launch_rows(const Geom &g, const typename Cplx<T>::type *f,
+                        const typename RecOf<T>::type *rec, const int *perm,
+                        const SubProb *subs, int *work, typename Cplx<T>::type *grid,
+                        int warps_cap, cudaStream_t stream)
+{
+    const size_t smem = RowsShape<T, MM, BS0, G>::per_warp * kRowsWarps;
+    int blocks = 0;
+    cudaError_t e;
+    if (g.lin_k) {
+        e = launch_persistent(spread_rows_kernel<T, MM, true, BS0, G>, smem, 32 * kRowsWarps,
+                              warps_cap, blocks);
+        if (e != cudaSuccess) return e;
+        spread_rows_kernel<T, MM, true, BS0, G><<<blocks, 32 * kRowsWarps, smem, stream>>>(
+            g, make_wincoef<T, MM>(g), f, rec, perm, subs, work, grid);
+    } else {
+        e = launch_persistent(spread_rows_kernel<T, MM, false, BS0, G>, smem, 32 * kRowsWarps,
+                              warps_cap, blocks);
+        if (e != cudaSuccess) return e;
+        spread_rows_kernel<T, MM, false, BS0, G><<<blocks, 32 * kRowsWarps, smem, stream>>>(
+            g, make_wincoef<T, MM>(g), f, rec, perm, subs, work, grid);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T, int D, int MM>
 cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
                             const typename RecOf<T>::type *rec, const int *perm,
@@ -1624,15 +1702,18 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
     const size_t half_tiles = (size_t)(g.bs[0] + 2 * MM) *
                               (size_t)half_pitch<T, MM>(g.bs[D - 1] + 2 * MM) *
                               sizeof(typename Cplx<T>::type) * kHalfTiles;
+    constexpr size_t half_stage = half_stage_bytes<T, MM>();
     if (method == kSpreadOctet &&
         (D != 2 || 2 * MM + 1 > 16 || octet_tiles + spread_stage_bytes<T>() > limit))
         method = kSpreadWarpPrivate;
-    if (method == kSpreadRows && (D != 2 || g.bs[D - 1] + 2 * MM > 32))
+    if (method == kSpreadRows &&
+        (D != 2 || g.bs[D - 1] + 2 * MM > 32 || (g.bs[0] != 4 && g.bs[0] != 8)))
         method = kSpreadHalf;
+    const int rows_g = g.bs[D - 1] + 2 * MM <= 16 ? 16 : 32;  // lanes per tile of the rows form
     if (method == kSpreadStripe &&
         (D != 2 || g.sw.R <= 0 || stripe_smem_bytes<T, MM>(g.bs[0] + 2 * MM) > limit))
         method = kSpreadHalf;
-    if (method == kSpreadHalf && (D != 2 || half_tiles + half_stage_bytes<T>() > 227 * 1024))
+    if (method == kSpreadHalf && (D != 2 || half_tiles + half_stage > 227 * 1024))
         method = kSpreadWarpPrivate;
     const size_t plane_tile = D == 3 ? ((size_t)(g.bs[0] + 2 * MM) * (size_t)(g.bs[1] + 2 * MM) *
                                            (size_t)plane_pitch<T>(g.bs[D - 1] + 2 * MM) *
@@ -1670,38 +1751,35 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
         }
     } else if (method == kSpreadHalf) {
         if constexpr (D == 2) {
-            const size_t smem = half_tiles + half_stage_bytes<T>();
+            const size_t smem = half_tiles + half_stage;
             if (g.lin_k) {
                 e = launch_persistent(spread_half_kernel<T, MM, true>, smem, 32 * kHalfWarps,
                                       max_subs, blocks);
                 if (e != cudaSuccess) return e;
                 spread_half_kernel<T, MM, true><<<blocks, 32 * kHalfWarps, smem, stream>>>(
-                    g, f, rec, perm, subs, nsub_total, grid);
+                    g, make_wincoef<T, MM>(g), f, rec, perm, subs, nsub_total, grid);
             } else {
                 e = launch_persistent(spread_half_kernel<T, MM, false>, smem, 32 * kHalfWarps,
                                       max_subs, blocks);
                 if (e != cudaSuccess) return e;
                 spread_half_kernel<T, MM, false><<<blocks, 32 * kHalfWarps, smem, stream>>>(
-                    g, f, rec, perm, subs, nsub_total, grid);
+                    g, make_wincoef<T, MM>(g), f, rec, perm, subs, nsub_total, grid);
             }
         }
     } else if (method == kSpreadRows) {
         if constexpr (D == 2) {
-            const size_t smem = RowsShape<T, MM>::per_warp * kRowsWarps;
             const int warps_cap = (max_subs + kRowsWarps - 1) / kRowsWarps;
-            if (g.lin_k) {
-                e = launch_persistent(spread_rows_kernel<T, MM, true>, smem, 32 * kRowsWarps,
-                                      warps_cap, blocks);
-                if (e != cudaSuccess) return e;
-                spread_rows_kernel<T, MM, true><<<blocks, 32 * kRowsWarps, smem, stream>>>(
-                    g, make_wincoef<T, MM>(g), f, rec, perm, subs, nsub_total, grid);
-            } else {
-                e = launch_persistent(spread_rows_kernel<T, MM, false>, smem, 32 * kRowsWarps,
-                                      warps_cap, blocks);
-                if (e != cudaSuccess) return e;
-                spread_rows_kernel<T, MM, false><<<blocks, 32 * kRowsWarps, smem, stream>>>(
-                    g, make_wincoef<T, MM>(g), f, rec, perm, subs, nsub_total, grid);
-            }
+            if (g.bs[0] == 4)
+                e = rows_g == 16 ? launch_rows<T, MM, 4, 16>(g, f, rec, perm, subs, nsub_total,
+                                                              grid, warps_cap, stream)
+                                 : launch_rows<T, MM, 4, 32>(g, f, rec, perm, subs, nsub_total,
+                                                              grid, warps_cap, stream);
+            else
+                e = rows_g == 16 ? launch_rows<T, MM, 8, 16>(g, f, rec, perm, subs, nsub_total,
+                                                              grid, warps_cap, stream)
+                                 : launch_rows<T, MM, 8, 32>(g, f, rec, perm, subs, nsub_total,
+                                                              grid, warps_cap, stream);
+            if (e != cudaSuccess) return e;
         }
     } else if (method == kSpreadStripe) {
         if constexpr (D == 2) {
