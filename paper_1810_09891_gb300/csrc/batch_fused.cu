@@ -5,10 +5,11 @@
 //   - B^H (spreading): the plans' subproblem lists concatenated, claimed one at a time through a
 //     work counter (persistent CTAs, as in the single-plan half-warp form);
 //   - the FFT passes: (plan, P lines) blocks (launch_fft_fused, fft_impl.cuh).
-// The kernels here are the 2-D FP32 forms (half-warp spreading, thread interpolation) for plans
-// of one window cutoff m and one window; a CTA looks its plan up in the per-plan table and copies
-// that plan's geometry into shared memory (and its window polynomials into registers, or reads
-// them from the kernel argument when every plan has the same ones) before working on it.
+// The kernels here are the 2-D FP32 forms (rows or half-warp spreading, thread interpolation) for
+// plans of one window cutoff m and one window; a CTA (a warp group in the rows form) looks its
+// plan up in the per-plan table and reads that plan's geometry before working on it; the window
+// polynomials come from the kernel argument when every plan has the same ones, else from each
+// plan's table.
 #include "interp_impl.cuh"
 #include "spread_impl.cuh"
 
@@ -204,6 +205,52 @@ __global__ void __launch_bounds__(32 * kHalfWarps)
     finish_subproblems(work);
 }
 
+// B^H of every plan in the rows form (register tiles, one subproblem per half-warp or warp):
+// the warps claim entries of the concatenated subproblem lists through the batch's work
+// counter; each group looks up its own entry's plan, so the two groups of a warp may work on
+// different plans. Every plan has sort bins of BS0 rows and tiles at most G cells wide.
+template <typename T, int MM, int BS0, int G, bool SHARED>
+__global__ void __launch_bounds__(32 * kRowsWarps)
+    spread_rows_fused_kernel(const FusedNodePlan *__restrict__ plans, int nplans,
+                             const int *__restrict__ item_start, int *__restrict__ work,
+                             const __grid_constant__ WinCoef<T, MM> wc,
+                             const __grid_constant__ FusedPtrs ptrs)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    using Sh = RowsShape<T, MM, BS0, G>;
+    constexpr int GROUPS = Sh::GROUPS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_start[kFusedMax + 1];
+    for (int q = threadIdx.x; q <= nplans; q += blockDim.x) s_start[q] = item_start[q];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / G, gl = lane % G;
+    const RowsStage<T, MM, BS0, G> st(smem_raw + (size_t)warp * Sh::per_warp +
+                                      (size_t)grp * Sh::group);
+    const int nitems = work[0];
+    for (int sp0 = rows_claim(work, GROUPS); sp0 < nitems; sp0 = rows_claim(work, GROUPS)) {
+        const int sp = sp0 + grp;
+        SubProb P;
+        P.bin = 0;
+        P.start = 0;
+        P.count = 0;
+        int p = 0;
+        if (sp < nitems) {
+            p = find_plan(nplans, sp, [&](int q) { return s_start[q]; });
+            P = plans[p].subs[sp - s_start[p]];
+        }
+        int most = P.count;
+        if constexpr (GROUPS == 2) most = max(most, __shfl_xor_sync(0xffffffffu, most, 16));
+        const Geom &g = plans[p].g;
+        const T *coef = SHARED ? wc.c : static_cast<const T *>(g.poly);
+        rows_subproblem<T, MM, 1, BS0, G>(g, coef, P, most, static_cast<const C *>(ptrs.in[p]),
+                                          static_cast<const Rec *>(plans[p].rec), plans[p].perm,
+                                          static_cast<C *>(plans[p].grid), st, gl);
+    }
+    rows_finish(work);
+}
+
 template <typename K>
 int persistent_blocks(K kernel, int threads, size_t smem, int cap)
 {
@@ -259,12 +306,54 @@ cudaError_t spread_fused_ms(const FusedNodePlan *plans, int nplans, const int *i
     return cudaGetLastError();
 }
 
+template <typename T, int MM, int BS0, int G, bool SHARED>
+cudaError_t spread_rows_fused_ms(const FusedNodePlan *plans, int nplans, const int *item_start,
+                                 int *work, int max_items, const WinCoef<T, MM> &wc,
+                                 const FusedPtrs &ptrs, cudaStream_t stream)
+{
+    using Sh = RowsShape<T, MM, BS0, G>;
+    const size_t smem = Sh::per_warp * kRowsWarps;
+    cudaError_t e = ensure_dynamic_smem(spread_rows_fused_kernel<T, MM, BS0, G, SHARED>, smem);
+    if (e != cudaSuccess) return e;
+    const int cap = (max_items + Sh::GROUPS * kRowsWarps - 1) / (Sh::GROUPS * kRowsWarps);
+    const int blocks = persistent_blocks(spread_rows_fused_kernel<T, MM, BS0, G, SHARED>,
+                                         32 * kRowsWarps, smem, cap);
+    if (!blocks) return cudaErrorInvalidValue;
+    spread_rows_fused_kernel<T, MM, BS0, G, SHARED><<<blocks, 32 * kRowsWarps, smem, stream>>>(
+        plans, nplans, item_start, work, wc, ptrs);
+    return cudaGetLastError();
+}
+
+template <typename T, int MM, int BS0, int G>
+cudaError_t spread_rows_fused_m(const FusedNodePlan *plans, int nplans, const int *item_start,
+                                int *work, int max_items, const WinCoef<T, MM> &wc,
+                                const FusedPtrs &ptrs, bool shared, cudaStream_t stream)
+{
+    return shared ? spread_rows_fused_ms<T, MM, BS0, G, true>(plans, nplans, item_start, work,
+                                                              max_items, wc, ptrs, stream)
+                  : spread_rows_fused_ms<T, MM, BS0, G, false>(plans, nplans, item_start, work,
+                                                               max_items, wc, ptrs, stream);
+}
+
 template <typename T, int MM>
 cudaError_t spread_fused_m(const FusedNodePlan *plans, int nplans, const int *item_start,
                            int *work, int max_items, int tile_cells, const Geom &g0,
-                           const FusedPtrs &ptrs, bool shared, cudaStream_t stream)
+                           const FusedPtrs &ptrs, bool shared, int rows_bs0, int rows_g,
+                           cudaStream_t stream)
 {
     const WinCoef<T, MM> wc = make_wincoef<T, MM>(g0);
+    if (rows_bs0 == 4 && rows_g == 16)
+        return spread_rows_fused_m<T, MM, 4, 16>(plans, nplans, item_start, work, max_items, wc,
+                                                 ptrs, shared, stream);
+    if (rows_bs0 == 4 && rows_g == 32)
+        return spread_rows_fused_m<T, MM, 4, 32>(plans, nplans, item_start, work, max_items, wc,
+                                                 ptrs, shared, stream);
+    if (rows_bs0 == 8 && rows_g == 16)
+        return spread_rows_fused_m<T, MM, 8, 16>(plans, nplans, item_start, work, max_items, wc,
+                                                 ptrs, shared, stream);
+    if (rows_bs0 == 8 && rows_g == 32)
+        return spread_rows_fused_m<T, MM, 8, 32>(plans, nplans, item_start, work, max_items, wc,
+                                                 ptrs, shared, stream);
     return shared ? spread_fused_ms<T, MM, true>(plans, nplans, item_start, work, max_items,
                                                  tile_cells, wc, ptrs, stream)
                   : spread_fused_ms<T, MM, false>(plans, nplans, item_start, work, max_items,
@@ -311,7 +400,8 @@ cudaError_t launch_interp_fused(const FusedNodePlan *plans, int nplans, const Fu
 
 cudaError_t launch_spread_fused(const FusedNodePlan *plans, int nplans, int *item_start,
                                 int *work, int max_items, int tile_cells, const Geom &g0,
-                                const FusedPtrs &ptrs, bool shared_window, cudaStream_t stream)
+                                const FusedPtrs &ptrs, bool shared_window, int rows_bs0,
+                                int rows_g, cudaStream_t stream)
 {
     detail::fused_items_kernel<<<1, kFusedMax, 0, stream>>>(plans, nplans, item_start, work);
     cudaError_t e = cudaGetLastError();
@@ -321,7 +411,8 @@ cudaError_t launch_spread_fused(const FusedNodePlan *plans, int nplans, int *ite
 #define GB_CASE(MM)                                                                               \
     case MM:                                                                                      \
         return detail::spread_fused_m<float, MM>(plans, nplans, item_start, work, max_items,      \
-                                                 tile_cells, g0, ptrs, shared_window, stream);
+                                                 tile_cells, g0, ptrs, shared_window, rows_bs0, \
+                                                 rows_g, stream);
         GB_CASE(1) GB_CASE(2) GB_CASE(3) GB_CASE(4) GB_CASE(5) GB_CASE(6) GB_CASE(7) GB_CASE(8)
 #undef GB_CASE
     default: return cudaErrorInvalidValue;

@@ -319,7 +319,8 @@ cudaError_t launch_interp_fused(const FusedNodePlan *plans, int nplans, const Fu
                                 bool shared_window, cudaStream_t stream);
 cudaError_t launch_spread_fused(const FusedNodePlan *plans, int nplans, int *item_start,
                                 int *work, int max_items, int tile_cells, const Geom &g0,
-                                const FusedPtrs &ptrs, bool shared_window, cudaStream_t stream);
+                                const FusedPtrs &ptrs, bool shared_window, int rows_bs0,
+                                int rows_g, cudaStream_t stream);
 int half_tile_cells_f32(int m, int bs0, int bs1);  // cells of one half-warp tile (FP32)
 size_t half_smem_bytes_f32(int m, int tile_cells);  // shared memory of the half-warp form
 

@@ -347,6 +347,10 @@ void setup_bins(gbnfft_plan *p)
             continue;
         }
         int64_t bs = p->bin_req[t] > 0 ? p->bin_req[t] : bin_default[p->d - 1][t];
+        // FP32 2-D with m <= 4: 4 x 8 bins, whose tiles (at most 16 cells wide) the rows
+        // spreading form holds a half-warp per tile
+        if (p->bin_req[t] <= 0 && p->d == 2 && p->dtype == NFFT_FP32 && p->m <= 4)
+            bs = t == 0 ? 4 : 8;
         if (is_pow2(p->n[t])) {
             if (bs > p->n[t]) bs = p->n[t];  // one bin covers the axis
         } else {
@@ -376,8 +380,12 @@ void setup_bins(gbnfft_plan *p)
         nbins *= g.nb[t];
     }
     p->nbins = (int)nbins;
+    // 2-D FP32: short subproblems even out the load of the heavy bins (64 nodes for the rows
+    // form's 4 x 8 bins, 128 for larger bins)
     p->sub_max = p->sub_req > 0 ? (int)p->sub_req
-                                : (p->d == 2 && p->dtype == NFFT_FP32 ? 128 : kMaxSub);
+                                : (p->d == 2 && p->dtype == NFFT_FP32
+                                       ? (g.bs[0] * g.bs[1] <= 32 ? 64 : 128)
+                                       : kMaxSub);
     p->max_subs = (int)(nbins + (p->M + p->sub_max - 1) / p->sub_max + 1);
     // stripe-form work (d = 2): stripes of stripe_width(m) >= 2m cells made of whole sort bins,
     // kStripeS stripes per super-bin; the super-bin tile must not wrap onto itself
@@ -1435,6 +1443,7 @@ struct gbnfft_batch {
     size_t fft_smem[kFusedPasses] = {};
     int node_blocks = 0, zero_blocks = 0, max_items = 0, tile_cells = 0;
     bool shared_window = false;  // every plan has the same window polynomials
+    int rows_bs0 = 0, rows_g = 0;  // rows-form spreading (bin rows, lanes per tile), 0: half-warp
     FusedOffsets offsets{};      // per-plan first blocks of the per-node and zeroing stages
 };
 
@@ -1464,9 +1473,9 @@ FusedSig fused_sig(const gbnfft_plan *p)
     return s;
 }
 
-// Whether the plans can run fused: 2-D FP32, one m and window, the half-warp spreading form and
-// the thread interpolation form (automatic or chosen), polynomial window, power-of-two FFT
-// lengths 16..4096.
+// Whether the plans can run fused: 2-D FP32, one m and window, the half-warp or automatic
+// spreading form and the thread interpolation form (automatic or chosen), polynomial window,
+// power-of-two FFT lengths 16..4096.
 bool fusable(const gbnfft_batch *b)
 {
     const auto &ps = b->plans;
@@ -1607,6 +1616,18 @@ int fused_build(gbnfft_batch *b)
     b->shared_window = true;
     for (int i = 1; i < n; i++)
         b->shared_window &= b->plans[i]->poly_host == b->plans[0]->poly_host;
+    // the rows form when every plan spreads automatically with sort bins of one height (4 or 8
+    // rows) and tiles at most 32 cells wide (16: a half-warp per tile)
+    b->rows_bs0 = b->plans[0]->geom.bs[0];
+    b->rows_g = 16;
+    for (int i = 0; i < n; i++) {
+        const gbnfft_plan *p = b->plans[i];
+        const int td1 = p->geom.bs[1] + 2 * p->m;
+        if (p->geom.spread_method != kSpreadAuto || p->geom.bs[0] != b->rows_bs0 || td1 > 32)
+            b->rows_bs0 = 0;
+        if (td1 > 16) b->rows_g = 32;
+    }
+    if (b->rows_bs0 != 4 && b->rows_bs0 != 8) b->rows_bs0 = 0;
     b->node_blocks = node_blocks;
     b->zero_blocks = zero_blocks;
     b->max_items = max_items;
@@ -1675,7 +1696,8 @@ int fused_adjoint(gbnfft_batch *b, const void *const *f, void *const *fhat)
     GB_CHECK(launch_zero_fused(nodes, n, b->offsets, sizeof(float2), b->stream));
     GB_CHECK(launch_spread_fused(nodes, n, fused_at<int>(b, b->off_istart),
                                  fused_at<int>(b, b->off_work), b->max_items, b->tile_cells,
-                                 b->plans[0]->geom, ptrs, b->shared_window, b->stream));
+                                 b->plans[0]->geom, ptrs, b->shared_window, b->rows_bs0,
+                                 b->rows_g, b->stream));
     int rc = fused_fft(b, kAdjCols, +1, ptrs);
     if (!rc) rc = fused_fft(b, kAdjRows, +1, ptrs);
     return rc;

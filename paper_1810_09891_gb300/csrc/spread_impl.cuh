@@ -1058,6 +1058,131 @@ __device__ __forceinline__ void load_aligned16(const T *p, T *w)
     }
 }
 
+// Staging area of one group of the rows form (G nodes).
+template <typename T, int MM, int BS0, int G> struct RowsStage {
+    using C = typename Cplx<T>::type;
+    using Sh = RowsShape<T, MM, BS0, G>;
+    T *w0;   // [G][TDP] row weights at the node's tile rows
+    C *cv;   // [G][NT] column weights times the node value
+    int *at; // [G] the node's first tile column
+    __device__ __forceinline__ RowsStage(unsigned char *base)
+        : w0(reinterpret_cast<T *>(base)),
+          cv(reinterpret_cast<C *>(base + G * Sh::TDP * sizeof(T))),
+          at(reinterpret_cast<int *>(base + G * (Sh::TDP * sizeof(T) + Sh::NT * sizeof(C))))
+    {
+    }
+};
+
+// One subproblem P of one group (gl = the lane's index in its group): `most` is the larger
+// node count of the warp's two subproblems (the warp runs that many rounds; the group with
+// fewer nodes idles at the end). Every lane of the warp calls it. `coef` is the polynomial
+// window table of axis 0 (axis 1 follows it).
+template <typename T, int MM, int MODE, int BS0, int G>
+__device__ __forceinline__ void rows_subproblem(
+    const Geom &g, const T *__restrict__ coef, const SubProb &P, int most,
+    const typename Cplx<T>::type *__restrict__ f, const typename RecOf<T>::type *__restrict__ rec,
+    const int *__restrict__ perm, typename Cplx<T>::type *__restrict__ grid,
+    const RowsStage<T, MM, BS0, G> &st, int gl)
+{
+    using C = typename Cplx<T>::type;
+    using Rec = typename RecOf<T>::type;
+    using Sh = RowsShape<T, MM, BS0, G>;
+    constexpr int NT = Sh::NT, TD0 = Sh::TD0, TDP = Sh::TDP;
+    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
+    const int org1 = (P.bin % g.nb[1]) * g.bs[1];
+    const int org0 = (P.bin / g.nb[1]) * g.bs[0];
+    C acc[TD0];
+#pragma unroll
+    for (int j = 0; j < TD0; j++) {
+        acc[j].x = (T)0;
+        acc[j].y = (T)0;
+    }
+    Rec nr;  // this lane's node of the next round, loaded one round ahead
+    C nv;
+    if (gl < P.count) {
+        nr = rec[P.start + gl];
+        nv = f[perm[P.start + gl]];
+    }
+    for (int k0 = 0; k0 < most; k0 += G) {
+        const int cnt = min(G, P.count - k0);  // this group's nodes in this round (may be <= 0)
+        if (gl < cnt) {  // stage this lane's node
+            const Rec r = nr;
+            const C v = nv;
+            if (k0 + G + gl < P.count) {
+                const int s = P.start + k0 + G + gl;
+                nr = rec[s];
+                nv = f[perm[s]];
+            }
+            const int loc1 = (r.cell & g.cmask[1]) - org1;
+            const int loc0 = ((r.cell >> g.cbits[1]) & g.cmask[0]) - org0;
+            T w0[NT], w1[NT];
+            eval_taps<T, MM, 0, MODE>(g, coef, 0, r.fr[0], w0);
+            eval_taps<T, MM, 0, MODE>(g, coef + AS, 1, r.fr[1], w1);
+            T *wr = st.w0 + gl * TDP;  // tile rows loc0 .. loc0 + 2m, zeros elsewhere
+#pragma unroll
+            for (int j = 0; j < TDP; j++) wr[j] = (T)0;
+#pragma unroll
+            for (int t = 0; t < NT; t++) wr[loc0 + t] = w0[t];
+#pragma unroll
+            for (int t = 0; t < NT; t++) {
+                C q;
+                q.x = w1[t] * v.x;
+                q.y = w1[t] * v.y;
+                st.cv[gl * NT + t] = q;
+            }
+            st.at[gl] = loc1;
+        }
+        __syncwarp();
+        const int cm = min(G, most - k0);
+        for (int k = 0; k < cm; k++) {
+            if (k < cnt) {  // (the two groups differ only at the end of the smaller one)
+                const int t = gl - st.at[k];  // this column's tap of the node
+                const bool in = (unsigned)t < (unsigned)NT;
+                const C cv = st.cv[k * NT + (in ? t : 0)];
+                const T cr = in ? cv.x : (T)0, ci = in ? cv.y : (T)0;
+                T w[TDP];
+                load_aligned16<T, TDP>(st.w0 + k * TDP, w);
+#pragma unroll
+                for (int j = 0; j < TD0; j++) {
+                    acc[j].x = fma(w[j], cr, acc[j].x);
+                    acc[j].y = fma(w[j], ci, acc[j].y);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // tile cell (j, gl) is grid point ((org0 - m + j) mod n0, (org1 - m + gl) mod n1)
+    if (P.count > 0 && gl < g.bs[1] + 2 * MM) {
+        const size_t gcol = (size_t)wrapn(org1 - MM + gl, g.n[1]);
+#pragma unroll
+        for (int j = 0; j < TD0; j++)
+            if (acc[j].x != (T)0 || acc[j].y != (T)0)
+                global_add(grid + (size_t)wrapn(org0 - MM + j, g.n[0]) * g.n[1] + gcol,
+                           acc[j].x, acc[j].y);
+    }
+}
+
+// Per-warp claims of the rows form: lane 0 takes GROUPS consecutive entries of the list at a
+// time (work[1] the next unclaimed entry); the last warp to finish puts work[1] and work[2] back
+// to zero for the next launch.
+__device__ __forceinline__ int rows_claim(int *work, int groups)
+{
+    int sp0 = 0;
+    if ((threadIdx.x & 31) == 0) sp0 = atomicAdd(work + 1, groups);
+    return __shfl_sync(0xffffffffu, sp0, 0);
+}
+
+__device__ __forceinline__ void rows_finish(int *work)
+{
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        if (atomicAdd(work + 2, 1) == (int)(gridDim.x * (blockDim.x >> 5)) - 1) {
+            work[1] = 0;
+            work[2] = 0;
+        }
+    }
+}
+
 template <typename T, int MM, bool LIN, int BS0, int G>
 __global__ void __launch_bounds__(32 * kRowsWarps)
     spread_rows_kernel(Geom g, const __grid_constant__ WinCoef<T, MM> wc,
@@ -1066,113 +1191,26 @@ __global__ void __launch_bounds__(32 * kRowsWarps)
                        const int *__restrict__ perm, const SubProb *__restrict__ subs,
                        int *__restrict__ work, typename Cplx<T>::type *__restrict__ grid)
 {
-    using C = typename Cplx<T>::type;
-    using Rec = typename RecOf<T>::type;
     using Sh = RowsShape<T, MM, BS0, G>;
-    constexpr int NT = Sh::NT, TD0 = Sh::TD0, TDP = Sh::TDP, GROUPS = Sh::GROUPS;
-    constexpr int AS = poly_axis_stride(sizeof(T) == 8, MM);
-    constexpr int MODE = LIN ? 2 : 1;
+    constexpr int GROUPS = Sh::GROUPS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G, gl = lane % G;
-    unsigned char *mine = smem_raw + (size_t)warp * Sh::per_warp + (size_t)grp * Sh::group;
-    T *st_w0 = reinterpret_cast<T *>(mine);                             // [G][TDP]
-    C *st_cv = reinterpret_cast<C *>(mine + G * TDP * sizeof(T));       // [G][NT]
-    int *st_at = reinterpret_cast<int *>(mine + G * (TDP * sizeof(T) + NT * sizeof(C)));
-    const int td1 = g.bs[1] + 2 * MM;  // tile columns (<= G)
+    const RowsStage<T, MM, BS0, G> st(smem_raw + (size_t)warp * Sh::per_warp +
+                                      (size_t)grp * Sh::group);
     const int nsub = work[0];
-    for (;;) {
-        int sp0 = 0;
-        if (lane == 0) sp0 = atomicAdd(work + 1, GROUPS);
-        sp0 = __shfl_sync(0xffffffffu, sp0, 0);
-        if (sp0 >= nsub) break;
+    for (int sp0 = rows_claim(work, GROUPS); sp0 < nsub; sp0 = rows_claim(work, GROUPS)) {
         const int sp = sp0 + grp;
         SubProb P;
         P.bin = 0;
         P.start = 0;
         P.count = 0;
         if (sp < nsub) P = subs[sp];
-        const int org1 = (P.bin % g.nb[1]) * g.bs[1];
-        const int org0 = (P.bin / g.nb[1]) * g.bs[0];
-        int most = P.count;  // rounds are run for the larger subproblem of the warp
+        int most = P.count;
         if constexpr (GROUPS == 2) most = max(most, __shfl_xor_sync(0xffffffffu, most, 16));
-        C acc[TD0];
-#pragma unroll
-        for (int j = 0; j < TD0; j++) {
-            acc[j].x = (T)0;
-            acc[j].y = (T)0;
-        }
-        Rec nr;  // this lane's node of the next round, loaded one round ahead
-        C nv;
-        if (gl < P.count) {
-            nr = rec[P.start + gl];
-            nv = f[perm[P.start + gl]];
-        }
-        for (int k0 = 0; k0 < most; k0 += G) {
-            const int cnt = min(G, P.count - k0);  // this group's nodes in this round (may be <= 0)
-            if (gl < cnt) {  // stage this lane's node
-                const Rec r = nr;
-                const C v = nv;
-                if (k0 + G + gl < P.count) {
-                    const int s = P.start + k0 + G + gl;
-                    nr = rec[s];
-                    nv = f[perm[s]];
-                }
-                const int loc1 = (r.cell & g.cmask[1]) - org1;
-                const int loc0 = ((r.cell >> g.cbits[1]) & g.cmask[0]) - org0;
-                T w0[NT], w1[NT];
-                eval_taps<T, MM, 0, MODE>(g, wc.c, 0, r.fr[0], w0);
-                eval_taps<T, MM, 0, MODE>(g, wc.c + AS, 1, r.fr[1], w1);
-                T *wr = st_w0 + gl * TDP;  // tile rows loc0 .. loc0 + 2m, zeros elsewhere
-#pragma unroll
-                for (int j = 0; j < TDP; j++) wr[j] = (T)0;
-#pragma unroll
-                for (int t = 0; t < NT; t++) wr[loc0 + t] = w0[t];
-#pragma unroll
-                for (int t = 0; t < NT; t++) {
-                    C q;
-                    q.x = w1[t] * v.x;
-                    q.y = w1[t] * v.y;
-                    st_cv[gl * NT + t] = q;
-                }
-                st_at[gl] = loc1;
-            }
-            __syncwarp();
-            const int cm = min(G, most - k0);
-            for (int k = 0; k < cm; k++) {
-                if (k < cnt) {  // (the two groups differ only at the end of the smaller one)
-                    const int t = gl - st_at[k];  // this column's tap of the node
-                    const bool in = (unsigned)t < (unsigned)NT;
-                    const C cv = st_cv[k * NT + (in ? t : 0)];
-                    const T cr = in ? cv.x : (T)0, ci = in ? cv.y : (T)0;
-                    T w[TDP];
-                    load_aligned16<T, TDP>(st_w0 + k * TDP, w);
-#pragma unroll
-                    for (int j = 0; j < TD0; j++) {
-                        acc[j].x = fma(w[j], cr, acc[j].x);
-                        acc[j].y = fma(w[j], ci, acc[j].y);
-                    }
-                }
-            }
-            __syncwarp();
-        }
-        // tile cell (j, gl) is grid point ((org0 - m + j) mod n0, (org1 - m + gl) mod n1)
-        if (P.count > 0 && gl < td1) {
-            const size_t gcol = (size_t)wrapn(org1 - MM + gl, g.n[1]);
-#pragma unroll
-            for (int j = 0; j < TD0; j++)
-                if (acc[j].x != (T)0 || acc[j].y != (T)0)
-                    global_add(grid + (size_t)wrapn(org0 - MM + j, g.n[0]) * g.n[1] + gcol,
-                               acc[j].x, acc[j].y);
-        }
+        rows_subproblem<T, MM, LIN ? 2 : 1, BS0, G>(g, wc.c, P, most, f, rec, perm, grid, st, gl);
     }
-    if (lane == 0) {  // the last warp to finish resets the counters for the next launch
-        __threadfence();
-        if (atomicAdd(work + 2, 1) == (int)(gridDim.x * kRowsWarps) - 1) {
-            work[1] = 0;
-            work[2] = 0;
-        }
-    }
+    rows_finish(work);
 }
 
 // ----------------------------------------------------------------------------- plane form (d = 3)
@@ -1690,9 +1728,9 @@ cudaError_t launch_spread_m(const Geom &g, const typename Cplx<T>::type *f,
     int method = g.spread_method;
     if (method == kSpreadAuto) {
         method = tile * kSpreadWarps <= 64 * 1024 ? kSpreadWarpPrivate : kSpreadWarpAtomic;
-        // measured fastest for 2-D: sixteen lanes per node in FP32, eight in FP64 (both with
-        // private tiles)
-        if (D == 2) method = sizeof(T) == 8 ? kSpreadOctet : kSpreadHalf;
+        // measured fastest for 2-D: register tiles in FP32, sixteen lanes per node with private
+        // tiles in FP64 (where the window evaluation, once per node, dominates)
+        if (D == 2) method = sizeof(T) == 8 ? kSpreadHalf : kSpreadRows;
         if (D == 3) method = kSpreadPlane;
     }
     // a form whose shared memory does not fit falls back to the one-tile form
