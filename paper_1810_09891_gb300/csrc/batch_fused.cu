@@ -229,17 +229,26 @@ __global__ void __launch_bounds__(32 * kRowsWarps)
     const RowsStage<T, MM, BS0, G> st(smem_raw + (size_t)warp * Sh::per_warp +
                                       (size_t)grp * Sh::group);
     const int nitems = work[0];
-    for (int sp0 = rows_claim(work, GROUPS); sp0 < nitems; sp0 = rows_claim(work, GROUPS)) {
-        const int sp = sp0 + grp;
+    auto entry = [&](int sp0, int &p) {  // this group's entry of a claim and its plan
         SubProb P;
         P.bin = 0;
         P.start = 0;
         P.count = 0;
-        int p = 0;
+        p = 0;
+        const int sp = sp0 + grp;
         if (sp < nitems) {
             p = find_plan(nplans, sp, [&](int q) { return s_start[q]; });
             P = plans[p].subs[sp - s_start[p]];
         }
+        return P;
+    };
+    int p;
+    int sp0 = rows_claim(work, GROUPS);
+    SubProb P = entry(sp0, p);
+    while (sp0 < nitems) {
+        int pn;
+        const int sp0n = rows_claim(work, GROUPS);  // the next claim, read while this one runs
+        const SubProb Pn = entry(sp0n, pn);
         int most = P.count;
         if constexpr (GROUPS == 2) most = max(most, __shfl_xor_sync(0xffffffffu, most, 16));
         const Geom &g = plans[p].g;
@@ -247,6 +256,9 @@ __global__ void __launch_bounds__(32 * kRowsWarps)
         rows_subproblem<T, MM, 1, BS0, G>(g, coef, P, most, static_cast<const C *>(ptrs.in[p]),
                                           static_cast<const Rec *>(plans[p].rec), plans[p].perm,
                                           static_cast<C *>(plans[p].grid), st, gl);
+        sp0 = sp0n;
+        P = Pn;
+        p = pn;
     }
     rows_finish(work);
 }

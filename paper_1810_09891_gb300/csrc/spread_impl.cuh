@@ -1134,8 +1134,9 @@ __device__ __forceinline__ void rows_subproblem(
         }
         __syncwarp();
         const int cm = min(G, most - k0);
-        for (int k = 0; k < cm; k++) {
-            if (k < cnt) {  // (the two groups differ only at the end of the smaller one)
+        // one node of the round (the two groups differ only at the end of the smaller one)
+        auto add_node = [&](int k) {
+            if (k < cnt) {
                 const int t = gl - st.at[k];  // this column's tap of the node
                 const bool in = (unsigned)t < (unsigned)NT;
                 const C cv = st.cv[k * NT + (in ? t : 0)];
@@ -1148,7 +1149,13 @@ __device__ __forceinline__ void rows_subproblem(
                     acc[j].y = fma(w[j], ci, acc[j].y);
                 }
             }
+        };
+        int k = 0;
+        for (; k + 2 <= cm; k += 2) {
+            add_node(k);
+            add_node(k + 1);
         }
+        if (k < cm) add_node(k);
         __syncwarp();
     }
     // tile cell (j, gl) is grid point ((org0 - m + j) mod n0, (org1 - m + gl) mod n1)
@@ -1199,16 +1206,24 @@ __global__ void __launch_bounds__(32 * kRowsWarps)
     const RowsStage<T, MM, BS0, G> st(smem_raw + (size_t)warp * Sh::per_warp +
                                       (size_t)grp * Sh::group);
     const int nsub = work[0];
-    for (int sp0 = rows_claim(work, GROUPS); sp0 < nsub; sp0 = rows_claim(work, GROUPS)) {
-        const int sp = sp0 + grp;
+    auto entry = [&](int sp0) {  // this group's entry of a claim (empty past the list)
         SubProb P;
         P.bin = 0;
         P.start = 0;
         P.count = 0;
-        if (sp < nsub) P = subs[sp];
+        if (sp0 + grp < nsub) P = subs[sp0 + grp];
+        return P;
+    };
+    int sp0 = rows_claim(work, GROUPS);
+    SubProb P = entry(sp0);
+    while (sp0 < nsub) {
+        const int sp0n = rows_claim(work, GROUPS);  // the next claim, read while this one runs
+        const SubProb Pn = entry(sp0n);
         int most = P.count;
         if constexpr (GROUPS == 2) most = max(most, __shfl_xor_sync(0xffffffffu, most, 16));
         rows_subproblem<T, MM, LIN ? 2 : 1, BS0, G>(g, wc.c, P, most, f, rec, perm, grid, st, gl);
+        sp0 = sp0n;
+        P = Pn;
     }
     rows_finish(work);
 }
