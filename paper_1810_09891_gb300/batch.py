@@ -8,8 +8,8 @@ forked from and joined into the current stream). ``trafo`` / ``adjoint`` / ``bac
 library batch; ``capture`` records the forward and the adjoint of the whole batch into one CUDA
 graph over static input and output buffers, and ``replay`` launches the batch with a single
 graph launch (no per-kernel host overhead).
-``autotune`` chooses, per plan, the spreading method and bin sizes by timing candidates on the
-plan's own nodes (the measured counterpart of the plan search the paper's FFTW flags select,
+``autotune`` chooses, per plan, the spreading method, bin sizes and subproblem size, then the
+interpolation form (threads per node), by timing candidates on the plan's own nodes (the measured counterpart of the plan search the paper's FFTW flags select,
 Section 3.1, Table tab:fttwflags). Every candidate computes the same transform up to rounding.
 """
 from __future__ import annotations
@@ -36,14 +36,18 @@ def _prod(v) -> int:
 CANDIDATES = {
     1: [(s, (b,), w) for s in ("warp_private", "warp_atomic") for b in (256, 1024, 4096)
         for w in (256, 1024)],
-    2: [("half", (8, 16), 128), ("half", (8, 16), 256), ("half", (16, 16), 128),
-        ("half", (16, 16), 256), ("octet", (8, 16), 1024), ("octet", (8, 16), 256),
-        ("warp_private", (16, 16), 256), ("warp_private", (8, 16), 256),
-        ("warp_private", (16, 16), 1024), ("warp_atomic", (16, 16), 256)],
+    2: [("rows", (4, 8), 32), ("rows", (4, 8), 64), ("rows", (4, 8), 128), ("rows", (8, 8), 64),
+        ("rows", (8, 16), 128), ("half", (8, 16), 128), ("half", (8, 16), 256),
+        ("half", (16, 16), 128), ("octet", (8, 16), 256), ("warp_private", (16, 16), 256),
+        ("warp_atomic", (16, 16), 256)],
     3: [("plane", b, w) for b in ((8, 8, 16), (4, 16, 16), (8, 8, 8)) for w in (512, 1024)] +
        [(s, b, w) for s in ("warp_atomic", "thread") for b in ((8, 8, 8), (8, 8, 16))
         for w in (256, 1024)],
 }
+
+# Interpolation forms, by threads per node: one thread per node, a warp per node, a CTA per
+# subproblem tile, eight lanes per node
+INTERP_CANDIDATES = ("thread", "warp", "tile", "octet")
 
 
 def _apply(plan: Plan, spread: str, bins, sub: int = 0) -> None:
@@ -53,31 +57,42 @@ def _apply(plan: Plan, spread: str, bins, sub: int = 0) -> None:
     plan.set_option("subproblem", int(sub))
 
 
-def time_step(plan: Plan, x: torch.Tensor, fhat: torch.Tensor, f: torch.Tensor,
-              steps: int = 5) -> float:
-    """Median milliseconds of one forward + one adjoint on the plan's stream (CUDA events)."""
-    plan.set_nodes(x)
-    plan.trafo(fhat)
-    plan.adjoint(f)
+def _timed(run, steps: int) -> float:
+    """Median milliseconds of `run()` over `steps` calls on the current stream (CUDA events)."""
+    run()
     times = []
     for _ in range(steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        plan.trafo(fhat)
-        plan.adjoint(f)
+        run()
         b.record()
         torch.cuda.synchronize()
         times.append(a.elapsed_time(b))
     return statistics.median(times)
 
 
+def time_step(plan: Plan, x: torch.Tensor, fhat: torch.Tensor, f: torch.Tensor,
+              steps: int = 5) -> float:
+    """Median milliseconds of one forward + one adjoint on the plan's stream (CUDA events)."""
+    plan.set_nodes(x)
+
+    def step():
+        plan.trafo(fhat)
+        plan.adjoint(f)
+    return _timed(step, steps)
+
+
 def autotune(plan: Plan, x: torch.Tensor, fhat: torch.Tensor, f: torch.Tensor,
-             candidates=None, steps: int = 5) -> dict:
-    """Try every candidate (spread_method, bins, subproblem) on this plan and these inputs; keep
-    the fastest (the plan ends configured with it, nodes set). Returns {"spread_method", "bins",
-    "subproblem", "ms", "tried": [(spread, bins, subproblem, ms), ...]}. Candidates that do not
-    fit the hardware are skipped."""
+             candidates=None, interp_candidates=INTERP_CANDIDATES, steps: int = 5) -> dict:
+    """Measured plan search. First every candidate (spread_method, bins, subproblem) on this
+    plan and these inputs, timing one forward + adjoint step (interpolation form automatic);
+    then, with the fastest of them, every interpolation form (threads per node), timing the
+    forward alone. The plan ends configured with the winners, nodes set. Returns
+    {"spread_method", "bins", "subproblem", "interp_method", "ms", "tried": [(spread, bins,
+    subproblem, ms), ...], "tried_interp": [(interp, ms), ...]}; "ms" is the step time with
+    both choices. Candidates that do not fit the hardware are skipped."""
     cands = candidates if candidates is not None else CANDIDATES[plan.d]
+    plan.set_option("interp_method", "auto")
     tried = []
     for spread, bins, sub in cands:
         bins = tuple(min(int(b), nn) for b, nn in zip(bins, plan.n))
@@ -89,11 +104,21 @@ def autotune(plan: Plan, x: torch.Tensor, fhat: torch.Tensor, f: torch.Tensor,
         tried.append((spread, bins, sub, ms))
     if not tried:
         raise RuntimeError("autotune: no candidate ran")
-    spread, bins, sub, ms = min(tried, key=lambda t: t[3])
+    spread, bins, sub, _ = min(tried, key=lambda t: t[3])
     _apply(plan, spread, bins, sub)
     plan.set_nodes(x)
-    return {"spread_method": spread, "bins": list(bins), "subproblem": sub, "ms": ms,
-            "tried": tried}
+    tried_interp = []
+    for form in interp_candidates:
+        try:
+            plan.set_option("interp_method", form)
+            tried_interp.append((form, _timed(lambda: plan.trafo(fhat), steps)))
+        except RuntimeError:
+            continue
+    interp = min(tried_interp, key=lambda t: t[1])[0] if tried_interp else "auto"
+    plan.set_option("interp_method", interp)
+    ms = time_step(plan, x, fhat, f, steps)
+    return {"spread_method": spread, "bins": list(bins), "subproblem": sub,
+            "interp_method": interp, "ms": ms, "tried": tried, "tried_interp": tried_interp}
 
 
 class TuningCache:
@@ -117,6 +142,7 @@ class TuningCache:
         self.table[self.key(plan)] = {"spread_method": choice["spread_method"],
                                       "bins": list(choice["bins"]),
                                       "subproblem": int(choice.get("subproblem", 0)),
+                                      "interp_method": choice.get("interp_method", "auto"),
                                       "ms": choice["ms"]}
         if self.path:
             with open(self.path, "w") as fh:
@@ -220,6 +246,7 @@ class PlanBatch:
                     cache.put(p, choice)
             else:
                 _apply(p, choice["spread_method"], choice["bins"], choice.get("subproblem", 0))
+                p.set_option("interp_method", choice.get("interp_method", "auto"))
                 p.set_nodes(x)
             out.append(choice)
         return out

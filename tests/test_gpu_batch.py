@@ -75,13 +75,17 @@ def test_autotune_keeps_the_transform(d, tmp_path):
     xt, fht, ft = to_dev(x, torch.float64), to_dev(fh, torch.float64), to_dev(f, torch.float64)
     choice = autotune(plan, xt, fht, ft, steps=2)
     assert choice["ms"] > 0 and len(choice["tried"]) >= 2
+    assert len(choice["tried_interp"]) >= 2  # the interpolation forms were timed too
+    assert choice["interp_method"] in [t[0] for t in choice["tried_interp"]]
     assert tuple(plan.bin) == tuple(choice["bins"])
     assert rel_l2(plan.trafo(fht).cpu().numpy(), oracle.nfft(x, fh, n=plan.n, m=4)) <= 1e-12
     assert rel_l2(plan.adjoint(ft).cpu().numpy(),
                   oracle.nfft_adjoint(x, f, N, n=plan.n, m=4)) <= 1e-12
     cache = TuningCache(str(tmp_path / "tune.json"))
     cache.put(plan, choice)
-    assert TuningCache(str(tmp_path / "tune.json")).get(plan)["bins"] == list(choice["bins"])
+    back = TuningCache(str(tmp_path / "tune.json")).get(plan)
+    assert back["bins"] == list(choice["bins"])
+    assert back["interp_method"] == choice["interp_method"]
 
 
 def test_batched_workload_specs():
