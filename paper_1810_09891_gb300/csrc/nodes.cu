@@ -136,20 +136,31 @@ cudaError_t launch_sub_starts(const int *sub_count, const int *bin_start, int S0
 }
 
 // Exclusive scans of the bin counts and of the subproblem counts ceil(count / sub_max), in one
-// CTA of 1024 threads (each thread owns a contiguous chunk of bins).
+// CTA of 1024 threads (each thread owns a contiguous chunk of bins). With `staged` the counts
+// are first copied into shared memory by coalesced loads (padded by one word per 32, so that
+// the threads' chunks of 32 fall on distinct banks) and the bin starts written back from there;
+// a thread walking its chunk in global memory would wait for one load after another.
+__host__ __device__ inline int scan_pad(int i) { return i + (i >> 5); }
+
 __global__ void __launch_bounds__(1024)
     bin_scan_kernel(const int *__restrict__ count, int *__restrict__ start,
                     int *__restrict__ sub_start, int *__restrict__ nsub_total, int nbins,
-                    int sub_max)
+                    int sub_max, int staged)
 {
+    extern __shared__ int s_cnt[];  // scan_pad(nbins) words when staged
     __shared__ int s_a[1024];
     __shared__ int s_b[1024];
     const int tid = threadIdx.x;
+    if (staged) {
+        for (int i = tid; i < nbins; i += 1024) s_cnt[scan_pad(i)] = count[i];
+        __syncthreads();
+    }
+    auto cnt_at = [&](int i) { return staged ? s_cnt[scan_pad(i)] : count[i]; };
     const int chunk = (nbins + 1023) / 1024;
     const int lo = min(nbins, tid * chunk), hi = min(nbins, lo + chunk);
     int a = 0, b = 0;
     for (int i = lo; i < hi; i++) {
-        const int c = count[i];
+        const int c = cnt_at(i);
         a += c;
         b += (c + sub_max - 1) / sub_max;
     }
@@ -167,11 +178,18 @@ __global__ void __launch_bounds__(1024)
     }
     int ra = s_a[tid] - a, rb = s_b[tid] - b;  // exclusive prefix of this chunk
     for (int i = lo; i < hi; i++) {
-        const int c = count[i];
-        start[i] = ra;
+        const int c = cnt_at(i);
         sub_start[i] = rb;
-        ra += c;
         rb += (c + sub_max - 1) / sub_max;
+        if (staged)
+            s_cnt[scan_pad(i)] = ra;  // (only this thread reads its chunk)
+        else
+            start[i] = ra;
+        ra += c;
+    }
+    if (staged) {
+        __syncthreads();
+        for (int i = tid; i < nbins; i += 1024) start[i] = s_cnt[scan_pad(i)];
     }
     if (tid == 1023) {
         nsub_total[0] = s_b[1023];
@@ -183,8 +201,15 @@ __global__ void __launch_bounds__(1024)
 cudaError_t launch_bin_scan(const int *bin_count, int *bin_start, int *sub_start, int *nsub_total,
                             int nbins, int sub_max, cudaStream_t stream)
 {
-    bin_scan_kernel<<<1, 1024, 0, stream>>>(bin_count, bin_start, sub_start, nsub_total, nbins,
-                                            sub_max);
+    constexpr int kStagedMax = 49152;  // bins staged in shared memory (196 KB with padding)
+    const int staged = nbins <= kStagedMax ? 1 : 0;
+    const size_t smem = staged ? (size_t)(scan_pad(nbins) + 1) * sizeof(int) : 0;
+    if (staged) {
+        const cudaError_t e = ensure_dynamic_smem(bin_scan_kernel, smem);
+        if (e != cudaSuccess) return e;
+    }
+    bin_scan_kernel<<<1, 1024, smem, stream>>>(bin_count, bin_start, sub_start, nsub_total,
+                                               nbins, sub_max, staged);
     return cudaGetLastError();
 }
 

@@ -268,6 +268,7 @@ struct gbnfft_plan {
     int64_t stripe_item_req = 0;  // requested nodes per stripe work item (0 = default)
     size_t ws_need = 0;
     bool nodes_ready = false;
+    bool stripe_ready = false;  // stripe-form work items built for the current node set
     // host-call staging (plan-owned)
     void *stage = nullptr;
     size_t stage_bytes = 0;
@@ -554,14 +555,22 @@ template <typename T> int do_set_nodes(gbnfft_plan *p, const void *x)
                                     at<Rec>(p, p->rec), at<int>(p, p->perm), s));
     GB_CHECK(launch_fill_subprobs(count, at<int>(p, p->binstart), at<int>(p, p->substart),
                                   at<SubProb>(p, p->subs), p->nbins, p->sub_max, s));
-    if (p->stripe_R > 0) {
-        const int item = p->stripe_item_req > 0 ? (int)p->stripe_item_req : kStripeItemDefault;
-        GB_CHECK(launch_stripe_items(count, p->geom.nb[0], p->geom.nb[1], p->stripe_R,
-                                     p->stripe_nsb1, at<int>(p, p->sbcount),
-                                     at<int>(p, p->sbstart), at<int>(p, p->sbsub),
-                                     at<int>(p, p->sbn), at<SubProb>(p, p->sitems), item, s));
-    }
+    p->stripe_ready = false;  // the stripe form's work items are built when it first runs
     return NFFT_OK;
+}
+
+// The stripe form's work items for the current node set (on the plan's stream, once per
+// set_nodes, on the first adjoint that uses the form).
+cudaError_t stripe_items(gbnfft_plan *p)
+{
+    if (p->stripe_R <= 0 || p->stripe_ready) return cudaSuccess;
+    const int item = p->stripe_item_req > 0 ? (int)p->stripe_item_req : kStripeItemDefault;
+    const cudaError_t e = launch_stripe_items(
+        at<int>(p, p->bincount), p->geom.nb[0], p->geom.nb[1], p->stripe_R, p->stripe_nsb1,
+        at<int>(p, p->sbcount), at<int>(p, p->sbstart), at<int>(p, p->sbsub), at<int>(p, p->sbn),
+        at<SubProb>(p, p->sitems), item, p->stream);
+    if (e == cudaSuccess) p->stripe_ready = true;
+    return e;
 }
 
 // The plan's geometry with the stripe-form work of the current node set attached.
@@ -608,6 +617,7 @@ template <typename T> int do_adjoint(gbnfft_plan *p, const void *f, void *fhat)
     }
     {
         ProfScope ps(p, NFFT_STAGE_SPREAD);
+        if (p->geom.spread_method == kSpreadStripe) GB_CHECK(stripe_items(p));
         GB_CHECK(launch_spread<T>(spread_geom(p), static_cast<const C *>(f), at<Rec>(p, p->rec),
                                   at<int>(p, p->perm), at<SubProb>(p, p->subs),
                                   at<int>(p, p->nsub), p->max_subs, at<C>(p, p->gA), p->stream));
