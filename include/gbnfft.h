@@ -95,7 +95,9 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
 /* Release the plan, its tables and any workspace it allocated itself. NULL is accepted. */
 int nfft_destroy(nfft_plan plan);
 
-/* Make every later call enqueue on this CUDA stream (a cudaStream_t; NULL = legacy default). */
+/* Make every later call enqueue on this CUDA stream (a cudaStream_t; NULL = legacy default).
+ * All calls of a plan share its workspace: work already enqueued on the old stream must be
+ * ordered before the next call on the new one (an event, or a synchronisation). */
 int nfft_set_stream(nfft_plan plan, void *cuda_stream);
 
 /* Device workspace the plan needs: oversampled grids, sorted node records, bin tables. */
@@ -251,10 +253,13 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           half-warps spread the even stripes together, then the odd ones (no
  *                           atomics, no private copies). Needs a last-axis bin of at most
  *                           2m rounded up to a power of two and n_(d-1) >= 16 such stripes + 2m,
- *                           8 (d = 2) no tile: a warp walks the row-ordered nodes of a
- *                           subproblem with lane c keeping 2m + 1 rows of tile column c in
- *                           registers, adding each completed row into the grid (needs a
- *                           last-axis bin + 2m <= 32).
+ *                           8 (d = 2) no shared-memory tile: a group of lanes (a half-warp when
+ *                           the last-axis bin + 2m <= 16, else a warp) holds a subproblem's whole
+ *                           tile in registers, lane c all rows of tile column c; each node's
+ *                           row weights are staged at its tile rows, so a node costs every lane
+ *                           one multiply-add per tile row. Needs a last-axis bin + 2m <= 32 and
+ *                           an axis-0 bin of 4 or 8.
+ *                           Automatic: 8 for d = 2 in FP32, 5 for d = 2 in FP64, 6 for d = 3.
  *                           A form whose tile does not fit or whose d does not match runs as
  *                           the nearest form that fits (6 -> 2 -> 1, 7 -> 5, 8 -> 5,
  *                           4/5 -> 3 -> 2 -> 1).
@@ -262,7 +267,8 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           2 one warp per node, 3 one thread per node gathering from a
  *                           shared-memory tile of the node's bin, 4 (d = 2, 3 and m <= 4;
  *                           else 1) eight lanes per node reading contiguous row segments.
- *   NFFT_OPT_BIN_0..2       bin (tile) size on axis 0..d-1: a power of two, 0 = default;
+ *   NFFT_OPT_BIN_0..2       bin (tile) size on axis 0..d-1: a power of two, 0 = default (1-D
+ *                           1024; 2-D 4 x 8 in FP32 with m <= 4, else 8 x 16; 3-D 8 x 8 x 16);
  *                           clipped to n_t (power-of-two n_t) or to the largest power of two
  *                           <= n_t / 2 (other n_t, whose last bin is then partial).
  *                           Changing a bin size discards the node precomputation (call
@@ -279,7 +285,8 @@ int nfft_profile_read(nfft_plan plan, double *ms, int64_t *count, int nstages);
  *                           x 2m values, plan precision) is allocated here and rebuilt when the
  *                           window changes; waits for the device to go idle.
  *   NFFT_OPT_SUBPROBLEM     nodes per spreading work item (a power of two in 32..1024, 0 = the
- *                           default: 128 for 2-D FP32, else 1024): the sorted nodes of a bin are
+ *                           default: for 2-D FP32 64 with bins of at most 32 cells, else 128;
+ *                           otherwise 1024): the sorted nodes of a bin are
  *                           cut into items of at most this many nodes. Like a bin size, it
  *                           discards the node precomputation and may change nfft_workspace_size.
  *   NFFT_OPT_STRIPE_ITEM    nodes per stripe in one work item of spreading form 7 (a power of

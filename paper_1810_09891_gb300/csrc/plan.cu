@@ -330,10 +330,12 @@ void layout_workspace(gbnfft_plan *p)
     p->ws_need = align_up(off, 256);
 }
 
-// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024, 2-D 8 x 16,
-// 3-D 8 x 8 x 16), clipped to n_t; nodes per spreading work item: the requested number, else 128
-// for 2-D FP32 and 1024 otherwise (the fastest choices measured with the default spreading forms
-// on a radial trajectory, whose bins hold very different node counts). Recomputes the bin
+// Bin (tile) sizes per axis: the requested ones, else the defaults (1-D 1024; 2-D 4 x 8 in FP32
+// with m <= 4, whose tiles the rows spreading form holds a half-warp per tile, else 8 x 16; 3-D
+// 8 x 8 x 16), clipped to n_t; nodes per spreading work item: the requested number, else for
+// 2-D FP32 64 (bins of at most 32 cells) or 128, and 1024 otherwise (the fastest choices
+// measured with the default spreading forms on a radial trajectory, whose bins hold very
+// different node counts). Recomputes the bin
 // counts and the workspace layout.
 void setup_bins(gbnfft_plan *p)
 {
