@@ -190,7 +190,8 @@ cudaError_t launch_bin_totals(const int *sub_count, int S0, int nbins, int *bin_
 cudaError_t launch_sub_starts(const int *sub_count, const int *bin_start, int S0, int nbins,
                               int *sub_start, cudaStream_t stream);
 cudaError_t launch_bin_scan(const int *bin_count, int *bin_start, int *sub_start, int *nsub_total,
-                            int nbins, int sub_max, cudaStream_t stream);
+                            int nbins, int sub_max, cudaStream_t stream, int nb0 = 0,
+                            int nb1 = 0);
 template <typename T>
 cudaError_t launch_node_scatter(const Geom &g, const T *x, int64_t M, const int2 *sub_rank,
                                 const int *sub_start, typename RecOf<T>::type *rec, int *perm,

@@ -136,28 +136,54 @@ cudaError_t launch_sub_starts(const int *sub_count, const int *bin_start, int S0
 }
 
 // Exclusive scans of the bin counts and of the subproblem counts ceil(count / sub_max), in one
-// CTA of 1024 threads (each thread owns a contiguous chunk of bins). With `staged` the counts
-// are first copied into shared memory by coalesced loads (padded by one word per 32, so that
-// the threads' chunks of 32 fall on distinct banks) and the bin starts written back from there;
-// a thread walking its chunk in global memory would wait for one load after another.
+// CTA of 1024 threads (each thread owns a contiguous chunk of slots). The scan visits the bins
+// in slot order: the natural order, or with nb1 > 0 (2-D) blocks of 2 x 2 bins one after the
+// other (block rows along axis 0, blocks along axis 1, inside a block the bins row-major), so
+// that consecutive sorted nodes cover a compact region of twice the bin in each direction;
+// slots of a partial block outside the bin grid are empty. With `staged` the counts are first
+// copied into shared memory (padded by one word per 32, so that the threads' chunks of 32 fall
+// on distinct banks) and the bin starts written back from there; a thread walking its chunk in
+// global memory would wait for one load after another.
 __host__ __device__ inline int scan_pad(int i) { return i + (i >> 5); }
+
+// The bin in slot i (-1: a slot of a partial block outside the grid).
+__host__ __device__ inline int scan_bin(int i, int nbins, int nb0, int nb1)
+{
+    if (nb1 <= 0) return i < nbins ? i : -1;
+    const int blk = i >> 2, q = i & 3, nbb1 = (nb1 + 1) >> 1;
+    const int b0 = 2 * (blk / nbb1) + (q >> 1), b1 = 2 * (blk % nbb1) + (q & 1);
+    return (b0 < nb0 && b1 < nb1) ? b0 * nb1 + b1 : -1;
+}
+
+__host__ __device__ inline int scan_slots(int nbins, int nb0, int nb1)
+{
+    return nb1 <= 0 ? nbins : 4 * ((nb0 + 1) >> 1) * ((nb1 + 1) >> 1);
+}
 
 __global__ void __launch_bounds__(1024)
     bin_scan_kernel(const int *__restrict__ count, int *__restrict__ start,
                     int *__restrict__ sub_start, int *__restrict__ nsub_total, int nbins,
-                    int sub_max, int staged)
+                    int nb0, int nb1, int sub_max, int staged)
 {
-    extern __shared__ int s_cnt[];  // scan_pad(nbins) words when staged
+    extern __shared__ int s_cnt[];  // scan_pad(slots) words when staged
     __shared__ int s_a[1024];
     __shared__ int s_b[1024];
     const int tid = threadIdx.x;
+    const int slots = scan_slots(nbins, nb0, nb1);
     if (staged) {
-        for (int i = tid; i < nbins; i += 1024) s_cnt[scan_pad(i)] = count[i];
+        for (int i = tid; i < slots; i += 1024) {
+            const int bin = scan_bin(i, nbins, nb0, nb1);
+            s_cnt[scan_pad(i)] = bin >= 0 ? count[bin] : 0;
+        }
         __syncthreads();
     }
-    auto cnt_at = [&](int i) { return staged ? s_cnt[scan_pad(i)] : count[i]; };
-    const int chunk = (nbins + 1023) / 1024;
-    const int lo = min(nbins, tid * chunk), hi = min(nbins, lo + chunk);
+    auto cnt_at = [&](int i) {
+        if (staged) return s_cnt[scan_pad(i)];
+        const int bin = scan_bin(i, nbins, nb0, nb1);
+        return bin >= 0 ? count[bin] : 0;
+    };
+    const int chunk = (slots + 1023) / 1024;
+    const int lo = min(slots, tid * chunk), hi = min(slots, lo + chunk);
     int a = 0, b = 0;
     for (int i = lo; i < hi; i++) {
         const int c = cnt_at(i);
@@ -179,17 +205,21 @@ __global__ void __launch_bounds__(1024)
     int ra = s_a[tid] - a, rb = s_b[tid] - b;  // exclusive prefix of this chunk
     for (int i = lo; i < hi; i++) {
         const int c = cnt_at(i);
-        sub_start[i] = rb;
+        const int bin = scan_bin(i, nbins, nb0, nb1);
+        if (bin >= 0) sub_start[bin] = rb;
         rb += (c + sub_max - 1) / sub_max;
         if (staged)
             s_cnt[scan_pad(i)] = ra;  // (only this thread reads its chunk)
-        else
-            start[i] = ra;
+        else if (bin >= 0)
+            start[bin] = ra;
         ra += c;
     }
     if (staged) {
         __syncthreads();
-        for (int i = tid; i < nbins; i += 1024) start[i] = s_cnt[scan_pad(i)];
+        for (int i = tid; i < slots; i += 1024) {
+            const int bin = scan_bin(i, nbins, nb0, nb1);
+            if (bin >= 0) start[bin] = s_cnt[scan_pad(i)];
+        }
     }
     if (tid == 1023) {
         nsub_total[0] = s_b[1023];
@@ -199,17 +229,18 @@ __global__ void __launch_bounds__(1024)
 }
 
 cudaError_t launch_bin_scan(const int *bin_count, int *bin_start, int *sub_start, int *nsub_total,
-                            int nbins, int sub_max, cudaStream_t stream)
+                            int nbins, int sub_max, cudaStream_t stream, int nb0, int nb1)
 {
-    constexpr int kStagedMax = 49152;  // bins staged in shared memory (196 KB with padding)
-    const int staged = nbins <= kStagedMax ? 1 : 0;
-    const size_t smem = staged ? (size_t)(scan_pad(nbins) + 1) * sizeof(int) : 0;
+    constexpr int kStagedMax = 49152;  // slots staged in shared memory (196 KB with padding)
+    const int slots = scan_slots(nbins, nb0, nb1);
+    const int staged = slots <= kStagedMax ? 1 : 0;
+    const size_t smem = staged ? (size_t)(scan_pad(slots) + 1) * sizeof(int) : 0;
     if (staged) {
         const cudaError_t e = ensure_dynamic_smem(bin_scan_kernel, smem);
         if (e != cudaSuccess) return e;
     }
     bin_scan_kernel<<<1, 1024, smem, stream>>>(bin_count, bin_start, sub_start, nsub_total,
-                                               nbins, sub_max, staged);
+                                               nbins, nb0, nb1, sub_max, staged);
     return cudaGetLastError();
 }
 

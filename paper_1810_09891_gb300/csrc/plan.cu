@@ -548,8 +548,12 @@ template <typename T> int do_set_nodes(gbnfft_plan *p, const void *x)
     GB_CHECK(launch_node_bin<T>(p->geom, static_cast<const T *>(x), p->M, rows,
                                 at<int2>(p, p->binrank), p->d_status, s));
     GB_CHECK(launch_bin_totals(rows, S0, p->nbins, count, s));
+    // 2-D: bins in 2 x 2 blocks (B then walks compact regions of twice the bin size); not when
+    // stripes of more than two bins need their bins' nodes contiguous
+    const bool blocked = p->d == 2 && p->stripe_R <= 2;
     GB_CHECK(launch_bin_scan(count, at<int>(p, p->binstart), at<int>(p, p->substart),
-                             at<int>(p, p->nsub), p->nbins, p->sub_max, s));
+                             at<int>(p, p->nsub), p->nbins, p->sub_max, s,
+                             blocked ? p->geom.nb[0] : 0, blocked ? p->geom.nb[1] : 0));
     GB_CHECK(launch_sub_starts(rows, at<int>(p, p->binstart), S0, p->nbins,
                                at<int>(p, p->rowstart), s));
     GB_CHECK(launch_node_scatter<T>(p->geom, static_cast<const T *>(x), p->M,
