@@ -291,11 +291,15 @@ __global__ void fill_subprobs_kernel(const int *__restrict__ count, const int *_
     if (b >= nbins) return;
     const int c = count[b];
     const int s0 = sub_start[b];
-    for (int k = 0; k * sub_max < c; k++) {
+    // ceil(c / sub_max) parts of equal size (within one node): the warps that take consecutive
+    // parts then run equally long
+    const int parts = (c + sub_max - 1) / sub_max;
+    for (int k = 0; k < parts; k++) {
+        const int lo = (int)((long long)c * k / parts), hi = (int)((long long)c * (k + 1) / parts);
         SubProb p;
         p.bin = b;
-        p.start = start[b] + k * sub_max;
-        p.count = min(sub_max, c - k * sub_max);
+        p.start = start[b] + lo;
+        p.count = hi - lo;
         p.pad = 0;
         subs[s0 + k] = p;
     }
