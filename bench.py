@@ -470,6 +470,31 @@ def parity(wl, y, h, m, n, sample=4096, seed=1, full_adjoint=True):
             "sample_nodes": int(idx.size), "sample_coefficients": int(kidx.size)}
 
 
+def run_concurrent(plan, fh, f, steps, flush, torch):
+    """Like run_variant, but each step runs the forward and the adjoint at the same time on two
+    streams (the plan keeps separate grids for them), joined before the step's end event;
+    returns per-step milliseconds."""
+    cur = torch.cuda.current_stream()
+    sf, sa = torch.cuda.Stream(), torch.cuda.Stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        a, b = ev[i]
+        a.record(cur)
+        sf.wait_stream(cur)
+        sa.wait_stream(cur)
+        with torch.cuda.stream(sf):
+            plan.trafo(fh)
+        with torch.cuda.stream(sa):
+            plan.adjoint(f)
+        cur.wait_stream(sf)
+        cur.wait_stream(sa)
+        b.record(cur)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
 def timed_steps(plan, fh, f, steps, warmup, flush, uuid, torch):
     """Warm-up, then `steps` timed forward + adjoint steps with the SM clocks sampled during the
     timed region; returns (forward ms, adjoint ms, outputs, clocks)."""
@@ -609,6 +634,14 @@ def ours(args):
     onchip = onchip_roofline(dom, wl, M, args.m, kernel_stages[dom]["ms_per_launch"], clk)
     alu = {"f32": alu_roofline(d, args.m, False, M, kernel_stages, clk)}
 
+    # the same steps with the forward and the adjoint running at the same time on two streams
+    run_concurrent(plan, fh, f, max(3, args.warmup), flush, torch)
+    conc = run_concurrent(plan, fh, f, args.steps, flush, torch)
+    concurrent = {"ms_per_step": sum(conc) / len(conc),
+                  "nodes_per_s": M * len(conc) / (sum(conc) * 1e-3),
+                  "how": "forward and adjoint of each step on two streams at once (separate "
+                         "grids per plan), L2 flushed between steps"}
+
     # cuFFT as a timed comparison for step F only: the full (unpruned) forward 2-D/3-D FFT of
     # the oversampled grid, complex64, torch.fft (cuFFT), no deconvolution or zero padding
     cufft = None
@@ -733,6 +766,7 @@ def ours(args):
             "fwd_nodes_per_s": M * args.steps / (sum(fwd) * 1e-3),
             "adj_nodes_per_s": M * args.steps / (sum(adj) * 1e-3),
             "set_nodes_ms": set_nodes_ms,
+            "concurrent": concurrent,
             "errors": errors,
             "roofline": roofline,
             "onchip": onchip,
@@ -894,6 +928,9 @@ def batched_record(args, dev, uuid, flush, torch):
     fused = b.fused
     b.capture(fhs, fs)
     total_ms, clk = timed_replays(True)
+    # the same step with the forward and the adjoint on two streams at once
+    b.capture(fhs, fs, concurrent=True)
+    conc_ms, _ = timed_replays()
     # the same step plus the backward of the forward transform (grad fhat and grad x for an
     # output gradient per problem) in one graph
     b.capture(fhs, fs, grad_fs=gs)
@@ -905,9 +942,14 @@ def batched_record(args, dev, uuid, flush, torch):
         b.set_fused(False)
         b.capture(fhs, fs)
         pbp_ms, _ = timed_replays()
+        b.capture(fhs, fs, concurrent=True)
+        pbpc_ms, _ = timed_replays()
         plan_by_plan = {"ms_per_step": pbp_ms / steps,
                         "nodes_per_s": sum(s["M"] for s in specs) * steps / (pbp_ms * 1e-3),
-                        "how": "per-plan launches on 8 side streams, one CUDA graph"}
+                        "how": "per-plan launches on 8 side streams, one CUDA graph",
+                        "concurrent": {"ms_per_step": pbpc_ms / steps,
+                                       "nodes_per_s": sum(s["M"] for s in specs) * steps /
+                                       (pbpc_ms * 1e-3)}}
         b.set_fused(True)
     nodes = sum(s["M"] for s in specs)
     # whole-step HBM view: the algorithmic bytes of every plan's four kernel stages over the
@@ -924,6 +966,10 @@ def batched_record(args, dev, uuid, flush, torch):
            "value": nodes * steps / (total_ms * 1e-3), "unit": UNIT,
            "graph": "one CUDA graph per step",
            "fused": fused, "plan_by_plan": plan_by_plan,
+           "concurrent": {"ms_per_step": conc_ms / steps,
+                          "nodes_per_s": nodes * steps / (conc_ms * 1e-3),
+                          "how": "the forward and the adjoint of the batch on two streams at once "
+                                 "in the graph"},
            "roofline": {"bound": "hbm", "kernel": "whole step (all plans, all stages)",
                         "achieved": alg / step_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                         "frac": alg / step_s / 1e9 / hbm_peak, "traffic": None,

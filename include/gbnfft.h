@@ -96,11 +96,15 @@ int nfft_plan_create(nfft_plan *out, int d, const int64_t *N, int64_t M, const i
 int nfft_destroy(nfft_plan plan);
 
 /* Make every later call enqueue on this CUDA stream (a cudaStream_t; NULL = legacy default).
- * All calls of a plan share its workspace: work already enqueued on the old stream must be
- * ordered before the next call on the new one (an event, or a synchronisation). */
+ * A plan keeps separate grids for the forward transform (and the node gradient) and for the
+ * adjoint, so one forward (or node gradient) and one adjoint may run at the same time on two
+ * streams. Any other two calls of a plan on different streams share workspace and must be
+ * ordered by the caller (an event, or a synchronisation); nfft_set_nodes must be ordered
+ * before and after every transform. */
 int nfft_set_stream(nfft_plan plan, void *cuda_stream);
 
-/* Device workspace the plan needs: oversampled grids, sorted node records, bin tables. */
+/* Device workspace the plan needs: oversampled grids (one set for the forward transform, one
+ * for the adjoint), sorted node records, bin tables. */
 int nfft_workspace_size(nfft_plan plan, size_t *bytes);
 
 /* Hand the plan a caller-owned device workspace of at least nfft_workspace_size() bytes,

@@ -281,19 +281,36 @@ class PlanBatch:
             self._call("nfft_batch_grad_x", coef, w, g_x)
         return g_fhat, g_x
 
-    def capture(self, fhats, fs, grad_fs=None) -> None:
+    def capture(self, fhats, fs, grad_fs=None, concurrent: bool = False) -> None:
         """Record forward(fhats) and adjoint(fs) of the whole batch into one CUDA graph. The
         graph reads the given input tensors and writes ``self.out_f`` / ``self.out_h``; copy new
         inputs into ``fhats`` / ``fs`` before each ``replay``. Nodes must be set beforehand.
         With ``grad_fs`` the graph also holds the backward of the forward transform for those
         output gradients (read from ``self.in_grad_f``), written to ``self.out_grad_fhat`` and
-        ``self.out_grad_x``."""
+        ``self.out_grad_x``. With ``concurrent`` the forward and the adjoint run on two streams
+        at the same time (a plan's forward and adjoint use separate grids); the backward, if
+        any, follows both."""
         self.in_fhat = list(fhats)
         self.in_f = list(fs)
         self.in_grad_f = list(grad_fs) if grad_fs is not None else None
+        if concurrent and not hasattr(self, "_pair"):
+            self._pair = (torch.cuda.Stream(self.device), torch.cuda.Stream(self.device))
 
         def step():
-            out = (self.trafo(self.in_fhat), self.adjoint(self.in_f))
+            if concurrent:
+                cur = torch.cuda.current_stream(self.device)
+                sf, sa = self._pair
+                sf.wait_stream(cur)
+                sa.wait_stream(cur)
+                with torch.cuda.stream(sf):
+                    yf = self.trafo(self.in_fhat)
+                with torch.cuda.stream(sa):
+                    yh = self.adjoint(self.in_f)
+                cur.wait_stream(sf)
+                cur.wait_stream(sa)
+                out = (yf, yh)
+            else:
+                out = (self.trafo(self.in_fhat), self.adjoint(self.in_f))
             if self.in_grad_f is not None:
                 out += self.backward(self.in_grad_f, self.in_fhat)
             return out

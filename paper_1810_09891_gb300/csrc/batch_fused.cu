@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kInterpThreads)
             T frac[2];
             bool edge;
             decode_node<T, 2>(sg, r, base, frac, edge);
-            const C *grid = static_cast<const C *>(plans[p].grid);
+            const C *grid = static_cast<const C *>(plans[p].fgrid);
             const T *tab = SHARED ? wc.c : static_cast<const T *>(sg.poly);
             const C v = edge ? interp_node<T, 2, MM, 0, 1>(sg, tab, grid, base, frac)
                              : interp_node<T, 2, MM, 1, 1>(sg, tab, grid, base, frac);
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kInterpThreads)
             T frac[2];
             bool edge;
             decode_node<T, 2>(sg, r, base, frac, edge);
-            const C *grid = static_cast<const C *>(plans[p].grid);
+            const C *grid = static_cast<const C *>(plans[p].fgrid);
             const T *tab = SHARED ? wc.c : static_cast<const T *>(sg.poly);
             C acc[2];
             if (!edge)

@@ -296,7 +296,8 @@ struct FusedFftPass {
 // The per-node stages of one plan (interpolation, node gradient, spreading) in a fused launch.
 struct FusedNodePlan {
     Geom g;
-    void *grid;          // the plan's oversampled grid (gA)
+    void *grid;          // the plan's spreading grid (gA)
+    void *fgrid;         // the plan's forward grid (gC), read by B and the node gradient
     const void *rec;     // sorted node records
     const int *perm;     // sorted position -> caller's node index
     const SubProb *subs; // spreading subproblems of the plan

@@ -260,7 +260,10 @@ struct gbnfft_plan {
     char *ws = nullptr;
     size_t ws_bytes = 0;
     bool ws_owned = false;
-    Region gA, gB, rec, perm, binrank, bincount, binstart, substart, nsub, subs, blu;
+    // gA, gB: grid and pruned intermediate of the adjoint; gC, gD: those of the forward
+    // transform and the node gradient (separate, so that a forward and an adjoint of one plan
+    // may run at the same time on different streams)
+    Region gA, gB, gC, gD, rec, perm, binrank, bincount, binstart, substart, nsub, subs, blu;
     Region rowcount, rowstart;  // row sub-bins of the bins: node counts and first positions
     // stripe-form spreading work (d = 2): super-bin counts, scans and items
     Region sbcount, sbstart, sbsub, sbn, sitems;
@@ -310,6 +313,8 @@ void layout_workspace(gbnfft_plan *p)
     const size_t recsz = p->dtype == NFFT_FP32 ? sizeof(RecF) : sizeof(RecD);
     put(p->gA, size_t(p->G) * p->csize);
     put(p->gB, size_t(p->Bsz) * p->csize);
+    put(p->gC, size_t(p->G) * p->csize);
+    put(p->gD, size_t(p->Bsz) * p->csize);
     put(p->rec, size_t(p->M) * recsz);
     put(p->perm, size_t(p->M) * sizeof(int));
     put(p->binrank, size_t(p->M) * sizeof(int2));
@@ -496,12 +501,13 @@ cudaError_t fft_pass(gbnfft_plan *p, int t, const typename Cplx<T>::type *in,
                                         pad ? 1 : 0, sign, dc, ax, p->stream);
 }
 
-// Forward FFT passes with D fused: fhat (centred, |I_N|) -> gA (|I_n|, natural order).
+// Forward FFT passes with D fused: fhat (centred, |I_N|) -> gC (|I_n|, natural order), through
+// gD.
 template <typename T> int forward_grid(gbnfft_plan *p, const void *fhat)
 {
     using C = typename Cplx<T>::type;
     const C *in = static_cast<const C *>(fhat);
-    C *A = at<C>(p, p->gA), *B = at<C>(p, p->gB);
+    C *A = at<C>(p, p->gC), *B = at<C>(p, p->gD);
     const int64_t *N = p->N, *n = p->n;
     if (p->d == 1) {
         GB_CHECK(fft_pass<T>(p, 0, in, A, 1, 1, true, -1));
@@ -607,7 +613,7 @@ template <typename T> int do_trafo(gbnfft_plan *p, const void *fhat, void *f)
     }
     if (rc) return rc;
     ProfScope ps(p, NFFT_STAGE_INTERP);
-    GB_CHECK(launch_interp<T>(p->geom, at<C>(p, p->gA), at<Rec>(p, p->rec), at<int>(p, p->perm),
+    GB_CHECK(launch_interp<T>(p->geom, at<C>(p, p->gC), at<Rec>(p, p->rec), at<int>(p, p->perm),
                               p->M, at<SubProb>(p, p->subs), at<int>(p, p->nsub), p->max_subs,
                               static_cast<C *>(f), p->stream));
     return NFFT_OK;
@@ -643,7 +649,7 @@ template <typename T> int do_grad(gbnfft_plan *p, const void *coef, const void *
     }
     if (rc) return rc;
     ProfScope ps(p, NFFT_STAGE_GRAD);
-    GB_CHECK(launch_grad<T>(p->geom, at<C>(p, p->gA), at<Rec>(p, p->rec), at<int>(p, p->perm),
+    GB_CHECK(launch_grad<T>(p->geom, at<C>(p, p->gC), at<Rec>(p, p->rec), at<int>(p, p->perm),
                             p->M, static_cast<const C *>(w), static_cast<T *>(gx), p->stream));
     return NFFT_OK;
 }
@@ -1541,6 +1547,7 @@ int fused_build(gbnfft_batch *b)
         q.g = p->geom;
         q.g.sw = StripeWork{};
         q.grid = at<float2>(p, p->gA);
+        q.fgrid = at<float2>(p, p->gC);
         q.rec = at<RecF>(p, p->rec);
         q.perm = at<int>(p, p->perm);
         q.subs = at<SubProb>(p, p->subs);
@@ -1556,12 +1563,14 @@ int fused_build(gbnfft_batch *b)
         // the four pruned passes of Algorithm "NFFT" (rows then columns, D fused) and of
         // Algorithm "adjoint NFFT" (columns then rows, D^H fused)
         float2 *A = at<float2>(p, p->gA), *B = at<float2>(p, p->gB);
+        float2 *Cf = at<float2>(p, p->gC), *Df = at<float2>(p, p->gD);  // forward buffers
         const int n0 = (int)p->n[0], n1 = (int)p->n[1], N0 = (int)p->N[0], N1 = (int)p->N[1];
         const int Pr = kFusedFftThreads * 8 / n1, Pc = kFusedFftThreads * 8 / n0;
         const FusedFftPass q4[kFusedPasses] = {
-            {nullptr, B, N0, 1, ilog2(n1), N1, Pr, fused_ls(n1, Pr, false), 1, p->tw[1],
+            {nullptr, Df, N0, 1, ilog2(n1), N1, Pr, fused_ls(n1, Pr, false), 1, p->tw[1],
              p->deconv[1]},
-            {B, A, 1, n1, ilog2(n0), N0, Pc, fused_ls(n0, Pc, true), 1, p->tw[0], p->deconv[0]},
+            {Df, Cf, 1, n1, ilog2(n0), N0, Pc, fused_ls(n0, Pc, true), 1, p->tw[0],
+             p->deconv[0]},
             {A, B, 1, n1, ilog2(n0), N0, Pc, fused_ls(n0, Pc, true), 0, p->tw[0], p->deconv[0]},
             {B, nullptr, N0, 1, ilog2(n1), N1, Pr, fused_ls(n1, Pr, false), 0, p->tw[1],
              p->deconv[1]}};
