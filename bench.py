@@ -181,10 +181,11 @@ def _clock_ghz(clk) -> float:
 
 
 def onchip_roofline(stage, wl, M, m, ms, clk):
-    """The spreading kernel against the L1 / shared-memory data pipe, which carries its tile
-    read-modify-writes: one 128-byte wavefront per cycle per SM. The tap floor is 2 (load and
-    store) x (2m)^d taps x 8 bytes (FP32 complex) / 128 per node; the measured wavefront count
-    comes from the committed ncu summary when it matches the kernel source."""
+    """The spreading kernel against the L1 / shared-memory data pipe, which carries the tile
+    read-modify-writes of the shared-memory tile forms: one 128-byte wavefront per cycle per SM.
+    The tap floor of those forms is 2 (load and store) x (2m)^d taps x 8 bytes (FP32 complex) /
+    128 per node; the measured wavefront and instruction counts come from the committed ncu
+    summary when it matches the kernel source."""
     if stage != "spread":
         return None
     d = len(wl["N"])
@@ -197,6 +198,15 @@ def onchip_roofline(stage, wl, M, m, ms, clk):
     if w is not None:
         out.update({"wavefronts_per_launch": w, "achieved_wavefronts_per_s": w / (ms * 1e-3),
                     "frac": w / (ms * 1e-3) / peak})
+    # the register-tile (rows) form moves few wavefronts and is bound by instruction issue
+    # instead: warp instructions per launch (ncu) over the event time, against one instruction
+    # per cycle per SM sub-partition (4 per SM)
+    wi = profiled_value(stage, wl["name"], "warp_instructions")
+    if wi is not None:
+        ipeak = NUM_SMS * 4 * _clock_ghz(clk) * 1e9
+        out["issue"] = {"warp_instructions_per_launch": wi,
+                        "achieved_per_s": wi / (ms * 1e-3), "peak_per_s": ipeak,
+                        "frac": wi / (ms * 1e-3) / ipeak}
     return out
 
 
