@@ -554,6 +554,11 @@ def clusters_record(args, flush, dev, hbm_peak, peak_kind, uuid, torch):
            "roofline": roof, "stages_us": {k: 1e3 * v["ms_per_launch"] for k, v in stages.items()},
            "clocks": clk,
            "l2": "inputs larger than L2 (grid 134 MB, nodes 84 MB); flushed between steps too"}
+    run_concurrent(plan, fh, f, 3, flush, torch)
+    conc = run_concurrent(plan, fh, f, steps, flush, torch)
+    rec["concurrent"] = {"ms_per_step": sum(conc) / len(conc),
+                         "nodes_per_s": M * len(conc) / (sum(conc) * 1e-3),
+                         "how": "forward and adjoint of each step on two streams at once"}
     if not args.no_parity:
         rec["errors"] = parity(wl, y.cpu().numpy(), h.cpu().numpy(), 4, plan.n,
                                full_adjoint=False)
