@@ -183,7 +183,8 @@ int nfft_batch_grad_x(nfft_batch batch, const void *const *coef, const void *con
  * call runs each stage for all plans in one launch on the batch's stream: the FFT passes over a
  * work list of (plan, lines) blocks, the interpolation and node gradient over (plan, 128 nodes)
  * blocks, and the spreading over the plans' subproblem lists concatenated and claimed by
- * persistent CTAs. The first fused call allocates the per-plan tables (device memory and pinned
+ * persistent warps (the register-tile form 8, when every plan spreads automatically with sort
+ * bins of one height, 4 or 8 rows) or CTAs (the half-warp form 5). The first fused call allocates the per-plan tables (device memory and pinned
  * host memory), uploads them on the batch's stream and waits for the upload; a call after a
  * plan's workspace or tuning changed rebuilds them the same way. Make such a call before
  * capturing the batch's calls into a CUDA graph (allocation and waiting are not allowed during
