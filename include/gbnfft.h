@@ -345,9 +345,9 @@ int nfft_use_device(int device);
  * share the array: calls that overlap on the GPU (other streams, other threads) race and give
  * wrong results, so serialise them.
  * Set-up: the first call on a device looks up the array's device address there
- * (cudaGetSymbolAddress) and keeps it for the life of the process; make that first call before
- * any stream capture begins. The kept address does not survive cudaDeviceReset (or any other
- * destruction of the device's primary context): do not call this entry point after one.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process. The kept address does not
+ * survive cudaDeviceReset (or any other destruction of the device's primary context): do not
+ * call this entry point after one.
  * Returns without waiting for the GPU. */
 int nfft_trafo_1d_noalloc(int64_t N, int64_t M, const int64_t *n, int m, const double *x,
                           const void *fhat, void *f, void *stream);
