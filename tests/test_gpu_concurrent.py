@@ -1,7 +1,8 @@
 """A forward and an adjoint of the same plan running at the same time on two streams (the plan
 keeps separate grids for the two), checked against the FP64 oracle: single plans of every d,
 and batches (fused and plan by plan) captured in a CUDA graph with the two transforms on two
-streams, replayed with new inputs."""
+streams, replayed with new inputs; and calls whose inputs are copied on another stream just
+before them."""
 import numpy as np
 import pytest
 import torch
@@ -44,6 +45,57 @@ def test_forward_and_adjoint_on_two_streams(N, dtype):
             <= TOL[dtype]
         assert rel_l2(h.cpu().numpy(), oracle.nfft_adjoint(xr, rounded(f, dtype), N, n=plan.n,
                                                            m=4)) <= TOL[dtype]
+    assert plan.status() == 0
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_inputs_copied_on_a_copy_stream_just_before_each_call(dtype):
+    """Each step's inputs arrive by copies from pinned host memory on a copy stream, into one of
+    two device buffers, and the compute stream waits for them by an event just before the
+    calls (the pipelined host-buffer pattern). Every result matches the oracle of its own step's
+    inputs: no kernel of a call (the FFT passes start as programmatic dependents of the previous
+    kernel) reads its input before the copies it waits for have landed."""
+    torch.cuda.set_device(DEV)
+    N, M, K, steps = (512, 512), 50000, 4, 24
+    npdt = np.float32 if dtype == torch.float32 else np.float64
+    cnp = np.complex64 if dtype == torch.float32 else np.complex128
+    cdt = torch.complex64 if dtype == torch.float32 else torch.complex128
+    x = W.round_nodes(W.uniform_nodes(M, 2, seed_offset=1100), npdt)
+    plan = Plan(N, M, m=4, dtype=dtype, device=DEV)
+    plan.set_nodes(to_dev(x, dtype))
+    xr = rounded(x, dtype)
+    fhs = [W.gaussian_fhat(N, 1110 + k) for k in range(K)]
+    fs = [W.gaussian_values(M, 1120 + k) for k in range(K)]
+    pin_fh = [torch.tensor(a.astype(cnp)).pin_memory() for a in fhs]
+    pin_f = [torch.tensor(a.astype(cnp)).pin_memory() for a in fs]
+    comp = torch.cuda.current_stream(DEV)
+    cin = torch.cuda.Stream(DEV)
+    d_fh = [torch.empty(N, dtype=cdt, device=DEV) for _ in range(2)]
+    d_f = [torch.empty(M, dtype=cdt, device=DEV) for _ in range(2)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_free = [torch.cuda.Event() for _ in range(2)]
+    for e in ev_free:
+        e.record(comp)
+    ys, hs, which = [], [], []
+    for s in range(steps):
+        j, k = s & 1, (s * 3) % K  # buffer j, input set k (consecutive steps differ)
+        with torch.cuda.stream(cin):
+            cin.wait_event(ev_free[j])
+            d_fh[j].copy_(pin_fh[k], non_blocking=True)
+            d_f[j].copy_(pin_f[k], non_blocking=True)
+            ev_in[j].record(cin)
+        comp.wait_event(ev_in[j])
+        ys.append(plan.trafo(d_fh[j]))
+        hs.append(plan.adjoint(d_f[j]))
+        ev_free[j].record(comp)
+        which.append(k)
+    torch.cuda.synchronize()
+    ref_y = [oracle.nfft(xr, rounded(fhs[k], dtype), n=plan.n, m=4) for k in range(K)]
+    ref_h = [oracle.nfft_adjoint(xr, rounded(fs[k], dtype), N, n=plan.n, m=4) for k in range(K)]
+    for y, h, k in zip(ys, hs, which):
+        assert rel_l2(y.cpu().numpy(), ref_y[k]) <= TOL[dtype]
+        assert rel_l2(h.cpu().numpy(), ref_h[k]) <= TOL[dtype]
     assert plan.status() == 0
     plan.close()
 
